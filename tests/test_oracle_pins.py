@@ -1,0 +1,448 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix.
+
+Nothing here compares the oracle with itself: each test checks a closed form,
+an invariant stated in the paper, a textbook special case, a library routine,
+or central finite differences of the oracle's own step.
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2609_08800_gb300 import scenes as S
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+
+
+# --------------------------------------------------------------------------
+# building blocks
+# --------------------------------------------------------------------------
+
+def test_fb_complementarity():
+    """Eq. (4): phi(a,b) = 0 <=> a >= 0, b >= 0, ab = 0 (eps -> 0)."""
+    for a, b in [(0.0, 3.0), (2.0, 0.0), (0.0, 0.0)]:
+        assert abs(O.fb(a, b, 0.0)[0]) < 1e-15
+    for a, b in [(1.0, 1.0), (-1.0, 2.0), (2.0, -0.5), (-1.0, -1.0)]:
+        assert abs(O.fb(a, b, 0.0)[0]) > 1e-3
+    # closed form and derivatives against central differences
+    a, b, eps = 0.3, -0.7, 1e-8
+    phi, fa, fb_ = O.fb(a, b, eps)
+    assert phi == pytest.approx(a + b - math.sqrt(a * a + b * b + eps * eps), abs=1e-15)
+    d = 1e-6
+    assert fa == pytest.approx((O.fb(a + d, b, eps)[0] - O.fb(a - d, b, eps)[0]) / (2 * d), rel=1e-7)
+    assert fb_ == pytest.approx((O.fb(a, b + d, eps)[0] - O.fb(a, b - d, eps)[0]) / (2 * d), rel=1e-7)
+
+
+def test_friction_weight_branches():
+    """Sec. III-B: W -> 0 when sticking, W = v_t/(mu lambda_n) on the cone while sliding, W >= 0."""
+    mu, ln = 0.8, 10.0
+    assert O.friction_W(0.0, 0.0, ln, 1.0, 0.5, mu, 1e-8, 0.05) < 1e-12
+    vt = 0.4
+    W = O.friction_W(vt * 0.6, vt * 0.8, ln, -mu * ln * 0.6, -mu * ln * 0.8, mu, 1e-8, 0.05)
+    assert W == pytest.approx(vt / (mu * ln), rel=1e-6)
+    rng = np.random.default_rng(0)
+    for _ in range(200):
+        args = rng.normal(size=5)
+        assert O.friction_W(*args, mu, 1e-8, 0.05) >= 0.0
+
+
+def _rodrigues(axis, ang):
+    k = np.asarray(axis, float) / np.linalg.norm(axis)
+    K = np.array([[0, -k[2], k[1]], [k[2], 0, -k[0]], [-k[1], k[0], 0]])
+    return np.eye(3) + math.sin(ang) * K + (1 - math.cos(ang)) * K @ K
+
+
+def test_rotation_matches_axis_angle():
+    rng = np.random.default_rng(1)
+    for _ in range(20):
+        axis, ang = rng.normal(size=3), rng.uniform(-3, 3)
+        k = axis / np.linalg.norm(axis)
+        q = np.r_[math.cos(ang / 2), math.sin(ang / 2) * k] * rng.uniform(0.5, 2.0)   # non-unit allowed
+        v = rng.normal(size=3)
+        np.testing.assert_allclose(O.rotate(q, v), _rodrigues(axis, ang) @ v, atol=1e-13)
+
+
+def test_dense_solve_matches_numpy():
+    rng = np.random.default_rng(2)
+    for n in (1, 5, 37):
+        B = rng.normal(size=(n, n))
+        A = B @ B.T + 0.1 * np.eye(n)
+        b = rng.normal(size=n)
+        np.testing.assert_allclose(O.lu_solve(A, b), np.linalg.solve(A, b), rtol=1e-10, atol=1e-12)
+
+
+# --------------------------------------------------------------------------
+# closed forms of the step (Eqs. (1), (2))
+# --------------------------------------------------------------------------
+
+def _box_cfg(kappa=0.0):
+    return S.SolverConfig(budget=60, k_min=4, tol=1e-11, kappa=kappa)
+
+
+def test_free_flight_and_torque_free_spin():
+    sc = S.box_drop_scene()
+    orc = O.Oracle(sc, _box_cfg())
+    s = np.zeros(sc.n_state)
+    s[0:3] = (0.1, -0.2, 5.0)
+    s[3:7] = (1, 0, 0, 0)
+    s[7:10] = (0.3, -0.1, 0.2)
+    s[10:13] = (0.0, 0.0, 1.5)       # spin about the principal z axis
+    h = 0.1
+    r = orc.step(s, np.zeros(1), h)
+    out = r["state"]
+    assert r["rows"] == 0
+    v = s[7:10] + h * np.array([0, 0, -9.81])
+    np.testing.assert_allclose(out[7:10], v, atol=1e-14)
+    np.testing.assert_allclose(out[0:3], s[0:3] + h * v, atol=1e-14)
+    np.testing.assert_allclose(out[10:13], s[10:13], atol=1e-14)      # no gyroscopic torque
+    # quaternion: normalised first-order update q + h/2 (0, w) (x) q
+    qz = np.array([1.0, 0.0, 0.0, 0.5 * h * 1.5])
+    np.testing.assert_allclose(out[3:7], qz / np.linalg.norm(qz), atol=1e-14)
+
+
+def test_box_drop_closed_form():
+    gold = json.load(open(os.path.join(GOLD, "box_drop_closed_form.json")))
+    sc, st = S.box_drop_inputs(0)
+    v0 = st[7, 0]
+    assert v0 > gold["stop_threshold_v0"]
+    orc = O.Oracle(sc, _box_cfg())
+    h = gold["h"]
+    s = st[:, 0]
+    sums = []
+    for k in range(6):
+        r = orc.step(s, np.zeros(1), h)
+        assert r["status"] == 0 and r["residual"] < 1e-10
+        imp = r["impulses"][sc.contact_row_offset:].reshape(-1, 3)
+        sums.append((imp[:, 0].sum(), imp[:, 1].sum(), imp[:, 2].sum()))
+        if k == 0:
+            assert r["state"][9] == pytest.approx(gold["step1_uz"], abs=1e-9)
+            assert r["state"][7] == pytest.approx(v0 + gold["step1_du_x_sliding"], abs=1e-9)
+            assert (r["ids"] >= 0).sum() == 4
+        s = r["state"]
+    assert sums[0][0] == pytest.approx(gold["step1_sum_hn"], abs=1e-8)
+    assert sums[0][1] == pytest.approx(-gold["mu"] * gold["step1_sum_hn"], abs=1e-8)
+    assert sums[1][0] == pytest.approx(gold["step2_sum_hn"], abs=1e-8)
+    for k in range(2, 6):
+        assert sums[k][0] == pytest.approx(gold["rest_sum_hn"], abs=1e-8)
+        assert abs(sums[k][1]) < 1e-8 and abs(sums[k][2]) < 1e-8
+    np.testing.assert_allclose(s[7:13], 0.0, atol=1e-9)
+
+
+def _box_rollout_x(orc, sc, v0, h, T):
+    s = S.box_drop_state(sc, v0)[:, 0]
+    states = [s]
+    for _ in range(T):
+        states.append(orc.step(states[-1], np.zeros(1), h)["state"])
+    return states
+
+
+def test_box_final_position_and_gradient_closed_form():
+    """x_T = x0 + h max(0, v0 - 0.3848) and dx_T/dv0 = h (central differences of the
+    oracle's forward rollout, hard contact)."""
+    gold = json.load(open(os.path.join(GOLD, "box_drop_closed_form.json")))
+    sc = S.box_drop_scene()
+    orc = O.Oracle(sc, _box_cfg())
+    h, T, thr = 0.1, 20, gold["stop_threshold_v0"]
+    for v0 in (0.2, 0.6369616873214543, 0.9):
+        xT = _box_rollout_x(orc, sc, v0, h, T)[-1][0]
+        assert xT == pytest.approx(h * max(0.0, v0 - thr), abs=1e-9)
+        d = 1e-5
+        fd = (_box_rollout_x(orc, sc, v0 + d, h, T)[-1][0] - _box_rollout_x(orc, sc, v0 - d, h, T)[-1][0]) / (2 * d)
+        assert fd == pytest.approx(h if v0 > thr else 0.0, abs=1e-7)
+
+
+def test_exact_adjoint_rollout_matches_fd():
+    """Exact-IFT adjoint swept over the 20-step drop (compliance 1e-4 makes the
+    four-corner impulse split unique) against central differences of the rollout."""
+    sc = S.box_drop_scene()
+    orc = O.Oracle(sc, S.SolverConfig(budget=80, k_min=4, tol=1e-12, kappa=1e-4))
+    h, T = 0.1, 20
+    for v0 in (0.2, 0.6369616873214543):
+        states = _box_rollout_x(orc, sc, v0, h, T)
+        g = np.zeros(sc.n_state)
+        g[0] = 1.0
+        for t in reversed(range(T)):
+            g = orc.step_adjoint(states[t], np.zeros(1), h, g, mode=O.ADJ_EXACT)["dstate"]
+        d = 1e-6
+        fd = (_box_rollout_x(orc, sc, v0 + d, h, T)[-1][0] - _box_rollout_x(orc, sc, v0 - d, h, T)[-1][0]) / (2 * d)
+        assert g[7] == pytest.approx(fd, abs=1e-6)
+        if v0 > 0.3848:
+            assert g[7] == pytest.approx(h, rel=5e-3)      # h up to the O(kappa) micro-slip
+
+
+def test_sliding_friction_is_timestep_consistent():
+    """Sec. III-B: the converged sliding force does not depend on h (mu m g)."""
+    sc = S.box_drop_scene()
+    orc = O.Oracle(sc, _box_cfg())
+    for h in (0.02, 0.05, 0.1, 0.2):
+        s = S.box_drop_state(sc, 0.0, gap=0.0)[:, 0]
+        for _ in range(3):
+            s = orc.step(s, np.zeros(1), h)["state"]          # settle at rest
+        s[7] = 5.0                                            # fast slide, stays sliding this step
+        r = orc.step(s, np.zeros(1), h)
+        imp = r["impulses"][sc.contact_row_offset:].reshape(-1, 3)
+        assert imp[:, 1].sum() / h == pytest.approx(-0.8 * 10.0 * 9.81, rel=1e-8)
+        assert imp[:, 0].sum() / h == pytest.approx(10.0 * 9.81, rel=1e-8)
+
+
+# --------------------------------------------------------------------------
+# robot: invariants at convergence (parity otherwise unpinned: no closed form)
+# --------------------------------------------------------------------------
+
+def _robot_states(n=6, seed=0):
+    sc = S.robot_box_scene()
+    return sc, S.robot_box_states(sc, n, seed=seed)
+
+
+def _world_R(q):
+    return S._quat_to_matrix(np.asarray(q))
+
+
+def _qmul(a, b):
+    aw, av, bw, bv = a[0], a[1:], b[0], b[1:]
+    return np.r_[aw * bw - av @ bv, aw * bv + bw * av + np.cross(av, bv)]
+
+
+@pytest.mark.parametrize("w", range(6))
+def test_robot_step_invariants(w):
+    sc, st = _robot_states()
+    cfg = S.SolverConfig(budget=60, k_min=4, tol=1e-9, kappa=1e-4)
+    orc = O.Oracle(sc, cfg)
+    ub = np.array([2.0, 2.0, 2.0, 2.0])
+    s = st[:, w]
+    h = 0.1
+    for _ in range(3):
+        r = orc.step(s, ub, h)
+        if r["status"] == 0:
+            break
+        s = r["state"]
+    if r["status"] != 0:
+        pytest.skip("step did not converge within the budget (best iterate returned)")
+    out, lam = r["state"], r["state"][sc.lam_index:]
+    nb = sc.n_bodies
+    # joint closure (Eq. (3), E = 0): anchors coincide, axes aligned
+    for j, jt in enumerate(sc.joints):
+        pp, Rp = out[7 * jt.parent:7 * jt.parent + 3], _world_R(out[7 * jt.parent + 3:7 * jt.parent + 7])
+        pc, Rc = out[7 * jt.child:7 * jt.child + 3], _world_R(out[7 * jt.child + 3:7 * jt.child + 7])
+        gap = (pp + Rp @ np.array(jt.anchor_parent)) - (pc + Rc @ np.array(jt.anchor_child))
+        assert np.abs(gap).max() < 1e-8
+        aw = Rc @ np.array(jt.axis_child)
+        for b in jt.perp_parent:
+            assert abs((Rp @ np.array(b)) @ aw) < 1e-8
+        # servo law (Eq. (8)): lambda_c = k_p (ubar - J_c u+); J_c u+ is the relative rotation
+        # rate about the axle through the step's map w -> E(w) w = w / (1 + (h|w|/2)^2)
+        wp = out[7 * nb + 6 * jt.parent + 3:7 * nb + 6 * jt.parent + 6]
+        wc = out[7 * nb + 6 * jt.child + 3:7 * nb + 6 * jt.child + 6]
+        eff = lambda w: w / (1.0 + (0.5 * h) ** 2 * (w @ w))
+        # the axle is evaluated at q+ before normalisation, i.e. q- + h G(q-) u+
+        qraw = s[7 * jt.parent + 3:7 * jt.parent + 7] + 0.5 * h * _qmul(np.r_[0.0, wp], s[7 * jt.parent + 3:7 * jt.parent + 7])
+        rel = (_world_R(qraw) @ np.array(jt.axis_parent)) @ (eff(wc) - eff(wp))
+        lc = lam[5 * len(sc.joints) + j]
+        assert lc == pytest.approx(jt.kp * (ub[j] - rel), abs=1e-6 * jt.kp)
+    # contacts: non-penetration, sign, complementarity, cone
+    act, ids, nd = orc.contacts(st[:, w] if False else s, h)
+    cl = lam[5 * len(sc.joints) + sc.n_servos:].reshape(-1, 3)
+    for sl in np.nonzero(act)[0]:
+        ln, lf = cl[sl, 0], cl[sl, 1:]
+        assert ln >= -1e-6
+        assert np.linalg.norm(lf) <= 0.9 * max(ln, 0.0) * (1 + 1e-6) + 1e-9
+    inactive = np.nonzero(act == 0)[0]
+    assert np.abs(cl[inactive]).max() == 0.0
+
+
+# --------------------------------------------------------------------------
+# Jacobian: analytic rows equal the definition d c(q+(u))/du / h
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("w", range(4))
+def test_row_jacobian_matches_definition(w):
+    sc, st = _robot_states(n=4, seed=3)
+    cfg = S.SolverConfig(kappa=1e-4)
+    orc = O.Oracle(sc, cfg)
+    rng = np.random.default_rng(w)
+    s = st[:, w]
+    nb = sc.n_bodies
+    u = s[7 * nb:13 * nb] + rng.normal(scale=1.0, size=6 * nb)
+    lam = rng.normal(size=sc.m_max)
+    rows = orc.rows(s, np.zeros(4), 0.1, u, lam)
+    assert rows["J"].shape[0] >= 24
+    mask = rows["meta"][:, 0] != 1          # servo rows are not covered by the definition here
+    np.testing.assert_allclose(rows["J"][mask], rows["Jdual"][mask], rtol=1e-9, atol=1e-9)
+
+
+def test_box_jacobian_matches_definition():
+    sc = S.box_drop_scene()
+    orc = O.Oracle(sc, S.SolverConfig())
+    s = S.box_drop_state(sc, 0.3, gap=0.001)[:, 0]
+    s[3:7] = np.array([0.99, 0.05, -0.08, 0.1]) / np.linalg.norm([0.99, 0.05, -0.08, 0.1])
+    s[2] = 0.13
+    rng = np.random.default_rng(5)
+    u = rng.normal(size=6)
+    rows = orc.rows(s, np.zeros(1), 0.1, u, rng.normal(size=sc.m_max))
+    assert rows["J"].shape[0] > 0
+    np.testing.assert_allclose(rows["J"], rows["Jdual"], rtol=1e-9, atol=1e-9)
+
+
+# --------------------------------------------------------------------------
+# adjoint against central finite differences of the oracle's own step
+# --------------------------------------------------------------------------
+
+def _fd_grad(orc, s, ub, h, g, idx, eps=1e-6):
+    out = np.zeros(len(idx))
+    for k, i in enumerate(idx):
+        sp, sm = s.copy(), s.copy()
+        sp[i] += eps; sm[i] -= eps
+        out[k] = g @ (orc.step(sp, ub, h)["state"] - orc.step(sm, ub, h)["state"]) / (2 * eps)
+    return out
+
+
+def _fd_ctrl(orc, s, ub, h, g, eps=1e-6):
+    out = np.zeros(len(ub))
+    for i in range(len(ub)):
+        up, um = ub.copy(), ub.copy()
+        up[i] += eps; um[i] -= eps
+        out[i] = g @ (orc.step(s, up, h)["state"] - orc.step(s, um, h)["state"]) / (2 * eps)
+    return out
+
+
+def _resting_box(kappa):
+    sc = S.box_drop_scene()
+    orc = O.Oracle(sc, S.SolverConfig(budget=60, k_min=4, tol=1e-12, kappa=kappa))
+    s = S.box_drop_state(sc, 0.0, gap=0.0)[:, 0]
+    for _ in range(3):
+        s = orc.step(s, np.zeros(1), 0.1)["state"]
+    s[7], s[8] = 0.05, 0.02          # small push: the box sticks
+    return sc, orc, s
+
+
+def _rolling_robot(kappa):
+    sc = S.robot_plane_scene()
+    st = S.robot_box_states(sc, 2, seed=0, phases=False)
+    orc = O.Oracle(sc, S.SolverConfig(budget=60, k_min=4, tol=1e-12, kappa=kappa))
+    s, ub = st[:, 1], np.full(4, 2.0)
+    for _ in range(5):
+        s = orc.step(s, ub, 0.1)["state"]
+    return sc, orc, s, ub
+
+
+@pytest.mark.parametrize("kappa", [0.0, 1e-4])
+def test_exact_adjoint_matches_fd_box(kappa):
+    sc, orc, s = _resting_box(kappa)
+    g = np.random.default_rng(7).normal(size=sc.n_state)
+    g[13:] = 0.0
+    ad = orc.step_adjoint(s, np.zeros(1), 0.1, g, mode=O.ADJ_EXACT)["dstate"][:13]
+    fd = _fd_grad(orc, s, np.zeros(1), 0.1, g, range(13))
+    assert np.abs(ad - fd).max() <= 1e-6 * np.abs(fd).max()
+
+
+def test_exact_adjoint_matches_fd_robot():
+    sc, orc, s, ub = _rolling_robot(1e-4)
+    g = np.random.default_rng(8).normal(size=sc.n_state)
+    g[13 * sc.n_bodies:] = 0.0
+    r = orc.step_adjoint(s, ub, 0.1, g, mode=O.ADJ_EXACT)
+    fd = _fd_grad(orc, s, ub, 0.1, g, range(13 * sc.n_bodies))
+    assert np.abs(r["dstate"][:13 * sc.n_bodies] - fd).max() <= 1e-6 * np.abs(fd).max()
+    fdu = _fd_ctrl(orc, s, ub, 0.1, g)
+    assert np.abs(r["dubar"] - fdu).max() <= 1e-6 * np.abs(fdu).max()
+
+
+@pytest.mark.parametrize("kappa", [0.0, 1e-4])
+def test_paper_adjoint_matches_fd_on_sticking_box(kappa):
+    """Sec. III-D: the paper's adjoint (forward Schur matrix, W lagged) against central
+    differences on a sticking contact; the paper reports <= 0.4 % on sticking scenes."""
+    sc, orc, s = _resting_box(kappa)
+    g = np.random.default_rng(9).normal(size=sc.n_state)
+    g[13:] = 0.0
+    ad = orc.step_adjoint(s, np.zeros(1), 0.1, g, mode=O.ADJ_PAPER)["dstate"][:13]
+    fd = _fd_grad(orc, s, np.zeros(1), 0.1, g, range(13))
+    assert np.abs(ad - fd).max() <= 4e-3 * np.abs(fd).max()
+
+
+def test_paper_adjoint_deviation_on_robot_is_bounded():
+    """The paper's Newton matrix drops the geometric stiffness d(J^T lambda)/dq (it keeps M
+    block diagonal); at h = 0.1 on the robot that costs a few percent against FD."""
+    sc, orc, s, ub = _rolling_robot(1e-4)
+    g = np.random.default_rng(10).normal(size=sc.n_state)
+    g[13 * sc.n_bodies:] = 0.0
+    r = orc.step_adjoint(s, ub, 0.1, g, mode=O.ADJ_PAPER)
+    fd = _fd_grad(orc, s, ub, 0.1, g, range(13 * sc.n_bodies))
+    assert np.abs(r["dstate"][:13 * sc.n_bodies] - fd).max() <= 0.1 * np.abs(fd).max()
+
+
+def test_truncated_pullback_differs_only_in_contact_terms():
+    """Sec. IV-D: truncation holds contact geometry fixed; with no contacts it is exact."""
+    sc = S.box_drop_scene()
+    cfg_f = S.SolverConfig(budget=60, tol=1e-12, pullback=S.PULLBACK_FULL)
+    cfg_t = S.SolverConfig(budget=60, tol=1e-12, pullback=S.PULLBACK_TRUNCATED)
+    s = S.box_drop_state(sc, 0.3, gap=3.0)[:, 0]
+    s[10:13] = (0.2, -0.4, 0.9)
+    g = np.random.default_rng(11).normal(size=sc.n_state)
+    a = O.Oracle(sc, cfg_f).step_adjoint(s, np.zeros(1), 0.1, g)["dstate"]
+    b = O.Oracle(sc, cfg_t).step_adjoint(s, np.zeros(1), 0.1, g)["dstate"]
+    np.testing.assert_allclose(a, b, rtol=1e-12, atol=1e-12)
+    sc2, orc2, s2 = _resting_box(1e-4)
+    a = O.Oracle(sc2, S.SolverConfig(budget=60, tol=1e-12, kappa=1e-4)).step_adjoint(s2, np.zeros(1), 0.1, g)
+    b = O.Oracle(sc2, S.SolverConfig(budget=60, tol=1e-12, kappa=1e-4, pullback=1)).step_adjoint(s2, np.zeros(1), 0.1, g)
+    assert np.abs(a["dstate"] - b["dstate"]).max() > 1e-6        # contact terms do change
+
+
+# --------------------------------------------------------------------------
+# contact predicate: hand-placed cases
+# --------------------------------------------------------------------------
+
+def test_box_corner_activation():
+    sc = S.box_drop_scene()
+    orc = O.Oracle(sc, S.SolverConfig())
+    h = 0.1
+    s = S.box_drop_state(sc, 0.0, gap=0.0)[:, 0]
+    s[2] = 0.1 + 0.019 + h * h * 9.81          # margin - 1 mm + one step at the predicted h g speed
+    act, ids, _ = orc.contacts(s, h)
+    assert list(act) == [1, 1, 1, 1, 0, 0, 0, 0]
+    s[2] = 0.1 + 0.021 + h * h * 9.81
+    act, _, _ = orc.contacts(s, h)
+    assert act.sum() == 0
+    s[9] = -1.0                                                     # approaching at 1 m/s
+    act, _, _ = orc.contacts(s, h)
+    assert list(act[:4]) == [1, 1, 1, 1]
+    assert list(ids[:4]) == [(0 << 24) | (k << 20) for k in range(4)]
+
+
+def _robot_at(x, z=None, scene=None):
+    sc = scene or S.robot_box_scene()
+    s = np.zeros((sc.n_state, 1))
+    S._place_robot(s, sc, 0, x, 0.0, S.ROBOT_CHASSIS_Z if z is None else z, 0.0)
+    return sc, s[:, 0]
+
+
+def test_wheel_features_on_box_scene():
+    sc, s = _robot_at(0.0)
+    orc = O.Oracle(sc, S.SolverConfig())
+    act, ids, nd = orc.contacts(s, 0.1)
+    # flat ground: each wheel touches the ground with both rims (feature 0), nothing else
+    assert act.sum() == 8
+    assert all((ids[act > 0] & 0xFFFFF) == 0)
+    # front wheels against the face: ground + near face (feature 2) on both rims
+    sc, s = _robot_at(1.0 - 0.25 - 0.15 - 0.005)
+    act, ids, nd = orc.contacts(s, 0.1)
+    feats = sorted(set(int(i) & 0xF for i in ids[act > 0]))
+    assert feats == [0, 2]
+    front = [int(i) for i in ids[act > 0] if (int(i) >> 24) in (1, 2)]
+    assert sum((i & 0xF) == 2 for i in front) == 4
+    for sl in np.nonzero(act)[0]:
+        if ids[sl] & 0xF == 2:
+            np.testing.assert_allclose(nd[sl], [-1, 0, 0, -1.0], atol=1e-7)
+    # robot on top: top face only
+    sc, s = _robot_at(1.5, z=S.ROBOT_CHASSIS_Z + 0.15)
+    act, ids, nd = orc.contacts(s, 0.1)
+    assert act.sum() == 8 and all((ids[act > 0] & 0xF) == 1)
+    # front wheels just past the back edge: edge feature with normal toward the rim centre
+    sc, s = _robot_at(2.0 - 0.25 + 0.03, z=S.ROBOT_CHASSIS_Z + 0.15)
+    act, ids, nd = orc.contacts(s, 0.1)
+    edge = [sl for sl in np.nonzero(act)[0] if ids[sl] & 0xF == 3]
+    assert len(edge) == 4
+    for sl in edge:
+        n = nd[sl, :3]
+        assert n[0] > 0 and n[2] > 0 and abs(np.linalg.norm(n) - 1) < 1e-6

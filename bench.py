@@ -1,0 +1,427 @@
+"""Benchmark: forward + adjoint world-steps/s of the Ostrich per-step solve on GB300.
+
+Workload (one bench step): the wheeled robot over a box obstacle, 8192 worlds,
+FP32, a 10-step horizon chunk (the checkpoint segment length): 10 forward steps
+that record the tape, then 10 adjoint steps back through it, every step one launch
+of the step kernel / adjoint kernel over all worlds.  Inputs (states, per-step
+servo targets from seeded control splines, the loss cotangent) are resident in HBM
+when the timed region starts; every bench step restarts from the same inputs.
+
+Prints one JSON line.  `value` counts forward+adjoint world-steps per second over
+all ranks (replicas: each GPU runs its own 8192 worlds).  Extra keys:
+  e2e            the same metric through the public API with pinned host buffers,
+                 host->device inputs and device->host results inside the timed region
+  plain_form     the same kernels launched once per world per step (W = 1)
+  roofline       ALU roofline of the step kernel (algorithmic flops / event time)
+  cpu_baseline   the FP64 oracle on the host cores, on a bounded sample
+`--impl reference` times the FP64 oracle instead (the reference arm).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2609_08800_gb300 import scenes as S  # noqa: E402
+from paper_2609_08800_gb300 import spline as SP  # noqa: E402
+
+METRIC = "fwd+adjoint world-steps/s @8192 worlds"
+UNIT = "world-steps/s"
+H = 0.1
+CHUNK = 10
+FP32_TOL = 1e-4      # m/s: the FP32 residual floor of this scene (FP32-rounded exact states sit near 1e-5)
+SM_COUNT_GB300 = 152
+FP32_LANES_PER_SM = 128
+
+
+def world_flops(iters, rows, groups, sep, refine=2, trials_per_iter=1):
+    """Algorithmic FP32 flops of one world-step of the forward kernel (structured count).
+
+    iters: Newton iterations run; rows: active rows m; groups: contact rows per body
+    group p_g; sep: separator rows s.  Per evaluation 250 m (residual, Jacobian,
+    dynamics); per assembly: group blocks 6 p(p+1), coupling 72 p, separator 12 s(s+1);
+    per factorisation: sum p^3/3 + 6 p^2 + 36 p, plus s^3/3; per solve 2 (sum p^2 + s^2)
+    + 24 sum p, plus 48 m per refinement product."""
+    m = rows
+    ev = 250.0 * m
+    asm = sum(6.0 * p * (p + 1) + 72.0 * p for p in groups) + 12.0 * sep * (sep + 1)
+    fac = sum(p ** 3 / 3.0 + 6.0 * p * p + 36.0 * p for p in groups) + sep ** 3 / 3.0
+    sol = 2.0 * (sum(p * p for p in groups) + sep * sep) + 24.0 * sum(groups)
+    per_iter = asm + fac + (1 + refine) * sol + refine * 48.0 * m + trials_per_iter * ev
+    return iters * per_iter + 2 * ev + asm + fac     # warm-start eval, final eval, taped factor
+
+
+def sample_clocks_start(path):
+    q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+    try:
+        f = open(path, "w")
+        p = subprocess.Popen(["nvidia-smi", f"--query-gpu={q}", "--format=csv,noheader,nounits", "-lms", "200"],
+                             stdout=f, stderr=subprocess.DEVNULL)
+        return p, f
+    except Exception:
+        return None, None
+
+
+def sample_clocks_stop(handle, path, gpu_index):
+    p, f = handle
+    if p is None:
+        return None
+    p.terminate()
+    try:
+        p.wait(timeout=5)
+    except Exception:
+        p.kill()
+    f.close()
+    sms, maxs, reasons = [], [], set()
+    for line in open(path):
+        parts = [x.strip() for x in line.split(",")]
+        if len(parts) < 9 or parts[0] != str(gpu_index):
+            continue
+        try:
+            sms.append(float(parts[1])); maxs.append(float(parts[2]))
+        except ValueError:
+            continue
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for n, v in zip(names, parts[5:9]):
+            if v.lower() == "active":
+                reasons.add(n)
+    if not sms:
+        return None
+    return {"sm_mhz": statistics.median(sms), "sm_max_mhz": max(maxs), "reasons": sorted(reasons), "samples": len(sms)}
+
+
+def measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {}
+
+
+# ---------------------------------------------------------------------------
+# workload
+# ---------------------------------------------------------------------------
+
+def make_inputs(n_worlds, seed=0):
+    scene = S.robot_box_scene()
+    states = S.robot_box_states(scene, n_worlds, seed=seed)
+    knots = S.spline_knots(n_worlds, n_wheels=4, n_knots=8, seed=seed)
+    T = 100
+    B = SP.basis(T, 8, H)                        # [T, K] natural cubic spline, knots over [0, T h]
+    controls = np.einsum("tk,wjk->tjw", B, knots)   # [T, 4, W]
+    # cotangent of the chunk's last state: d/ds of |p_xy - (3, 0)|^2 of the chassis
+    g = np.zeros((scene.n_state, n_worlds))
+    g[0] = 2.0 * (states[0] - 3.0)
+    g[1] = 2.0 * states[1]
+    return scene, states, controls[:CHUNK].astype(np.float32), g
+
+
+class Chunk:
+    """Forward CHUNK steps recording the tape, then CHUNK adjoint steps, on one stream."""
+
+    def __init__(self, ctx, torch, n_worlds):
+        self.ctx, self.torch = ctx, torch
+        dev = "cuda"
+        ns, W = ctx.n_state, ctx.ld
+        f32 = torch.float32
+        self.states = [torch.empty(ns, W, dtype=f32, device=dev) for _ in range(CHUNK + 1)]
+        self.imp = torch.empty(ctx.m_max, W, dtype=f32, device=dev)
+        self.ids = torch.empty(ctx.n_slots, W, dtype=torch.int32, device=dev)
+        self.status = torch.empty(W, dtype=torch.int32, device=dev)
+        self.iters = [torch.empty(W, dtype=torch.int32, device=dev) for _ in range(CHUNK)]
+        self.ids_all = [torch.empty(ctx.n_slots, W, dtype=torch.int32, device=dev) for _ in range(CHUNK)]
+        self.g = [torch.empty(ns, W, dtype=f32, device=dev) for _ in range(CHUNK + 1)]
+        self.dctl = torch.empty(CHUNK, ctx.n_servo, W, dtype=f32, device=dev)
+
+    def run(self, s0, controls, gT, ev_step=None, ev_adj=None, record_ids=False):
+        ctx = self.ctx
+        self.states[0].copy_(s0)
+        for t in range(CHUNK):
+            if ev_step is not None:
+                ev_step[t][0].record()
+            ctx.ostrich_step(self.states[t], controls[t], H, self.states[t + 1], self.imp,
+                             self.ids_all[t] if record_ids else self.ids, self.status, self.iters[t], tape_slot=t)
+            if ev_step is not None:
+                ev_step[t][1].record()
+        self.g[CHUNK].copy_(gT)
+        for t in reversed(range(CHUNK)):
+            if ev_adj is not None:
+                ev_adj[t][0].record()
+            ctx.ostrich_adjoint(t, self.g[t + 1], H, self.g[t], self.dctl[t])
+            if ev_adj is not None:
+                ev_adj[t][1].record()
+
+
+def run_ours(args, rank, world_size, local_rank):
+    import torch
+    from paper_2609_08800_gb300.ostrich import Context
+    torch.cuda.set_device(local_rank)
+    dev = "cuda"
+    W = args.worlds
+    scene, states, controls, g = make_inputs(W, seed=rank)
+    cfg = S.SolverConfig(tol=FP32_TOL)
+    ctx = Context(scene, cfg, W, dtype="f32", tape_slots=CHUNK, threads=args.threads)
+    s0 = torch.tensor(states, dtype=torch.float32, device=dev)
+    ctl = torch.tensor(controls, dtype=torch.float32, device=dev)
+    gT = torch.tensor(g, dtype=torch.float32, device=dev)
+    chunk = Chunk(ctx, torch, W)
+    for _ in range(args.warmup):
+        chunk.run(s0, ctl, gT, record_ids=True)
+    torch.cuda.synchronize()
+    dist_barrier()
+    # live per-launch timing of the two kernels over the timed region
+    evs = [[[torch.cuda.Event(enable_timing=True) for _ in range(2)] for _ in range(CHUNK)] for _ in range(args.steps)]
+    eva = [[[torch.cuda.Event(enable_timing=True) for _ in range(2)] for _ in range(CHUNK)] for _ in range(args.steps)]
+    clk_path = os.path.join(ROOT, "gpurun_out" if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else ".",
+                            f".clocks_rank{rank}.csv")
+    clk = sample_clocks_start(clk_path)
+    start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    start.record()
+    for k in range(args.steps):
+        chunk.run(s0, ctl, gT, evs[k], eva[k])
+    stop.record()
+    torch.cuda.synchronize()
+    clocks = sample_clocks_stop(clk, clk_path, local_rank)
+    ms = start.elapsed_time(stop) / args.steps
+    ms = dist_max(ms)
+    step_ms = [e[0].elapsed_time(e[1]) for k in range(args.steps) for e in evs[k]]
+    adj_ms = [e[0].elapsed_time(e[1]) for k in range(args.steps) for e in eva[k]]
+    # algorithmic flops of the step launches (from the warm-up run: same inputs, same work)
+    iters = np.stack([t.cpu().numpy() for t in chunk.iters])           # [CHUNK, W]
+    ids = np.stack([t.cpu().numpy() for t in chunk.ids_all])           # [CHUNK, slots, W]
+    n_iter = iters & 0xFFFF
+    n_rows = iters >> 16
+    sep = 5 * len(scene.joints) + scene.n_servos
+    flops = 0.0
+    for t in range(CHUNK):
+        for w in range(W):
+            groups = []
+            for b in range(scene.n_bodies):
+                n = scene.slots_of_body(b)
+                if n == 0:
+                    continue
+                base = sum(scene.slots_of_body(bb) for bb in range(b))
+                groups.append(3 * int((ids[t, base:base + n, w] >= 0).sum()))
+            flops += world_flops(int(n_iter[t, w]), int(n_rows[t, w]), groups, sep)
+    flops_per_launch = flops / CHUNK
+    avg_step_ms = statistics.mean(step_ms)
+    achieved = flops_per_launch / (avg_step_ms * 1e-3) / 1e12
+    sm_mhz = (clocks or {}).get("sm_max_mhz") or measured_peaks().get("sm_max_mhz", 2070.0)
+    peak = SM_COUNT_GB300 * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
+    world_steps = W * CHUNK * world_size
+    value = world_steps / (ms * 1e-3)
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world_size, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "robot_over_box_8192_worlds_fp32_fwd_adj_chunk10", "worlds_per_gpu": W,
+                   "steps_per_chunk": CHUNK, "h": H, "newton_budget": cfg.budget,
+                   "parallelism": f"replicas{world_size}",
+                   "l2": f"tape of one chunk {ctx.tape_bytes() * CHUNK / 1e9:.2f} GB > 129 MB L2 (no flush needed)"},
+        "gpu_launches": 2 * CHUNK * args.steps,
+        "kernels": {"step_ms_avg": avg_step_ms, "adjoint_ms_avg": statistics.mean(adj_ms),
+                    "newton_iters_mean": float(n_iter.mean()), "active_rows_mean": float(n_rows.mean())},
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                     "frac": achieved / peak, "traffic": None,
+                     "peak_source": f"152 SMs x 128 FP32 lanes x 2 flop x {sm_mhz:.0f} MHz (SM max clock)",
+                     "kernel": "step_kernel<float>", "flops_per_launch": flops_per_launch},
+    }
+    if clocks:
+        out["clocks"] = clocks
+    if rank == 0 and not args.skip_extras:
+        out["e2e"] = run_e2e(args, ctx, chunk, states, controls, g, torch)
+        out["plain_form"] = run_plain(args, scene, cfg, states, controls, g, torch)
+        out["cpu_baseline"] = run_cpu_baseline(args)
+    ctx.close()
+    return out
+
+
+def run_e2e(args, ctx, chunk, states, controls, g, torch):
+    """Same chunk through the public API with pinned host buffers; copies inside the timing."""
+    W = states.shape[1]
+    hs = torch.tensor(states, dtype=torch.float32).pin_memory()
+    hc = torch.tensor(controls, dtype=torch.float32).pin_memory()
+    hg = torch.tensor(g, dtype=torch.float32).pin_memory()
+    ds0 = torch.empty(ctx.n_state, W, dtype=torch.float32, device="cuda")
+    dc = torch.empty_like(hc, device="cuda")
+    dg = torch.empty_like(hg, device="cuda")
+    out_state = torch.empty(ctx.n_state, W, dtype=torch.float32).pin_memory()
+    out_grad = torch.empty(ctx.n_state, W, dtype=torch.float32).pin_memory()
+    out_dctl = torch.empty(CHUNK, ctx.n_servo, W, dtype=torch.float32).pin_memory()
+
+    def once():
+        ds0.copy_(hs, non_blocking=True)
+        dc.copy_(hc, non_blocking=True)
+        dg.copy_(hg, non_blocking=True)
+        chunk.run(ds0, dc, dg)
+        out_state.copy_(chunk.states[CHUNK], non_blocking=True)
+        out_grad.copy_(chunk.g[0], non_blocking=True)
+        out_dctl.copy_(chunk.dctl, non_blocking=True)
+
+    for _ in range(2):
+        once()
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    n = max(2, args.steps)
+    a.record()
+    for _ in range(n):
+        once()
+    b.record()
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(b) / n
+    h2d = (hs.numel() + hc.numel() + hg.numel()) * 4
+    d2h = (out_state.numel() + out_grad.numel() + out_dctl.numel()) * 4
+    return {"value": W * CHUNK / (ms * 1e-3), "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+            "ms_per_step": ms}
+
+
+def run_plain(args, scene, cfg, states, controls, g, torch):
+    """One world per launch: W = 1 contexts over the same kernels, host loop over worlds."""
+    from paper_2609_08800_gb300.ostrich import Context
+    n = min(args.plain_worlds, states.shape[1])
+    W = states.shape[1]
+    ctx = Context(scene, cfg, 1, dtype="f32", tape_slots=CHUNK, ld=W)
+    s0 = torch.tensor(states, dtype=torch.float32, device="cuda")
+    ctl = torch.tensor(controls, dtype=torch.float32, device="cuda")
+    gT = torch.tensor(g, dtype=torch.float32, device="cuda")
+    st = [torch.empty_like(s0) for _ in range(CHUNK + 1)]
+    gr = [torch.empty_like(s0) for _ in range(CHUNK + 1)]
+    dctl = torch.empty_like(ctl)
+    imp = torch.empty(ctx.m_max, W, dtype=torch.float32, device="cuda")
+    st[0].copy_(s0)
+    gr[CHUNK].copy_(gT)
+    esz = 4
+
+    class P:   # a device address with an element offset
+        def __init__(self, t, off):
+            self.p = t.data_ptr() + off * esz
+
+        def data_ptr(self):
+            return self.p
+
+    def world(w):
+        for t in range(CHUNK):
+            ctx.ostrich_step(P(st[t], w), P(ctl[t], w), H, P(st[t + 1], w), P(imp, w), tape_slot=t)
+        for t in reversed(range(CHUNK)):
+            ctx.ostrich_adjoint(t, P(gr[t + 1], w), H, P(gr[t], w), P(dctl[t], w))
+
+    for w in range(min(8, n)):
+        world(w)
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    for w in range(n):
+        world(w)
+    b.record()
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(b)
+    ctx.close()
+    return {"value": n * CHUNK / (ms * 1e-3), "unit": UNIT, "worlds_timed": n, "launches": 2 * CHUNK * n,
+            "note": "same kernels, one world per launch (W = 1), host loop over worlds"}
+
+
+def run_cpu_baseline(args, impl_line=False):
+    """FP64 oracle on the host: forward + adjoint of a bounded sample of the workload."""
+    from oracle import oracle as O
+    W = args.cpu_worlds
+    scene, states, controls, g = make_inputs(max(W, 1), seed=0)
+    orc = O.Oracle(scene, S.SolverConfig(tol=FP32_TOL))
+    t0 = time.perf_counter()
+    n = 0
+    for w in range(W):
+        s = states[:, w].astype(np.float32).astype(np.float64)
+        traj = [s]
+        for t in range(CHUNK):
+            traj.append(orc.step(traj[-1], controls[t, :, w].astype(np.float64), H)["state"])
+        gg = g[:, w].copy()
+        for t in reversed(range(CHUNK)):
+            gg = orc.step_adjoint(traj[t], controls[t, :, w].astype(np.float64), H, gg)["dstate"]
+        n += CHUNK
+    dt = time.perf_counter() - t0
+    return {"value": n / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{W} worlds x {CHUNK}-step chunk, forward + adjoint (the adjoint call re-solves the step), "
+                      f"single thread, {dt:.1f} s"}
+
+
+# ---------------------------------------------------------------------------
+# distributed helpers (replicas; the only collectives are the timing barrier/max)
+# ---------------------------------------------------------------------------
+_DIST = None
+
+
+def dist_init():
+    global _DIST
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if os.environ.get("OSTRICH_BENCH_GLOO") is None else "gloo")
+        _DIST = dist
+    return int(os.environ.get("RANK", "0")), ws, int(os.environ.get("LOCAL_RANK", "0"))
+
+
+def dist_barrier():
+    if _DIST is not None:
+        _DIST.barrier()
+
+
+def dist_max(x):
+    if _DIST is None:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    _DIST.all_reduce(t, op=_DIST.ReduceOp.MAX)
+    return float(t.item())
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--worlds", type=int, default=8192)
+    ap.add_argument("--threads", type=int, default=64)
+    ap.add_argument("--plain-worlds", type=int, default=512)
+    ap.add_argument("--cpu-worlds", type=int, default=24)
+    ap.add_argument("--skip-extras", action="store_true",
+                    help="time the batched kernels only (no e2e, plain-form or CPU legs); profiling runs")
+    args = ap.parse_args()
+    rank, ws, local_rank = dist_init()
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        times = []
+        for _ in range(args.warmup):
+            run_cpu_baseline(args)
+        for _ in range(args.steps):
+            times.append(run_cpu_baseline(args))
+        v = statistics.median(t["value"] for t in times)
+        line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": 1e3 * args.cpu_worlds * CHUNK / v, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": {"workload": "robot_over_box_8192_worlds_fp32_fwd_adj_chunk10",
+                           "sample_worlds": args.cpu_worlds},
+                "cpu_baseline": dict(times[-1], value=v),
+                "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(line))
+        return
+    out = run_ours(args, rank, ws, local_rank)
+    if rank == 0:
+        print(json.dumps(out))
+    if _DIST is not None:
+        _DIST.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,144 @@
+/*
+ * ostrich.h -- C ABI of libostrich: the per-timestep non-smooth Newton solve of
+ * many independent rigid-body worlds and its implicit-function-theorem adjoint,
+ * for NVIDIA GB300 (sm_103a).
+ *
+ * The problem follows the paper's statement (Sec. III-C, III-D): one step is the
+ * implicit map s+ = s+(s-, a) defined by the stacked residual r(s+, s-, a) = 0 of
+ * Eqs. (9)-(11) (backward-Euler kinematics Eq. (1), implicit dynamics Eq. (2),
+ * joint rows Eq. (3), Fischer-Burmeister normal contact Eq. (4), friction Eq. (7),
+ * implicit velocity servos Eq. (8)); the adjoint maps dL/ds+ to dL/ds- and dL/da
+ * through Eqs. (16)-(19) with the Schur factor of the forward step.
+ *
+ * Layout.  Every state, control, impulse and gradient array is a device pointer
+ * owned by the caller, structure of arrays with the world index fastest: component
+ * c of world w sits at ptr[c * ld + w], ld >= n_worlds (ld is fixed at create).
+ *   state   = [q: 7 per body (p, quaternion w x y z)] [u: 6 per body (v, w_world)]
+ *             [lambda: 5 per joint, 1 per servo, 3 per contact slot]        (n_state)
+ *   controls: one target joint velocity per servo (rad/s)                     (n_servo)
+ *   impulses: h * lambda in the lambda layout, zero on inactive rows          (m_max)
+ *   contact ids: per slot (body << 24 | rim_or_corner << 20 | feature), -1 if inactive
+ * Element type is float for OSTRICH_F32 contexts and double for OSTRICH_F64.
+ *
+ * Errors.  Functions return an ostrich_status and never abort or print; the text of
+ * the last error of a context is available from ostrich_last_error.  Work is queued
+ * asynchronously on the given stream; per-world outcome bits are written to
+ * world_status (1: not converged, best iterate returned; 2: non-finite; 4: contact
+ * overflow).  Calls on one context must not overlap on the device when they use the
+ * same tape slot.
+ */
+#ifndef OSTRICH_H
+#define OSTRICH_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct ostrich_ctx ostrich_ctx;
+
+typedef enum {
+  OSTRICH_OK = 0,
+  OSTRICH_EINVAL = 1,   /* bad argument, size or layout */
+  OSTRICH_ENOMEM = 2,   /* device allocation failed */
+  OSTRICH_ECUDA = 3,    /* a CUDA call failed (see ostrich_last_error) */
+  OSTRICH_ETAPE = 4     /* adjoint on a tape slot that holds no recorded step */
+} ostrich_status;
+
+enum { OSTRICH_F32 = 0, OSTRICH_F64 = 1 };
+enum { OSTRICH_ENV_PLANE = 0, OSTRICH_ENV_BOX = 1, OSTRICH_ENV_HEIGHTMAP = 2 };
+enum { OSTRICH_SHAPE_NONE = 0, OSTRICH_SHAPE_BOX = 1, OSTRICH_SHAPE_WHEEL = 2 };
+enum { OSTRICH_PULLBACK_FULL = 0, OSTRICH_PULLBACK_TRUNCATED = 1 };
+
+#define OSTRICH_MAX_BODIES 8
+#define OSTRICH_MAX_JOINTS 8
+
+/* Rigid body: mass, principal inertia (body frame), collision shape (box corners
+ * or a wheel cylinder whose axle is the body y axis). */
+typedef struct {
+  double mass, inertia[3];
+  int shape;
+  double half_extents[3];
+  double radius, half_width;
+} ostrich_body_desc;
+
+/* Revolute joint (Eq. (3), 3 anchor + 2 axis-alignment rows, no compliance); kp > 0
+ * adds a velocity servo row (Eq. (8), compliance 1/kp). */
+typedef struct {
+  int parent, child;
+  double anchor_parent[3], anchor_child[3];
+  double axis_parent[3], axis_child[3];
+  double perp1_parent[3], perp2_parent[3];
+  double kp;
+} ostrich_joint_desc;
+
+/* Scene shared by all worlds of a context.  heights: host pointer to hm_n*hm_n
+ * FP32 heights (copied at create), or NULL. */
+typedef struct {
+  int n_bodies, n_joints, env;
+  double mu, gravity;
+  double box[5];                 /* obstacle x0, x1, y0, y1, height */
+  int hm_n;
+  double hm_spacing, hm_origin[2];
+  const float* heights;
+  ostrich_body_desc bodies[OSTRICH_MAX_BODIES];
+  ostrich_joint_desc joints[OSTRICH_MAX_JOINTS];
+} ostrich_scene_desc;
+
+/* Solver settings: Newton budget and best-iterate floor (Sec. III-C), stopping
+ * tolerance on sqrt(merit) in m/s, step damping relative to mean diag(h J M^-1 J^T),
+ * contact compliance kappa (s/kg), FB smoothing eps (Sec. III-D), activation margin
+ * (m), line search (0: full steps, 1: backtracking), position pull-back mode. */
+typedef struct {
+  int budget, k_min, line_search, pullback;
+  double tol, delta_rel, kappa, eps_fb, margin;
+} ostrich_solver_cfg;
+
+/* Create a context for n_worlds worlds (arrays strided by ld >= n_worlds), with
+ * tape_slots recorded steps of device workspace (library-owned, freed by destroy).
+ * EINVAL on sizes beyond the caps, ENOMEM if the tape cannot be allocated. */
+ostrich_status ostrich_create(const ostrich_scene_desc* scene, const ostrich_solver_cfg* cfg, int n_worlds, int ld,
+                              int dtype, int tape_slots, ostrich_ctx** out);
+
+/* Layout sizes: out[0] n_state, out[1] m_max, out[2] n_slots, out[3] n_servo. */
+ostrich_status ostrich_layout(const ostrich_ctx* ctx, int32_t out[4]);
+
+/* Threads per world (32, 64 or 128) used by both kernels; the autotuner's knob. */
+ostrich_status ostrich_set_threads(ostrich_ctx* ctx, int threads);
+
+/* One forward step of every world (Sec. III-C): state_in -> state_out, with
+ * h the time step.  impulses_out, contact_ids_out, world_status and iters_out
+ * (per world: Newton iterations | active rows << 16) may be NULL.  tape_slot >= 0
+ * records what the adjoint needs in that slot; -1 records nothing.  state_in and
+ * state_out may not alias. */
+ostrich_status ostrich_step(ostrich_ctx* ctx, const void* state_in, const void* controls, double h, void* state_out,
+                            void* impulses_out, int32_t* contact_ids_out, uint32_t* world_status, int32_t* iters_out,
+                            int tape_slot, void* stream);
+
+/* Adjoint of the step recorded in tape_slot (Sec. III-D): dL/dstate_next (state
+ * layout; lambda entries ignored) -> dL/dstate (lambda entries zero) and
+ * dL/dcontrols (may be NULL).  h must equal the recorded step's.  ETAPE if the slot
+ * holds no step. */
+ostrich_status ostrich_adjoint(ostrich_ctx* ctx, int tape_slot, const void* dL_dstate_next, double h,
+                               void* dL_dstate, void* dL_dcontrols, void* stream);
+
+/* Diagnostic: when merits is a device pointer of n_worlds * (budget + 2) doubles, the
+ * following steps record the merit of the warm start and of every Newton iterate of
+ * each world there; NULL switches it off. */
+ostrich_status ostrich_debug_trace(ostrich_ctx* ctx, double* merits);
+
+/* Mark every tape slot empty (checkpoint recomputation reuses slots). */
+ostrich_status ostrich_tape_clear(ostrich_ctx* ctx);
+
+/* Device bytes of one tape slot (all worlds). */
+size_t ostrich_tape_bytes(const ostrich_ctx* ctx);
+
+const char* ostrich_last_error(const ostrich_ctx* ctx);
+void ostrich_destroy(ostrich_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* OSTRICH_H */

@@ -1,0 +1,218 @@
+// C ABI of libostrich (declared in include/ostrich.h): context, tape memory,
+// argument checks and kernel launches.  Every step of the path runs in the CUDA
+// kernels of ostrich_kernels.cu; this file only validates and dispatches.
+#include <cuda_runtime.h>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "ostrich.h"
+#include "ostrich_scene.h"
+
+namespace ost {
+template <class Real> cudaError_t launch_step(const DevScene&, const StepArgs&, int, cudaStream_t);
+template <class Real> cudaError_t launch_adjoint(const DevScene&, const AdjArgs&, int, cudaStream_t);
+template <class Real> size_t ws_bytes(const DevScene&);
+template <class Real> size_t ws_used(const DevScene&);
+}  // namespace ost
+
+struct ostrich_ctx {
+  ost::DevScene sc;
+  int n_worlds = 0, ld = 0, dtype = 0, tape_slots = 0, threads = 64;
+  size_t tape_world_elems = 0;
+  void* tape = nullptr;
+  float* d_heights = nullptr;
+  std::vector<unsigned char> slot_written;
+  std::vector<double> slot_h;
+  double* trace = nullptr;
+  char err[512] = {0};
+};
+
+static ostrich_status fail(ostrich_ctx* c, ostrich_status s, const char* msg) {
+  if (c) std::snprintf(c->err, sizeof(c->err), "%s", msg);
+  return s;
+}
+
+static ostrich_status cuda_fail(ostrich_ctx* c, cudaError_t e, const char* where) {
+  if (c) std::snprintf(c->err, sizeof(c->err), "%s: %s", where, cudaGetErrorString(e));
+  return OSTRICH_ECUDA;
+}
+
+static size_t elem_size(int dtype) { return dtype == OSTRICH_F64 ? sizeof(double) : sizeof(float); }
+
+extern "C" {
+
+ostrich_status ostrich_create(const ostrich_scene_desc* d, const ostrich_solver_cfg* cfg, int n_worlds, int ld,
+                              int dtype, int tape_slots, ostrich_ctx** out) {
+  if (!out) return OSTRICH_EINVAL;
+  *out = nullptr;
+  if (!d || !cfg) return OSTRICH_EINVAL;
+  ostrich_ctx* c = new (std::nothrow) ostrich_ctx();
+  if (!c) return OSTRICH_ENOMEM;
+  if (n_worlds < 1 || (ld != 0 && ld < n_worlds) || (dtype != OSTRICH_F32 && dtype != OSTRICH_F64) || tape_slots < 0 ||
+      d->n_bodies < 1 || d->n_bodies > ost::NB_CAP || d->n_joints < 0 || d->n_joints > ost::NJ_CAP ||
+      d->env < 0 || d->env > 2 || cfg->budget < 0 || cfg->k_min < 0) {
+    delete c;
+    return OSTRICH_EINVAL;
+  }
+  ost::DevScene& s = c->sc;
+  std::memset(&s, 0, sizeof(s));
+  s.nb = d->n_bodies; s.nj = d->n_joints; s.env = d->env;
+  s.mu = d->mu; s.g = d->gravity;
+  for (int i = 0; i < 5; ++i) s.box[i] = d->box[i];
+  s.hn = d->hm_n; s.hsp = d->hm_spacing; s.hox = d->hm_origin[0]; s.hoy = d->hm_origin[1];
+  s.nf = s.env == ost::ENV_PLANE ? 1 : (s.env == ost::ENV_BOX ? 4 : 8);
+  if (s.env == ost::ENV_HEIGHTMAP) {
+    // terrain contact generation is not part of this build of the library
+    std::snprintf(c->err, sizeof(c->err), "heightmap environment not supported by this library build");
+    ostrich_ctx* keep = c;
+    *out = nullptr;
+    delete keep;
+    return OSTRICH_EINVAL;
+  }
+  int slots = 0;
+  for (int b = 0; b < s.nb; ++b) {
+    const ostrich_body_desc& bd = d->bodies[b];
+    if (!(bd.mass > 0) || !(bd.inertia[0] > 0) || !(bd.inertia[1] > 0) || !(bd.inertia[2] > 0)) { delete c; return OSTRICH_EINVAL; }
+    s.mass[b] = bd.mass;
+    for (int k = 0; k < 3; ++k) { s.inertia[b][k] = bd.inertia[k]; s.half[b][k] = bd.half_extents[k]; }
+    s.radius[b] = bd.radius; s.hw[b] = bd.half_width; s.shape[b] = bd.shape;
+    int cnt = bd.shape == ost::SHAPE_BOX ? 8 : (bd.shape == ost::SHAPE_WHEEL ? 2 * s.nf : 0);
+    s.slot_base[b] = slots; s.slot_count[b] = cnt;
+    for (int k = 0; k < cnt && slots + k < ost::SLOT_CAP; ++k) s.slot_body[slots + k] = (unsigned char)b;
+    slots += cnt;
+  }
+  if (slots > ost::SLOT_CAP) { delete c; return OSTRICH_EINVAL; }
+  s.n_slots = slots;
+  s.n_servo = 0;
+  for (int j = 0; j < s.nj; ++j) {
+    const ostrich_joint_desc& jd = d->joints[j];
+    if (jd.parent < 0 || jd.parent >= s.nb || jd.child < 0 || jd.child >= s.nb || jd.parent == jd.child) { delete c; return OSTRICH_EINVAL; }
+    s.jp[j] = jd.parent; s.jc[j] = jd.child;
+    for (int k = 0; k < 3; ++k) {
+      s.ap[j][k] = jd.anchor_parent[k]; s.ac[j][k] = jd.anchor_child[k];
+      s.axp[j][k] = jd.axis_parent[k]; s.axc[j][k] = jd.axis_child[k];
+      s.p1[j][k] = jd.perp1_parent[k]; s.p2[j][k] = jd.perp2_parent[k];
+    }
+    s.kp[j] = jd.kp;
+    s.servo_of[j] = jd.kp > 0 ? s.n_servo++ : -1;
+  }
+  s.m_max = 5 * s.nj + s.n_servo + 3 * s.n_slots;
+  s.n_state = 13 * s.nb + s.m_max;
+  s.n_groups = 0; s.pg = 0;
+  for (int b = 0; b < s.nb; ++b)
+    if (s.slot_count[b] > 0) {
+      s.group_body[s.n_groups++] = b;
+      if (3 * s.slot_count[b] > s.pg) s.pg = 3 * s.slot_count[b];
+    }
+  s.ss = 5 * s.nj + s.n_servo;
+  s.budget = cfg->budget; s.kmin = cfg->k_min; s.ls = cfg->line_search; s.pullback = cfg->pullback;
+  s.tol = cfg->tol; s.delta_rel = cfg->delta_rel; s.kappa = cfg->kappa; s.eps = cfg->eps_fb; s.margin = cfg->margin;
+  if (s.m_max < 7 * s.nb) { delete c; return OSTRICH_EINVAL; }   // adjoint scratch reuse
+  // FP32 factors lose the small eigenvalues (contact compliance kappa) of the Schur
+  // matrix; two sweeps of refinement against the matrix-free product recover them.
+  s.refine = dtype == OSTRICH_F32 ? 2 : 0;
+  c->n_worlds = n_worlds; c->ld = ld ? ld : n_worlds; c->dtype = dtype; c->tape_slots = tape_slots;
+  size_t smem = dtype == OSTRICH_F64 ? ost::ws_bytes<double>(s) : ost::ws_bytes<float>(s);
+  size_t used = dtype == OSTRICH_F64 ? ost::ws_used<double>(s) : ost::ws_used<float>(s);
+  if (smem > 227 * 1024 || used > smem) { delete c; return OSTRICH_EINVAL; }
+  ost::TapeLayout tl = ost::tape_layout(s);
+  c->tape_world_elems = (size_t)tl.total;
+  if (tape_slots > 0) {
+    size_t bytes = (size_t)tape_slots * (size_t)n_worlds * c->tape_world_elems * elem_size(dtype);
+    cudaError_t e = cudaMalloc(&c->tape, bytes);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      delete c;
+      return OSTRICH_ENOMEM;
+    }
+  }
+  c->slot_written.assign(tape_slots, 0);
+  c->slot_h.assign(tape_slots, 0.0);
+  *out = c;
+  return OSTRICH_OK;
+}
+
+ostrich_status ostrich_layout(const ostrich_ctx* c, int32_t out[4]) {
+  if (!c || !out) return OSTRICH_EINVAL;
+  out[0] = c->sc.n_state; out[1] = c->sc.m_max; out[2] = c->sc.n_slots; out[3] = c->sc.n_servo;
+  return OSTRICH_OK;
+}
+
+ostrich_status ostrich_set_threads(ostrich_ctx* c, int threads) {
+  if (!c) return OSTRICH_EINVAL;
+  if (threads != 32 && threads != 64 && threads != 128) return fail(c, OSTRICH_EINVAL, "threads must be 32, 64 or 128");
+  c->threads = threads;
+  return OSTRICH_OK;
+}
+
+static void* slot_ptr(ostrich_ctx* c, int slot) {
+  return static_cast<char*>(c->tape) + (size_t)slot * c->n_worlds * c->tape_world_elems * elem_size(c->dtype);
+}
+
+ostrich_status ostrich_step(ostrich_ctx* c, const void* state_in, const void* controls, double h, void* state_out,
+                            void* impulses_out, int32_t* ids, uint32_t* status, int32_t* iters, int tape_slot,
+                            void* stream) {
+  if (!c) return OSTRICH_EINVAL;
+  if (!state_in || !state_out || state_in == state_out) return fail(c, OSTRICH_EINVAL, "state_in/state_out missing or aliased");
+  if (c->sc.n_servo > 0 && !controls) return fail(c, OSTRICH_EINVAL, "controls required: the scene has servos");
+  if (!(h > 0)) return fail(c, OSTRICH_EINVAL, "h must be positive");
+  if (tape_slot >= c->tape_slots || tape_slot < -1) return fail(c, OSTRICH_EINVAL, "tape_slot out of range");
+  ost::StepArgs a;
+  a.state_in = state_in; a.controls = controls; a.state_out = state_out; a.impulses = impulses_out;
+  a.ids = ids; a.status = status; a.iters = iters;
+  a.tape = tape_slot >= 0 ? slot_ptr(c, tape_slot) : nullptr;
+  a.ld = c->ld; a.n_worlds = c->n_worlds; a.world0 = 0; a.h = h;
+  a.trace = c->trace;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  cudaError_t e = c->dtype == OSTRICH_F64 ? ost::launch_step<double>(c->sc, a, c->threads, st)
+                                          : ost::launch_step<float>(c->sc, a, c->threads, st);
+  if (e != cudaSuccess) return cuda_fail(c, e, "ostrich_step launch");
+  if (tape_slot >= 0) { c->slot_written[tape_slot] = 1; c->slot_h[tape_slot] = h; }
+  return OSTRICH_OK;
+}
+
+ostrich_status ostrich_adjoint(ostrich_ctx* c, int tape_slot, const void* dL_dnext, double h, void* dL_dstate,
+                               void* dL_dcontrols, void* stream) {
+  if (!c) return OSTRICH_EINVAL;
+  if (tape_slot < 0 || tape_slot >= c->tape_slots) return fail(c, OSTRICH_EINVAL, "tape_slot out of range");
+  if (!c->slot_written[tape_slot]) return fail(c, OSTRICH_ETAPE, "tape slot holds no recorded step");
+  if (h != c->slot_h[tape_slot]) return fail(c, OSTRICH_EINVAL, "h differs from the recorded step");
+  if (!dL_dnext || !dL_dstate) return fail(c, OSTRICH_EINVAL, "gradient pointers missing");
+  ost::AdjArgs a;
+  a.tape = slot_ptr(c, tape_slot); a.dL_dnext = dL_dnext; a.dL_dstate = dL_dstate; a.dL_dcontrols = dL_dcontrols;
+  a.ld = c->ld; a.n_worlds = c->n_worlds; a.world0 = 0; a.h = h;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  cudaError_t e = c->dtype == OSTRICH_F64 ? ost::launch_adjoint<double>(c->sc, a, c->threads, st)
+                                          : ost::launch_adjoint<float>(c->sc, a, c->threads, st);
+  if (e != cudaSuccess) return cuda_fail(c, e, "ostrich_adjoint launch");
+  return OSTRICH_OK;
+}
+
+ostrich_status ostrich_debug_trace(ostrich_ctx* c, double* merits) {
+  if (!c) return OSTRICH_EINVAL;
+  c->trace = merits;
+  return OSTRICH_OK;
+}
+
+ostrich_status ostrich_tape_clear(ostrich_ctx* c) {
+  if (!c) return OSTRICH_EINVAL;
+  for (auto& v : c->slot_written) v = 0;
+  return OSTRICH_OK;
+}
+
+size_t ostrich_tape_bytes(const ostrich_ctx* c) {
+  return c ? (size_t)c->n_worlds * c->tape_world_elems * elem_size(c->dtype) : 0;
+}
+
+const char* ostrich_last_error(const ostrich_ctx* c) { return c ? c->err : "null context"; }
+
+void ostrich_destroy(ostrich_ctx* c) {
+  if (!c) return;
+  if (c->tape) cudaFree(c->tape);
+  if (c->d_heights) cudaFree(c->d_heights);
+  delete c;
+}
+
+}  // extern "C"

@@ -1,0 +1,1269 @@
+// Ostrich per-timestep solve and IFT adjoint for many independent worlds, sm_103a.
+//
+// One CTA runs one world; its whole working set (bodies, constraint rows, contact
+// slots, Schur blocks) lives in shared memory.  The work follows the paper:
+//   Sec. III-A  backward-Euler kinematics Eq. (1), implicit dynamics Eq. (2);
+//   Sec. III-B  joint rows Eq. (3), FB normal contact Eq. (4), friction Eq. (7)
+//               with the two cone safeguards, velocity servo Eq. (8);
+//   Sec. III-C  kinematic substitution, Schur step Eq. (12), back-substitution
+//               Eq. (13), best-iterate backtracking (optional line search);
+//   Sec. III-D  adjoint Eqs. (16)-(19) with the forward Schur factor read back from
+//               the tape, vector-Jacobian products Eq. (17) with the position
+//               pull-back evaluated by forward-mode duals, one row at a time.
+// The Schur matrix A = h J M^-1 J^T + C + delta I is never formed densely: rows are
+// ordered contact rows first, grouped by body (each group touches one body only,
+// so groups do not couple), then the joint/servo rows (the separator).  That block-
+// arrowhead structure is factored as Cholesky of each group block, elimination of
+// the group-separator coupling, then Cholesky of the reduced separator block.
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include "ostrich_scene.h"
+#include "ostrich_math.cuh"
+#include "ostrich_contacts.cuh"
+
+namespace ost {
+
+// ---------------------------------------------------------------------------
+// shared-memory layout of one world
+// ---------------------------------------------------------------------------
+template <class Real> struct WS {
+  // bodies
+  Real *qm, *um, *ubar, *uk, *ut, *ub, *du, *f, *rdyn, *mr, *Iw, *Iwi, *R, *qp;
+  // rows
+  Real *J, *Y, *C, *rhat, *r2, *lk, *lt, *lb, *dl, *rhs;
+  int *meta;      // 4 per row: type | sub << 4, b0, b1 (or -1), lam index (state lambda block)
+  int *ref;       // slot or joint of the row
+  // slots
+  Real *sn, *sd, *st1, *st2, *swhat, *srad, *sedge;
+  int *sact, *srow, *sid, *sftype;
+  // per-body row lists
+  int *bgrp, *bsepn, *bsep;
+  // groups
+  int *g0, *gn;
+  // Schur storage
+  Real *L, *F, *Ls, *Li, *Lsi, *tmp, *tmp2;
+  unsigned char *cpl;
+  // scratch
+  Real *red;
+  int *ints;      // [0] rows, [1] contact rows, [2] items, [3] converged, [4] best_k, [5] iters, [6] status
+  Real *scal;     // [0] merit cur, [1] best merit, [2] delta, [3] merit trial
+};
+
+template <class T> __host__ __device__ __forceinline__ T* carve(char*& p, int n) {
+  size_t a = alignof(T) < 8 ? 8 : alignof(T);
+  uintptr_t q = (reinterpret_cast<uintptr_t>(p) + a - 1) & ~(uintptr_t)(a - 1);
+  T* r = reinterpret_cast<T*>(q);
+  p = reinterpret_cast<char*>(q + sizeof(T) * (size_t)(n > 0 ? n : 1));
+  return r;
+}
+
+template <class Real> __host__ __device__ size_t ws_bytes(const DevScene& s) {
+  // mirrors carve(): every array rounded up to 8 bytes, plus one 8-byte pad each
+  auto sz = [](size_t elem, int n) { return ((elem * (size_t)(n > 0 ? n : 1)) + 15) & ~(size_t)7; };
+  int nb = s.nb, m = s.m_max, ns = s.n_slots > 0 ? s.n_slots : 1, ng = s.n_groups > 0 ? s.n_groups : 1;
+  int ss = s.ss > 0 ? s.ss : 1, pg = s.pg > 0 ? s.pg : 1;
+  size_t b = 0;
+  b += sz(sizeof(Real), 7 * nb) + sz(sizeof(Real), 6 * nb) + sz(sizeof(Real), s.n_servo + 1);
+  b += 8 * sz(sizeof(Real), 6 * nb);                       // uk ut ub du f rdyn mr + spare
+  b += 2 * sz(sizeof(Real), 9 * nb) + sz(sizeof(Real), 9 * nb) + sz(sizeof(Real), 7 * nb);
+  b += 2 * sz(sizeof(Real), 12 * m) + 8 * sz(sizeof(Real), m);
+  b += sz(sizeof(int), 4 * m) + sz(sizeof(int), m);
+  b += 4 * sz(sizeof(Real), 3 * ns) + 2 * sz(sizeof(Real), ns) + sz(sizeof(Real), 2 * ns);
+  b += 4 * sz(sizeof(int), ns);
+  b += sz(sizeof(int), nb) * 2 + sz(sizeof(int), nb * ss);
+  b += 2 * sz(sizeof(int), ng);
+  int lsz = ng * pg * pg > 14 * m ? ng * pg * pg : 14 * m;
+  b += sz(sizeof(Real), lsz) + sz(sizeof(Real), ng * ss * pg) + sz(sizeof(Real), ss * ss);
+  b += sz(sizeof(Real), ng * pg * pg) + sz(sizeof(Real), ss * ss) + 2 * sz(sizeof(Real), m);
+  b += sz(1, ng * ss);
+  b += sz(sizeof(Real), 64) + sz(sizeof(int), 16) + sz(sizeof(Real), 8);
+  b += 256;
+  return b;
+}
+
+template <class Real> __host__ __device__ WS<Real> ws_carve(char* base, const DevScene& s) {
+  WS<Real> w;
+  char* p = base;
+  int nb = s.nb, m = s.m_max, ns = s.n_slots > 0 ? s.n_slots : 1, ng = s.n_groups > 0 ? s.n_groups : 1;
+  int ss = s.ss > 0 ? s.ss : 1, pg = s.pg > 0 ? s.pg : 1;
+  w.qm = carve<Real>(p, 7 * nb); w.um = carve<Real>(p, 6 * nb); w.ubar = carve<Real>(p, s.n_servo + 1);
+  w.uk = carve<Real>(p, 6 * nb); w.ut = carve<Real>(p, 6 * nb); w.ub = carve<Real>(p, 6 * nb);
+  w.du = carve<Real>(p, 6 * nb); w.f = carve<Real>(p, 6 * nb); w.rdyn = carve<Real>(p, 6 * nb);
+  w.mr = carve<Real>(p, 6 * nb); (void)carve<Real>(p, 6 * nb);
+  w.Iw = carve<Real>(p, 9 * nb); w.Iwi = carve<Real>(p, 9 * nb); w.R = carve<Real>(p, 9 * nb);
+  w.qp = carve<Real>(p, 7 * nb);
+  w.J = carve<Real>(p, 12 * m); w.Y = carve<Real>(p, 12 * m);
+  w.C = carve<Real>(p, m); w.rhat = carve<Real>(p, m); w.r2 = carve<Real>(p, m); w.lk = carve<Real>(p, m);
+  w.lt = carve<Real>(p, m); w.lb = carve<Real>(p, m); w.dl = carve<Real>(p, m); w.rhs = carve<Real>(p, m);
+  w.meta = carve<int>(p, 4 * m); w.ref = carve<int>(p, m);
+  w.sn = carve<Real>(p, 3 * ns); w.st1 = carve<Real>(p, 3 * ns); w.st2 = carve<Real>(p, 3 * ns);
+  w.srad = carve<Real>(p, 3 * ns); w.sd = carve<Real>(p, ns); w.swhat = carve<Real>(p, ns);
+  w.sedge = carve<Real>(p, 2 * ns);
+  w.sact = carve<int>(p, ns); w.srow = carve<int>(p, ns); w.sid = carve<int>(p, ns); w.sftype = carve<int>(p, ns);
+  w.bgrp = carve<int>(p, nb); w.bsepn = carve<int>(p, nb); w.bsep = carve<int>(p, nb * ss);
+  w.g0 = carve<int>(p, ng); w.gn = carve<int>(p, ng);
+  int lsz = ng * pg * pg > 14 * m ? ng * pg * pg : 14 * m;     // also holds the adjoint's VJP items
+  w.L = carve<Real>(p, lsz); w.F = carve<Real>(p, ng * ss * pg); w.Ls = carve<Real>(p, ss * ss);
+  w.Li = carve<Real>(p, ng * pg * pg); w.Lsi = carve<Real>(p, ss * ss);
+  w.tmp = carve<Real>(p, m); w.tmp2 = carve<Real>(p, m);
+  w.cpl = carve<unsigned char>(p, ng * ss);
+  w.red = carve<Real>(p, 64); w.ints = carve<int>(p, 16); w.scal = carve<Real>(p, 8);
+  return w;
+}
+
+// deterministic block reduction (fixed tree); result broadcast through w.red[0]
+template <class Real> __device__ Real block_sum(WS<Real>& w, Real v) {
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = (blockDim.x + 31) >> 5;
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  __syncthreads();
+  if (lane == 0) w.red[wid] = v;
+  __syncthreads();
+  if (tid == 0) {
+    Real acc = Real(0);
+    for (int i = 0; i < nw; ++i) acc += w.red[i];
+    w.red[32] = acc;
+  }
+  __syncthreads();
+  return w.red[32];
+}
+
+// ---------------------------------------------------------------------------
+// geometry helpers in any scalar type S
+// ---------------------------------------------------------------------------
+template <class S> __device__ __forceinline__ void tangent_basis(vec3<S> n, vec3<S>& t1, vec3<S>& t2) {
+  vec3<S> e = fabs((double)sval(n.x)) < 0.9 ? v3(S(1), S(0), S(0)) : v3(S(0), S(1), S(0));
+  vec3<S> t = e - scale(n, dot3(n, e));
+  S l = ssqrt(dot3(t, t));
+  t1 = scale(t, S(1) / l);
+  t2 = cross3(n, t1);
+}
+
+// contact point on body b at pose (p, q) for slot kind: box corner (material point) or
+// rim (deepest point of the rim circle along -n)
+template <class S> __device__ __forceinline__ vec3<S> slot_point(const DevScene& sc, int b, int local, vec3<S> p,
+                                                                 const S* q, vec3<S> n) {
+  if (sc.shape[b] == SHAPE_BOX) {
+    int k = local;
+    vec3<S> rb = v3(S((k & 1) ? sc.half[b][0] : -sc.half[b][0]), S((k & 2) ? sc.half[b][1] : -sc.half[b][1]),
+                    S((k & 4) ? sc.half[b][2] : -sc.half[b][2]));
+    return p + qrot(q, rb);
+  }
+  int rim = local / sc.nf;
+  vec3<S> a = qrot(q, v3(S(0), S(1), S(0)));
+  vec3<S> cen = p + qrot(q, v3(S(0), S(rim ? sc.hw[b] : -sc.hw[b]), S(0)));
+  S nd = dot3(n, a);
+  vec3<S> perp = n - scale(a, nd);
+  S pl = ssqrt(dot3(perp, perp));
+  if ((double)sval(pl) <= 1e-12) return cen;
+  return cen - scale(perp, S(sc.radius[b]) / pl);
+}
+
+// frame (n, d) of a slot: fixed plane, or box edge with normal toward the rim centre at q-
+template <class S, class Real> __device__ __forceinline__ void slot_frame2(const DevScene& sc, int b, int local, int ftype,
+                                                                           const S* qm7, const Real* nstore, Real dstore,
+                                                                           const Real* edge, vec3<S>& n, S& d) {
+  if (ftype == 1) {
+    int rim = local / sc.nf;
+    vec3<S> p = v3(qm7[0], qm7[1], qm7[2]);
+    vec3<S> cen = p + qrot(qm7 + 3, v3(S(0), S(rim ? sc.hw[b] : -sc.hw[b]), S(0)));
+    S dx = cen.x - S(edge[0]), dz = cen.z - S(edge[1]);
+    S len = ssqrt(dx * dx + dz * dz);
+    n = v3(dx / len, S(0), dz / len);
+    d = n.x * S(edge[0]) + n.z * S(edge[1]);
+  } else {
+    n = v3(S(nstore[0]), S(nstore[1]), S(nstore[2]));
+    d = S(dstore);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// per-world setup: load inputs, contacts, rows, masses, warm start
+// ---------------------------------------------------------------------------
+// element i of an input vector lives at p[i * stride] (stride = ld for the structure-of-
+// arrays state, 1 for a tape record)
+template <class Real> struct Src { const Real* p; size_t stride; };
+
+template <class Real>
+__device__ void world_setup(const DevScene& sc, WS<Real>& w, Src<Real> qmv, Src<Real> umv, Src<Real> ubarv,
+                            double h) {
+  const int tid = threadIdx.x, nth = blockDim.x;
+  const int nb = sc.nb;
+  for (int i = tid; i < 7 * nb; i += nth) w.qm[i] = qmv.p[i * qmv.stride];
+  for (int i = tid; i < 6 * nb; i += nth) w.um[i] = umv.p[i * umv.stride];
+  for (int i = tid; i < sc.n_servo; i += nth) w.ubar[i] = ubarv.p[i * ubarv.stride];
+  __syncthreads();
+  // contact activation (FP32 predicate) and slot frames in working precision
+  for (int sl = tid; sl < sc.n_slots; sl += nth) {
+    int b = sc.slot_body[sl];
+    int local = sl - sc.slot_base[b];
+    float q7[7], u6[6];
+    for (int k = 0; k < 7; ++k) q7[k] = (float)w.qm[7 * b + k];
+    for (int k = 0; k < 6; ++k) u6[k] = (float)w.um[6 * b + k];
+    SlotAct a = activate_slot(sc, b, local, q7, u6, h);
+    w.sact[sl] = a.active; w.sid[sl] = a.id; w.sftype[sl] = a.ftype;
+    w.sedge[2 * sl] = (Real)a.ex; w.sedge[2 * sl + 1] = (Real)a.ez;
+    vec3<Real> n; Real d;
+    Real ns[3] = {(Real)a.n[0], (Real)a.n[1], (Real)a.n[2]};
+    slot_frame2<Real, Real>(sc, b, local, a.ftype, w.qm + 7 * b, ns, (Real)a.d, w.sedge + 2 * sl, n, d);
+    vec3<Real> t1, t2;
+    tangent_basis(n, t1, t2);
+    w.sn[3 * sl] = n.x; w.sn[3 * sl + 1] = n.y; w.sn[3 * sl + 2] = n.z; w.sd[sl] = d;
+    w.st1[3 * sl] = t1.x; w.st1[3 * sl + 1] = t1.y; w.st1[3 * sl + 2] = t1.z;
+    w.st2[3 * sl] = t2.x; w.st2[3 * sl + 1] = t2.y; w.st2[3 * sl + 2] = t2.z;
+  }
+  // bodies: world inertia at q-, external force, warm-start velocity
+  for (int b = tid; b < nb; b += nth) {
+    Real R[9];
+    qmat(w.qm + 7 * b + 3, R);
+    for (int k = 0; k < 9; ++k) w.R[9 * b + k] = R[k];
+    for (int i = 0; i < 3; ++i)
+      for (int j = 0; j < 3; ++j) {
+        Real a = 0, ai = 0;
+        for (int k = 0; k < 3; ++k) {
+          a += R[3 * i + k] * Real(sc.inertia[b][k]) * R[3 * j + k];
+          ai += R[3 * i + k] * (Real(1) / Real(sc.inertia[b][k])) * R[3 * j + k];
+        }
+        w.Iw[9 * b + 3 * i + j] = a; w.Iwi[9 * b + 3 * i + j] = ai;
+      }
+    Real m = Real(sc.mass[b]);
+    vec3<Real> om = v3(w.um[6 * b + 3], w.um[6 * b + 4], w.um[6 * b + 5]);
+    vec3<Real> Io = mat3<Real>(w.Iw + 9 * b, om);
+    vec3<Real> gy = cross3(om, Io);
+    w.f[6 * b] = 0; w.f[6 * b + 1] = 0; w.f[6 * b + 2] = m * Real(sc.g);
+    w.f[6 * b + 3] = -gy.x; w.f[6 * b + 4] = -gy.y; w.f[6 * b + 5] = -gy.z;
+    vec3<Real> dw = mat3<Real>(w.Iwi + 9 * b, v3(w.f[6 * b + 3], w.f[6 * b + 4], w.f[6 * b + 5]));
+    w.uk[6 * b] = w.um[6 * b];
+    w.uk[6 * b + 1] = w.um[6 * b + 1];
+    w.uk[6 * b + 2] = w.um[6 * b + 2] + Real(h) * Real(sc.g);
+    w.uk[6 * b + 3] = w.um[6 * b + 3] + Real(h) * dw.x;
+    w.uk[6 * b + 4] = w.um[6 * b + 4] + Real(h) * dw.y;
+    w.uk[6 * b + 5] = w.um[6 * b + 5] + Real(h) * dw.z;
+  }
+  __syncthreads();
+  // row compaction (one thread, fixed order): groups of contact rows, then separator
+  if (tid == 0) {
+    int m = 0;
+    for (int g = 0; g < sc.n_groups; ++g) {
+      int b = sc.group_body[g];
+      w.g0[g] = m;
+      for (int sl = sc.slot_base[b]; sl < sc.slot_base[b] + sc.slot_count[b]; ++sl) {
+        if (!w.sact[sl]) { w.srow[sl] = -1; continue; }
+        w.srow[sl] = m;
+        int lam = 5 * sc.nj + sc.n_servo + 3 * sl;
+        for (int k = 0; k < 3; ++k) {
+          int t = k == 0 ? ROW_NORMAL : ROW_FRIC;
+          w.meta[4 * m] = t | (k << 4); w.meta[4 * m + 1] = b; w.meta[4 * m + 2] = -1; w.meta[4 * m + 3] = lam + k;
+          w.ref[m] = sl;
+          ++m;
+        }
+      }
+      w.gn[g] = m - w.g0[g];
+    }
+    int mc = m;
+    for (int j = 0; j < sc.nj; ++j)
+      for (int k = 0; k < 5; ++k) {
+        w.meta[4 * m] = ROW_JOINT | (k << 4); w.meta[4 * m + 1] = sc.jp[j]; w.meta[4 * m + 2] = sc.jc[j];
+        w.meta[4 * m + 3] = 5 * j + k; w.ref[m] = j; ++m;
+      }
+    for (int j = 0; j < sc.nj; ++j) {
+      if (sc.servo_of[j] < 0) continue;
+      w.meta[4 * m] = ROW_SERVO; w.meta[4 * m + 1] = sc.jp[j]; w.meta[4 * m + 2] = sc.jc[j];
+      w.meta[4 * m + 3] = 5 * sc.nj + sc.servo_of[j]; w.ref[m] = j; ++m;
+    }
+    w.ints[0] = m; w.ints[1] = mc;
+    // per-body lists: its group and the separator rows that touch it
+    for (int b = 0; b < nb; ++b) { w.bgrp[b] = -1; w.bsepn[b] = 0; }
+    for (int g = 0; g < sc.n_groups; ++g) w.bgrp[sc.group_body[g]] = g;
+    int ssd = sc.ss > 0 ? sc.ss : 1;
+    for (int i = mc; i < m; ++i) {
+      int b0 = w.meta[4 * i + 1], b1 = w.meta[4 * i + 2];
+      w.bsep[b0 * ssd + w.bsepn[b0]++] = i;
+      if (b1 >= 0) w.bsep[b1 * ssd + w.bsepn[b1]++] = i;
+    }
+  }
+  __syncthreads();
+  // normal-row scaling what = J_n M^-1 J_n^T at q- (geometric Jacobian, E = I)
+  for (int sl = tid; sl < sc.n_slots; sl += nth) {
+    if (!w.sact[sl]) { w.swhat[sl] = 0; continue; }
+    int b = w.meta[4 * w.srow[sl] + 1];
+    int local = sl - sc.slot_base[b];
+    vec3<Real> n = v3(w.sn[3 * sl], w.sn[3 * sl + 1], w.sn[3 * sl + 2]);
+    vec3<Real> p = v3(w.qm[7 * b], w.qm[7 * b + 1], w.qm[7 * b + 2]);
+    vec3<Real> x = slot_point<Real>(sc, b, local, p, w.qm + 7 * b + 3, n);
+    vec3<Real> a = cross3(x - p, n);
+    vec3<Real> ia = mat3<Real>(w.Iwi + 9 * b, a);
+    w.swhat[sl] = Real(1) / Real(sc.mass[b]) + dot3(a, ia);
+  }
+  __syncthreads();
+}
+
+template <class Real> __device__ __forceinline__ void clamp_cone(const DevScene& sc, WS<Real>& w, Real* lam) {
+  // first safeguard of Sec. III-B: |lambda_f| <= mu lambda_n
+  for (int sl = threadIdx.x; sl < sc.n_slots; sl += blockDim.x) {
+    if (!w.sact[sl]) continue;
+    int i = w.srow[sl];
+    Real rad = Real(sc.mu) * (lam[i] > Real(0) ? lam[i] : Real(0));
+    Real nn = ssqrt(lam[i + 1] * lam[i + 1] + lam[i + 2] * lam[i + 2]);
+    if (nn > rad) {
+      Real f = nn > Real(0) ? rad / nn : Real(0);
+      lam[i + 1] *= f; lam[i + 2] *= f;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// one residual / Jacobian evaluation at iterate (u, lam); returns the merit
+// ---------------------------------------------------------------------------
+template <class Real>
+__device__ Real evaluate(const DevScene& sc, WS<Real>& w, const Real* u, const Real* lam, double h) {
+  const int tid = threadIdx.x, nth = blockDim.x;
+  const int nb = sc.nb, m = w.ints[0], mc = w.ints[1];
+  const Real hR = Real(h);
+  // poses at q+ = q- + h G(q-) u
+  for (int b = tid; b < nb; b += nth) {
+    kin_body<Real, Real>(w.qm + 7 * b, u + 6 * b, h, w.qp + 7 * b);
+    qmat(w.qp + 7 * b + 3, w.R + 9 * b);
+  }
+  __syncthreads();
+  const int n_items = sc.n_slots + sc.nj + sc.n_servo;
+  for (int it = tid; it < n_items; it += nth) {
+    if (it < sc.n_slots) {
+      int sl = it;
+      if (!w.sact[sl]) continue;
+      int i = w.srow[sl];
+      int b = w.meta[4 * i + 1];
+      int local = sl - sc.slot_base[b];
+      vec3<Real> p = v3(w.qp[7 * b], w.qp[7 * b + 1], w.qp[7 * b + 2]);
+      vec3<Real> n = v3(w.sn[3 * sl], w.sn[3 * sl + 1], w.sn[3 * sl + 2]);
+      vec3<Real> t1 = v3(w.st1[3 * sl], w.st1[3 * sl + 1], w.st1[3 * sl + 2]);
+      vec3<Real> t2 = v3(w.st2[3 * sl], w.st2[3 * sl + 1], w.st2[3 * sl + 2]);
+      vec3<Real> x = slot_point<Real>(sc, b, local, p, w.qp + 7 * b + 3, n);
+      vec3<Real> lev = x - p;
+      vec3<Real> wk = v3(u[6 * b + 3], u[6 * b + 4], u[6 * b + 5]);
+      vec3<Real> dirs[3] = {n, t1, t2};
+      Real vel[3];
+      const Real mi = Real(1) / Real(sc.mass[b]);
+      for (int k = 0; k < 3; ++k) {
+        vec3<Real> ang = map_Et(cross3(lev, dirs[k]), wk, h);
+        Real* Jr = w.J + 12 * (i + k);
+        Jr[0] = dirs[k].x; Jr[1] = dirs[k].y; Jr[2] = dirs[k].z; Jr[3] = ang.x; Jr[4] = ang.y; Jr[5] = ang.z;
+        for (int q = 6; q < 12; ++q) Jr[q] = 0;
+        Real* Yr = w.Y + 12 * (i + k);
+        Yr[0] = dirs[k].x * mi; Yr[1] = dirs[k].y * mi; Yr[2] = dirs[k].z * mi;
+        vec3<Real> ia = mat3<Real>(w.Iwi + 9 * b, ang);
+        Yr[3] = ia.x; Yr[4] = ia.y; Yr[5] = ia.z;
+        for (int q = 6; q < 12; ++q) Yr[q] = 0;
+        vel[k] = dirs[k].x * u[6 * b] + dirs[k].y * u[6 * b + 1] + dirs[k].z * u[6 * b + 2] + ang.x * u[6 * b + 3] +
+                 ang.y * u[6 * b + 4] + ang.z * u[6 * b + 5];
+      }
+      const Real kap = Real(sc.kappa), eps = Real(sc.eps);
+      const Real hw = hR * w.swhat[sl];
+      // normal row, Eq. (4): phi_eps(c_n/h + kappa lambda_n, h what lambda_n)
+      Real cn = dot3(n, x) - w.sd[sl];
+      Real ln = lam[i], l1 = lam[i + 1], l2 = lam[i + 2];
+      Real a = cn / hR + kap * ln, bb = hw * ln;
+      Real s = ssqrt(a * a + bb * bb + eps * eps);
+      Real phi = a + bb - s, fa = Real(1) - a / s, fb = Real(1) - bb / s;
+      Real scl = fa > Real(1e-12) ? fa : Real(1e-12);
+      w.r2[i] = phi; w.rhat[i] = phi / scl; w.C[i] = kap + hw * fb / scl;
+      // friction rows, Eq. (7): J_f u + (W + kappa) lambda_f with W from the FB reading
+      Real vt = ssqrt(vel[1] * vel[1] + vel[2] * vel[2] + eps * eps);
+      Real lfn = ssqrt(l1 * l1 + l2 * l2 + eps * eps);
+      Real lnp = ln > Real(0) ? ln : Real(0);
+      Real g = hw * (Real(sc.mu) * lnp - lfn);
+      Real sg = ssqrt(vt * vt + g * g + eps * eps);
+      Real phif = vt + g - sg;
+      Real num = vt - phif; if (num < Real(0)) num = Real(0);
+      Real den = Real(sc.mu) * lnp; if (den < Real(1e-12)) den = Real(1e-12);
+      Real W = num / den;
+      Real rf1 = vel[1] + (W + kap) * l1, rf2 = vel[2] + (W + kap) * l2;
+      Real wgt = hw / (hw + W);
+      w.r2[i + 1] = rf1 * wgt; w.r2[i + 2] = rf2 * wgt;
+      w.rhat[i + 1] = rf1; w.rhat[i + 2] = rf2;
+      w.C[i + 1] = W + kap; w.C[i + 2] = W + kap;
+      // radial part of the friction block: rho e e^T, e = lambda_f/|lambda_f|
+      Real rho = Real(0);
+      if (num > Real(0)) {
+        Real fbg = Real(1) - g / sg;
+        rho = fbg * hw * lfn / den;
+      }
+      Real e1 = l1 / lfn, e2 = l2 / lfn;
+      w.srad[3 * sl] = rho * e1 * e1; w.srad[3 * sl + 1] = rho * e1 * e2; w.srad[3 * sl + 2] = rho * e2 * e2;
+    } else if (it < sc.n_slots + sc.nj) {
+      int j = it - sc.n_slots;
+      int i0 = mc + 5 * j;
+      int bp = sc.jp[j], bc = sc.jc[j];
+      vec3<Real> pp = v3(w.qp[7 * bp], w.qp[7 * bp + 1], w.qp[7 * bp + 2]);
+      vec3<Real> pc = v3(w.qp[7 * bc], w.qp[7 * bc + 1], w.qp[7 * bc + 2]);
+      vec3<Real> rp = mat3<Real>(w.R + 9 * bp, v3(Real(sc.ap[j][0]), Real(sc.ap[j][1]), Real(sc.ap[j][2])));
+      vec3<Real> rc = mat3<Real>(w.R + 9 * bc, v3(Real(sc.ac[j][0]), Real(sc.ac[j][1]), Real(sc.ac[j][2])));
+      vec3<Real> wp = v3(u[6 * bp + 3], u[6 * bp + 4], u[6 * bp + 5]);
+      vec3<Real> wc = v3(u[6 * bc + 3], u[6 * bc + 4], u[6 * bc + 5]);
+      vec3<Real> gap = (pp + rp) - (pc + rc);
+      Real gv[3] = {gap.x, gap.y, gap.z};
+      vec3<Real> aw = mat3<Real>(w.R + 9 * bc, v3(Real(sc.axc[j][0]), Real(sc.axc[j][1]), Real(sc.axc[j][2])));
+      for (int k = 0; k < 5; ++k) {
+        vec3<Real> lin_p, ang_p, lin_c, ang_c;
+        Real c;
+        if (k < 3) {
+          vec3<Real> e = v3(Real(k == 0), Real(k == 1), Real(k == 2));
+          lin_p = e; ang_p = cross3(rp, e); lin_c = scale(e, Real(-1)); ang_c = scale(cross3(rc, e), Real(-1));
+          c = gv[k];
+        } else {
+          const double* pb = k == 3 ? sc.p1[j] : sc.p2[j];
+          vec3<Real> bw = mat3<Real>(w.R + 9 * bp, v3(Real(pb[0]), Real(pb[1]), Real(pb[2])));
+          vec3<Real> ba = cross3(bw, aw);
+          lin_p = v3(Real(0), Real(0), Real(0)); lin_c = lin_p;
+          ang_p = ba; ang_c = scale(ba, Real(-1));
+          c = dot3(bw, aw);
+        }
+        ang_p = map_Et(ang_p, wp, h); ang_c = map_Et(ang_c, wc, h);
+        int i = i0 + k;
+        Real* Jr = w.J + 12 * i;
+        Jr[0] = lin_p.x; Jr[1] = lin_p.y; Jr[2] = lin_p.z; Jr[3] = ang_p.x; Jr[4] = ang_p.y; Jr[5] = ang_p.z;
+        Jr[6] = lin_c.x; Jr[7] = lin_c.y; Jr[8] = lin_c.z; Jr[9] = ang_c.x; Jr[10] = ang_c.y; Jr[11] = ang_c.z;
+        Real* Yr = w.Y + 12 * i;
+        Real mip = Real(1) / Real(sc.mass[bp]), mic = Real(1) / Real(sc.mass[bc]);
+        Yr[0] = lin_p.x * mip; Yr[1] = lin_p.y * mip; Yr[2] = lin_p.z * mip;
+        vec3<Real> ia = mat3<Real>(w.Iwi + 9 * bp, ang_p);
+        Yr[3] = ia.x; Yr[4] = ia.y; Yr[5] = ia.z;
+        Yr[6] = lin_c.x * mic; Yr[7] = lin_c.y * mic; Yr[8] = lin_c.z * mic;
+        vec3<Real> ic = mat3<Real>(w.Iwi + 9 * bc, ang_c);
+        Yr[9] = ic.x; Yr[10] = ic.y; Yr[11] = ic.z;
+        w.r2[i] = c / hR; w.rhat[i] = c / hR; w.C[i] = Real(0);
+      }
+    } else {
+      int k = it - sc.n_slots - sc.nj;
+      // k-th servo: find its joint
+      int j = 0, cnt = -1;
+      for (j = 0; j < sc.nj; ++j) if (sc.servo_of[j] >= 0 && ++cnt == k) break;
+      int i = mc + 5 * sc.nj + k;
+      int bp = sc.jp[j], bc = sc.jc[j];
+      vec3<Real> ax = mat3<Real>(w.R + 9 * bp, v3(Real(sc.axp[j][0]), Real(sc.axp[j][1]), Real(sc.axp[j][2])));
+      vec3<Real> wp = v3(u[6 * bp + 3], u[6 * bp + 4], u[6 * bp + 5]);
+      vec3<Real> wc = v3(u[6 * bc + 3], u[6 * bc + 4], u[6 * bc + 5]);
+      vec3<Real> ap_ = map_Et(scale(ax, Real(-1)), wp, h), ac_ = map_Et(ax, wc, h);
+      Real* Jr = w.J + 12 * i;
+      Jr[0] = 0; Jr[1] = 0; Jr[2] = 0; Jr[3] = ap_.x; Jr[4] = ap_.y; Jr[5] = ap_.z;
+      Jr[6] = 0; Jr[7] = 0; Jr[8] = 0; Jr[9] = ac_.x; Jr[10] = ac_.y; Jr[11] = ac_.z;
+      Real* Yr = w.Y + 12 * i;
+      vec3<Real> ia = mat3<Real>(w.Iwi + 9 * bp, ap_), ic = mat3<Real>(w.Iwi + 9 * bc, ac_);
+      Yr[0] = 0; Yr[1] = 0; Yr[2] = 0; Yr[3] = ia.x; Yr[4] = ia.y; Yr[5] = ia.z;
+      Yr[6] = 0; Yr[7] = 0; Yr[8] = 0; Yr[9] = ic.x; Yr[10] = ic.y; Yr[11] = ic.z;
+      Real v = dot3(ap_, wp) + dot3(ac_, wc);
+      Real kp = Real(sc.kp[j]);
+      Real r = v + lam[i] / kp - w.ubar[sc.servo_of[j]];
+      w.r2[i] = r; w.rhat[i] = r; w.C[i] = Real(1) / kp;
+    }
+  }
+  __syncthreads();
+  // Eq. (10): r_dyn = M (u - u-) - h f - h J^T lambda, per body; merit part |M^-1 r_dyn|^2.
+  // The inertia and constraint terms nearly cancel at convergence, so the sum is
+  // accumulated with exact products and exact partial sums (acc2).
+  Real part = Real(0);
+  const int ssd = sc.ss > 0 ? sc.ss : 1;
+  for (int b = tid; b < nb; b += nth) {
+    acc2<Real> rd[6];
+    int g = w.bgrp[b];
+    if (g >= 0)
+      for (int i = w.g0[g]; i < w.g0[g] + w.gn[g]; ++i) {
+        Real hl = -hR * lam[i];
+        for (int k = 0; k < 6; ++k) rd[k].add_prod(w.J[12 * i + k], hl);
+      }
+    for (int t = 0; t < w.bsepn[b]; ++t) {
+      int i = w.bsep[b * ssd + t];
+      int side = w.meta[4 * i + 1] == b ? 0 : 6;
+      Real hl = -hR * lam[i];
+      for (int k = 0; k < 6; ++k) rd[k].add_prod(w.J[12 * i + side + k], hl);
+    }
+    Real m_ = Real(sc.mass[b]);
+    for (int k = 0; k < 3; ++k) {
+      rd[k].add_prod(m_, u[6 * b + k]);
+      rd[k].add_prod(-m_, w.um[6 * b + k]);
+    }
+    for (int r = 0; r < 3; ++r)
+      for (int c = 0; c < 3; ++c) {
+        rd[3 + r].add_prod(w.Iw[9 * b + 3 * r + c], u[6 * b + 3 + c]);
+        rd[3 + r].add_prod(-w.Iw[9 * b + 3 * r + c], w.um[6 * b + 3 + c]);
+      }
+    for (int k = 0; k < 6; ++k) rd[k].add_prod(-hR, w.f[6 * b + k]);
+    Real rv[6];
+    for (int k = 0; k < 6; ++k) { rv[k] = rd[k].value(); w.rdyn[6 * b + k] = rv[k]; }
+    Real mi = Real(1) / m_;
+    vec3<Real> iw = mat3<Real>(w.Iwi + 9 * b, v3(rv[3], rv[4], rv[5]));
+    Real mr[6] = {rv[0] * mi, rv[1] * mi, rv[2] * mi, iw.x, iw.y, iw.z};
+    for (int k = 0; k < 6; ++k) { w.mr[6 * b + k] = mr[k]; part += mr[k] * mr[k]; }
+  }
+  for (int i = tid; i < m; i += nth) part += w.r2[i] * w.r2[i];
+  return block_sum(w, part);
+}
+
+// ---------------------------------------------------------------------------
+// Schur assembly, factorisation and solves
+// ---------------------------------------------------------------------------
+template <class Real> __device__ __forceinline__ Real rowdot(const Real* Ja, int sa, const Real* Yb, int sb) {
+  return Ja[sa] * Yb[sb] + Ja[sa + 1] * Yb[sb + 1] + Ja[sa + 2] * Yb[sb + 2] + Ja[sa + 3] * Yb[sb + 3] +
+         Ja[sa + 4] * Yb[sb + 4] + Ja[sa + 5] * Yb[sb + 5];
+}
+
+template <class Real> __device__ void assemble(const DevScene& sc, WS<Real>& w, double h) {
+  const int tid = threadIdx.x, nth = blockDim.x;
+  const int m = w.ints[0], mc = w.ints[1], pg = sc.pg, ss = sc.ss, ssd = ss > 0 ? ss : 1;
+  const Real hR = Real(h);
+  // delta = delta_rel * mean diag(h J M^-1 J^T)
+  Real part = 0;
+  for (int i = tid; i < m; i += nth) {
+    const Real* Ji = w.J + 12 * i; const Real* Yi = w.Y + 12 * i;
+    part += hR * (rowdot(Ji, 0, Yi, 0) + rowdot(Ji, 6, Yi, 6));
+  }
+  Real tot = block_sum(w, part);
+  const Real delta = m > 0 ? Real(sc.delta_rel) * tot / Real(m) : Real(0);
+  if (tid == 0) w.scal[2] = delta;
+  // group blocks (lower triangle)
+  for (int g = 0; g < sc.n_groups; ++g) {
+    const int r0 = w.g0[g], n = w.gn[g];
+    Real* L = w.L + g * pg * pg;
+    for (int e = tid; e < n * n; e += nth) {
+      int a = e / n, b = e % n;
+      if (b > a) continue;
+      int i = r0 + a, j = r0 + b;
+      Real v = hR * rowdot(w.J + 12 * i, 0, w.Y + 12 * j, 0);
+      if (a == b) v += w.C[i] + delta;
+      // radial friction block of the same slot
+      int ti = w.meta[4 * i] & 15, tj = w.meta[4 * j] & 15;
+      if (ti == ROW_FRIC && tj == ROW_FRIC && w.ref[i] == w.ref[j]) {
+        int si = w.meta[4 * i] >> 4, sj = w.meta[4 * j] >> 4;
+        const Real* rd = w.srad + 3 * w.ref[i];
+        v += (si == 1 && sj == 1) ? rd[0] : ((si == 2 && sj == 2) ? rd[2] : rd[1]);
+      }
+      L[a * pg + b] = v;
+    }
+  }
+  // coupling E_g (separator rows x group rows)
+  for (int g = 0; g < sc.n_groups; ++g) {
+    const int r0 = w.g0[g], n = w.gn[g], bg = sc.group_body[g];
+    Real* F = w.F + g * ssd * pg;
+    for (int e = tid; e < ss * n; e += nth) {
+      int s = e / n, c = e % n;
+      int i = mc + s;
+      int side = w.meta[4 * i + 1] == bg ? 0 : (w.meta[4 * i + 2] == bg ? 6 : -1);
+      F[s * pg + c] = side < 0 ? Real(0) : hR * rowdot(w.J + 12 * i, side, w.Y + 12 * (r0 + c), 0);
+      if (c == 0) w.cpl[g * ssd + s] = side >= 0 ? 1 : 0;
+    }
+  }
+  // separator block
+  for (int e = tid; e < ss * ss; e += nth) {
+    int a = e / ss, b = e % ss;
+    if (b > a) continue;
+    int i = mc + a, j = mc + b;
+    int ia0 = w.meta[4 * i + 1], ia1 = w.meta[4 * i + 2], jb0 = w.meta[4 * j + 1], jb1 = w.meta[4 * j + 2];
+    Real v = 0;
+    if (ia0 == jb0) v += rowdot(w.J + 12 * i, 0, w.Y + 12 * j, 0);
+    if (ia0 == jb1) v += rowdot(w.J + 12 * i, 0, w.Y + 12 * j, 6);
+    if (ia1 >= 0 && ia1 == jb0) v += rowdot(w.J + 12 * i, 6, w.Y + 12 * j, 0);
+    if (ia1 >= 0 && ia1 == jb1) v += rowdot(w.J + 12 * i, 6, w.Y + 12 * j, 6);
+    v *= hR;
+    if (a == b) v += w.C[i] + delta;
+    w.Ls[a * ss + b] = v;
+  }
+  __syncthreads();
+}
+
+// pair (i, j), j <= i, of the e-th entry of a lower triangle stored row by row
+__device__ __forceinline__ void tri_pair(int e, int& i, int& j) {
+  int r = (int)((sqrtf(8.0f * (float)e + 1.0f) - 1.0f) * 0.5f);
+  while ((r + 1) * (r + 2) / 2 <= e) ++r;
+  while (r * (r + 1) / 2 > e) --r;
+  i = r; j = e - r * (r + 1) / 2;
+}
+
+// in-place Cholesky of the lower triangle of an n x n block (row-major, leading dim ld),
+// one warp; the trailing update is spread over the lanes by matrix entry
+template <class Real> __device__ void warp_chol(Real* A, int n, int ld) {
+  const int lane = threadIdx.x & 31;
+  for (int k = 0; k < n; ++k) {
+    Real akk = A[k * ld + k];
+    Real d = ssqrt(akk > Real(0) ? akk : Real(1e-30));
+    Real inv = Real(1) / d;
+    __syncwarp();
+    if (lane == 0) A[k * ld + k] = d;
+    for (int i = k + 1 + lane; i < n; i += 32) A[i * ld + k] *= inv;
+    __syncwarp();
+    const int r = n - k - 1, np = r * (r + 1) / 2;
+    for (int e = lane; e < np; e += 32) {
+      int ii, jj;
+      tri_pair(e, ii, jj);
+      const int i = k + 1 + ii, j = k + 1 + jj;
+      A[i * ld + j] -= A[i * ld + k] * A[j * ld + k];
+    }
+    __syncwarp();
+  }
+}
+
+// X = L^-1 (lower triangular) for an n x n Cholesky factor, one warp, a lane per column
+template <class Real> __device__ void warp_trinv(const Real* L, int n, int ld, Real* X) {
+  const int lane = threadIdx.x & 31;
+  for (int c = lane; c < n; c += 32) {
+    for (int i = 0; i < c; ++i) X[i * ld + c] = Real(0);
+    for (int i = c; i < n; ++i) {
+      Real acc = i == c ? Real(1) : Real(0);
+      for (int l = c; l < i; ++l) acc -= L[i * ld + l] * X[l * ld + c];
+      X[i * ld + c] = acc / L[i * ld + i];
+    }
+  }
+  __syncwarp();
+}
+
+// Block-arrowhead factorisation of A, kept in inverse form for row-parallel solves:
+//   Li_g = L_g^-1 (group blocks), F_g = E_g L_g^-T (coupling), Lsi = L_s^-1 with
+//   L_s L_s^T = S - sum_g F_g F_g^T (reduced separator).
+template <class Real> __device__ void factor(const DevScene& sc, WS<Real>& w) {
+  const int tid = threadIdx.x, nth = blockDim.x, wid = tid >> 5, nw = (blockDim.x + 31) >> 5;
+  const int pg = sc.pg, ss = sc.ss, ssd = ss > 0 ? ss : 1;
+  for (int g = wid; g < sc.n_groups; g += nw) {
+    warp_chol(w.L + g * pg * pg, w.gn[g], pg);
+    warp_trinv(w.L + g * pg * pg, w.gn[g], pg, w.Li + g * pg * pg);
+  }
+  __syncthreads();
+  // F_g[s][j] = sum_{l <= j} E_g[s][l] Li_g[j][l], in place from high j to low j
+  for (int e = tid; e < sc.n_groups * ss; e += nth) {
+    int g = e / ssd, s = e % ssd;
+    if (s >= ss || !w.cpl[g * ssd + s]) continue;
+    const Real* Li = w.Li + g * pg * pg;
+    Real* f = w.F + g * ssd * pg + s * pg;
+    for (int j = w.gn[g] - 1; j >= 0; --j) {
+      Real acc = 0;
+      for (int l = 0; l <= j; ++l) acc += f[l] * Li[j * pg + l];
+      f[j] = acc;
+    }
+  }
+  __syncthreads();
+  // S <- S - sum_g F_g F_g^T
+  for (int e = tid; e < ss * ss; e += nth) {
+    int a = e / ss, b = e % ss;
+    if (b > a) continue;
+    Real acc = 0;
+    for (int g = 0; g < sc.n_groups; ++g) {
+      if (!w.cpl[g * ssd + a] || !w.cpl[g * ssd + b]) continue;
+      const Real* fa = w.F + g * ssd * pg + a * pg;
+      const Real* fb = w.F + g * ssd * pg + b * pg;
+      for (int j = 0; j < w.gn[g]; ++j) acc += fa[j] * fb[j];
+    }
+    w.Ls[a * ss + b] -= acc;
+  }
+  __syncthreads();
+  if (wid == 0 && ss > 0) {
+    warp_chol(w.Ls, ss, ss);
+    warp_trinv(w.Ls, ss, ss, w.Lsi);
+  }
+  __syncthreads();
+}
+
+// v <- A^-1 v with the inverse-form arrowhead factor (row-parallel; scratch tmp, tmp2)
+template <class Real> __device__ void arrow_solve(const DevScene& sc, WS<Real>& w, Real* v) {
+  const int tid = threadIdx.x, nth = blockDim.x;
+  const int pg = sc.pg, ss = sc.ss, ssd = ss > 0 ? ss : 1, mc = w.ints[1], m = w.ints[0];
+  Real* y = w.tmp;
+  Real* z = w.tmp2;
+  // y_g = Li_g b_g
+  for (int r = tid; r < mc; r += nth) {
+    int g = 0;
+    while (g + 1 < sc.n_groups && r >= w.g0[g + 1]) ++g;
+    const int j = r - w.g0[g];
+    const Real* Li = w.Li + g * pg * pg + j * pg;
+    const Real* b = v + w.g0[g];
+    Real acc = 0;
+    for (int l = 0; l <= j; ++l) acc += Li[l] * b[l];
+    y[r] = acc;
+  }
+  __syncthreads();
+  // b_s' = b_s - sum_g F_g y_g
+  for (int s = tid; s < ss; s += nth) {
+    Real acc = v[mc + s];
+    for (int g = 0; g < sc.n_groups; ++g) {
+      if (!w.cpl[g * ssd + s]) continue;
+      const Real* f = w.F + g * ssd * pg + s * pg;
+      for (int j = 0; j < w.gn[g]; ++j) acc -= f[j] * y[w.g0[g] + j];
+    }
+    z[mc + s] = acc;
+  }
+  __syncthreads();
+  // y_s = Lsi b_s'
+  for (int s = tid; s < ss; s += nth) {
+    Real acc = 0;
+    for (int t = 0; t <= s; ++t) acc += w.Lsi[s * ss + t] * z[mc + t];
+    y[mc + s] = acc;
+  }
+  __syncthreads();
+  // x_s = Lsi^T y_s
+  for (int s = tid; s < ss; s += nth) {
+    Real acc = 0;
+    for (int t = s; t < ss; ++t) acc += w.Lsi[t * ss + s] * y[mc + t];
+    v[mc + s] = acc;
+  }
+  __syncthreads();
+  // r_g = y_g - F_g^T x_s
+  for (int r = tid; r < mc; r += nth) {
+    int g = 0;
+    while (g + 1 < sc.n_groups && r >= w.g0[g + 1]) ++g;
+    const int j = r - w.g0[g];
+    Real acc = y[r];
+    for (int s = 0; s < ss; ++s)
+      if (w.cpl[g * ssd + s]) acc -= w.F[g * ssd * pg + s * pg + j] * v[mc + s];
+    z[r] = acc;
+  }
+  __syncthreads();
+  // x_g = Li_g^T r_g
+  for (int r = tid; r < mc; r += nth) {
+    int g = 0;
+    while (g + 1 < sc.n_groups && r >= w.g0[g + 1]) ++g;
+    const int j = r - w.g0[g], n = w.gn[g];
+    const Real* Li = w.Li + g * pg * pg;
+    const Real* zz = z + w.g0[g];
+    Real acc = 0;
+    for (int l = j; l < n; ++l) acc += Li[l * pg + j] * zz[l];
+    v[r] = acc;
+  }
+  __syncthreads();
+  (void)m;
+}
+
+// out_b = sum over rows touching body b of J_row,b^T x_row  (6 per body)
+template <class Real> __device__ void jt_apply(const DevScene& sc, WS<Real>& w, const Real* x, Real* out) {
+  const int ssd = sc.ss > 0 ? sc.ss : 1;
+  for (int b = threadIdx.x; b < sc.nb; b += blockDim.x) {
+    Real jt[6] = {0, 0, 0, 0, 0, 0};
+    int g = w.bgrp[b];
+    if (g >= 0)
+      for (int i = w.g0[g]; i < w.g0[g] + w.gn[g]; ++i)
+        for (int k = 0; k < 6; ++k) jt[k] += w.J[12 * i + k] * x[i];
+    for (int t = 0; t < w.bsepn[b]; ++t) {
+      int i = w.bsep[b * ssd + t];
+      int side = w.meta[4 * i + 1] == b ? 0 : 6;
+      for (int k = 0; k < 6; ++k) jt[k] += w.J[12 * i + side + k] * x[i];
+    }
+    for (int k = 0; k < 6; ++k) out[6 * b + k] = jt[k];
+  }
+}
+
+// compensated variant of jt_apply (exact products, exact partial sums)
+template <class Real> __device__ void jt_apply_acc(const DevScene& sc, WS<Real>& w, const Real* x, Real* out) {
+  const int ssd = sc.ss > 0 ? sc.ss : 1;
+  for (int b = threadIdx.x; b < sc.nb; b += blockDim.x) {
+    acc2<Real> jt[6];
+    int g = w.bgrp[b];
+    if (g >= 0)
+      for (int i = w.g0[g]; i < w.g0[g] + w.gn[g]; ++i)
+        for (int k = 0; k < 6; ++k) jt[k].add_prod(w.J[12 * i + k], x[i]);
+    for (int t = 0; t < w.bsepn[b]; ++t) {
+      int i = w.bsep[b * ssd + t];
+      int side = w.meta[4 * i + 1] == b ? 0 : 6;
+      for (int k = 0; k < 6; ++k) jt[k].add_prod(w.J[12 * i + side + k], x[i]);
+    }
+    for (int k = 0; k < 6; ++k) out[6 * b + k] = jt[k].value();
+  }
+}
+
+// M^-1 v per body (6 per body)
+template <class Real> __device__ __forceinline__ void minv6(const DevScene& sc, const WS<Real>& w, int b, const Real* v,
+                                                            Real* o) {
+  Real mi = Real(1) / Real(sc.mass[b]);
+  o[0] = v[0] * mi; o[1] = v[1] * mi; o[2] = v[2] * mi;
+  vec3<Real> a = mat3<Real>(w.Iwi + 9 * b, v3(v[3], v[4], v[5]));
+  o[3] = a.x; o[4] = a.y; o[5] = a.z;
+}
+
+// Schur solve with iterative refinement: x = A^-1 b with the arrowhead factor, then
+// `sweeps` corrections x += A^-1 (b - A x), where A x = h J (M^-1 J^T x) + (C + delta) x
+// (+ the radial friction blocks) is formed matrix-free from J.  b is kept in `b`,
+// the solution is returned in `x`; t6 (6 per body) and r (rows) are scratch.
+template <class Real>
+__device__ void schur_solve(const DevScene& sc, WS<Real>& w, const Real* b, Real* x, Real* t6, Real* r, double h,
+                            int sweeps) {
+  const int tid = threadIdx.x, nth = blockDim.x, m = w.ints[0];
+  const Real hR = Real(h);
+  for (int i = tid; i < m; i += nth) x[i] = b[i];
+  __syncthreads();
+  arrow_solve(sc, w, x);
+  const Real delta = w.scal[2];
+  for (int sweep = 0; sweep < sweeps; ++sweep) {
+    jt_apply(sc, w, x, t6);
+    __syncthreads();
+    for (int bb = tid; bb < sc.nb; bb += nth) {
+      Real o[6];
+      minv6(sc, w, bb, t6 + 6 * bb, o);
+      for (int k = 0; k < 6; ++k) t6[6 * bb + k] = o[k];
+    }
+    __syncthreads();
+    for (int i = tid; i < m; i += nth) {
+      const Real* Ji = w.J + 12 * i;
+      int b0 = w.meta[4 * i + 1], b1 = w.meta[4 * i + 2];
+      acc2<Real> ax;
+      for (int k = 0; k < 6; ++k) ax.add_prod(Ji[k], t6[6 * b0 + k]);
+      if (b1 >= 0) for (int k = 0; k < 6; ++k) ax.add_prod(Ji[6 + k], t6[6 * b1 + k]);
+      Real v = hR * ax.value() + (w.C[i] + delta) * x[i];
+      int t = w.meta[4 * i] & 15, sub = w.meta[4 * i] >> 4;
+      if (t == ROW_FRIC) {
+        const Real* rd = w.srad + 3 * w.ref[i];
+        v += sub == 1 ? rd[0] * x[i] + rd[1] * x[i + 1] : rd[1] * x[i - 1] + rd[2] * x[i];
+      }
+      r[i] = b[i] - v;
+    }
+    __syncthreads();
+    arrow_solve(sc, w, r);
+    for (int i = tid; i < m; i += nth) x[i] += r[i];
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------------------
+// forward step kernel
+// ---------------------------------------------------------------------------
+template <class Real>
+__global__ void __launch_bounds__(128) step_kernel(const DevScene sc, const StepArgs a) {
+  extern __shared__ __align__(16) char smem[];
+  WS<Real> w = ws_carve<Real>(smem, sc);
+  const int tid = threadIdx.x, nth = blockDim.x;
+  const int world = a.world0 + blockIdx.x;
+  if (world >= a.n_worlds) return;
+  const int ld = a.ld, nb = sc.nb;
+  const Real* sin = reinterpret_cast<const Real*>(a.state_in);
+  const Real* ctl = reinterpret_cast<const Real*>(a.controls);
+  const double h = a.h;
+  // this world's inputs (structure of arrays, world index fastest)
+  Src<Real> sq = {sin + world, (size_t)ld}, su = {sin + (size_t)7 * nb * ld + world, (size_t)ld};
+  Src<Real> sb = {ctl ? ctl + world : sin, ctl ? (size_t)ld : (size_t)0};
+  world_setup<Real>(sc, w, sq, su, sb, h);
+  const int m = w.ints[0];
+  // warm start: lambda from the previous step on the active rows
+  for (int i = tid; i < m; i += nth) w.lk[i] = sin[(size_t)(13 * nb + w.meta[4 * i + 3]) * ld + world];
+  __syncthreads();
+  clamp_cone(sc, w, w.lk);
+  __syncthreads();
+  Real merit = evaluate(sc, w, w.uk, w.lk, h);
+  double* trace = a.trace ? a.trace + (size_t)world * (sc.budget + 2) : nullptr;
+  if (trace && tid == 0) trace[0] = (double)merit;
+  Real best = Real(INFINITY);
+  int best_k = -1, k = 0, conv = 0;
+  const Real tol2 = Real(sc.tol) * Real(sc.tol);
+  const int n_alpha = sc.ls ? 4 : 1;
+  for (k = 0; k < sc.budget; ++k) {
+    if (k >= sc.kmin && merit < best) {
+      best = merit; best_k = k;
+      for (int i = tid; i < 6 * nb; i += nth) w.ub[i] = w.uk[i];
+      for (int i = tid; i < m; i += nth) w.lb[i] = w.lk[i];
+    }
+    if (merit < tol2) { conv = 1; break; }
+    // Schur step, Eq. (12): (h J M^-1 J^T + C + delta) dl = J M^-1 r_dyn - rhat
+    assemble(sc, w, h);
+    factor(sc, w);
+    for (int i = tid; i < m; i += nth) {
+      const Real* Ji = w.J + 12 * i;
+      int b0 = w.meta[4 * i + 1], b1 = w.meta[4 * i + 2];
+      acc2<Real> jm;
+      for (int q = 0; q < 6; ++q) jm.add_prod(Ji[q], w.mr[6 * b0 + q]);
+      if (b1 >= 0) for (int q = 0; q < 6; ++q) jm.add_prod(Ji[6 + q], w.mr[6 * b1 + q]);
+      jm.add(-w.rhat[i]);
+      w.rhs[i] = jm.value();
+    }
+    __syncthreads();
+    schur_solve(sc, w, w.rhs, w.dl, w.du, w.lt, h, sc.refine);
+    // Eq. (13): du = M^-1 (h J^T dl - r_dyn)
+    jt_apply(sc, w, w.dl, w.du);
+    __syncthreads();
+    for (int b = tid; b < nb; b += nth) {
+      Real t[6];
+      for (int q = 0; q < 6; ++q) t[q] = Real(h) * w.du[6 * b + q] - w.rdyn[6 * b + q];
+      minv6(sc, w, b, t, w.du + 6 * b);
+    }
+    __syncthreads();
+    // step control: full step (Sec. III-C) or backtracking on the merit
+    Real alpha = Real(1), mt = merit;
+    for (int ai = 0; ai < n_alpha; ++ai) {
+      if (ai > 0) alpha *= Real(0.5);
+      for (int i = tid; i < 6 * nb; i += nth) w.ut[i] = w.uk[i] + alpha * w.du[i];
+      for (int i = tid; i < m; i += nth) w.lt[i] = w.lk[i] + alpha * w.dl[i];
+      __syncthreads();
+      clamp_cone(sc, w, w.lt);
+      __syncthreads();
+      mt = evaluate(sc, w, w.ut, w.lt, h);
+      if (mt < merit) break;
+    }
+    for (int i = tid; i < 6 * nb; i += nth) w.uk[i] = w.ut[i];
+    for (int i = tid; i < m; i += nth) w.lk[i] = w.lt[i];
+    merit = mt;
+    if (trace && tid == 0) trace[k + 1] = (double)merit;
+    __syncthreads();
+  }
+  uint32_t status = 0;
+  if (!conv) {
+    if (k >= sc.kmin && merit < best) { best = merit; best_k = k; }
+    else if (best_k >= 0) {
+      for (int i = tid; i < 6 * nb; i += nth) w.uk[i] = w.ub[i];
+      for (int i = tid; i < m; i += nth) w.lk[i] = w.lb[i];
+      merit = best;
+    }
+    status |= 1u;
+  }
+  __syncthreads();
+  // the returned iterate: its Jacobian, compliance and Schur factor go to the tape
+  Real mret = evaluate(sc, w, w.uk, w.lk, h);
+  if (!(mret == mret) || !(fabs((double)mret) < 1e300)) status |= 2u;
+  const TapeLayout tl = tape_layout(sc);
+  const bool record = a.tape != nullptr;
+  if (record) {
+    assemble(sc, w, h);
+    factor(sc, w);
+    Real* tp = reinterpret_cast<Real*>(a.tape) + (size_t)world * tl.total;
+    for (int i = tid; i < 7 * nb; i += nth) tp[tl.off_qm + i] = w.qm[i];
+    for (int i = tid; i < 6 * nb; i += nth) { tp[tl.off_um + i] = w.um[i]; tp[tl.off_u + i] = w.uk[i]; }
+    for (int i = tid; i < sc.n_servo; i += nth) tp[tl.off_ubar + i] = w.ubar[i];
+    for (int i = tid; i < sc.m_max; i += nth) tp[tl.off_lam + i] = Real(0);
+    __syncthreads();
+    for (int i = tid; i < m; i += nth) tp[tl.off_lam + w.meta[4 * i + 3]] = w.lk[i];
+    const int pg = sc.pg, ssd = sc.ss > 0 ? sc.ss : 1;
+    for (int i = tid; i < sc.n_groups * pg * pg; i += nth) tp[tl.off_leaf + i] = w.Li[i];
+    for (int i = tid; i < sc.n_groups * ssd * pg; i += nth) tp[tl.off_cpl + i] = w.F[i];
+    for (int i = tid; i < sc.ss * sc.ss; i += nth) tp[tl.off_sep + i] = w.Lsi[i];
+  }
+  // outputs: q+ (normalised quaternions), u+, lambda+, impulses h lambda, contact ids
+  Real* so = reinterpret_cast<Real*>(a.state_out);
+  Real* imp = reinterpret_cast<Real*>(a.impulses);
+  for (int b = tid; b < nb; b += nth) {
+    Real qp[7];
+    kin_body<Real, Real>(w.qm + 7 * b, w.uk + 6 * b, h, qp);
+    Real nq = ssqrt(qp[3] * qp[3] + qp[4] * qp[4] + qp[5] * qp[5] + qp[6] * qp[6]);
+    for (int c = 3; c < 7; ++c) qp[c] /= nq;
+    for (int c = 0; c < 7; ++c) so[(size_t)(7 * b + c) * ld + world] = qp[c];
+    for (int c = 0; c < 6; ++c) so[(size_t)(7 * nb + 6 * b + c) * ld + world] = w.uk[6 * b + c];
+  }
+  for (int i = tid; i < sc.m_max; i += nth) {
+    so[(size_t)(13 * nb + i) * ld + world] = Real(0);
+    if (imp) imp[(size_t)i * ld + world] = Real(0);
+  }
+  __syncthreads();
+  for (int i = tid; i < m; i += nth) {
+    int li = w.meta[4 * i + 3];
+    so[(size_t)(13 * nb + li) * ld + world] = w.lk[i];
+    if (imp) imp[(size_t)li * ld + world] = Real(h) * w.lk[i];
+  }
+  if (a.ids)
+    for (int sl = tid; sl < sc.n_slots; sl += nth) a.ids[(size_t)sl * ld + world] = w.sact[sl] ? w.sid[sl] : -1;
+  if (tid == 0) {
+    if (a.status) a.status[world] = status;
+    if (a.iters) a.iters[world] = k | (m << 16);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// adjoint kernel
+// ---------------------------------------------------------------------------
+// Scalar Psi_row(q-) of the VJP of Eq. (17) for one constraint row, differentiated along
+// one coordinate (body db, component dc) of q-:  w_row * rlin_row - h lambda_row J_row . w_u.
+template <class Real>
+__device__ Real row_vjp(const DevScene& sc, const WS<Real>& w, int i, int db, int dc, const Real* wl, const Real* wu,
+                        bool trunc, double h) {
+  typedef dual<Real> D;
+  const int type = w.meta[4 * i] & 15, sub = w.meta[4 * i] >> 4;
+  const int b0 = w.meta[4 * i + 1], b1 = w.meta[4 * i + 2];
+  const Real hR = Real(h);
+  // q- (dual) and q+ (dual) of the row's bodies
+  D qm0[7], qp0[7], qm1[7], qp1[7];
+  for (int c = 0; c < 7; ++c) qm0[c] = D(w.qm[7 * b0 + c], (b0 == db && c == dc) ? Real(1) : Real(0));
+  kin_body<D, Real>(qm0, w.uk + 6 * b0, h, qp0);
+  if (b1 >= 0) {
+    for (int c = 0; c < 7; ++c) qm1[c] = D(w.qm[7 * b1 + c], (b1 == db && c == dc) ? Real(1) : Real(0));
+    kin_body<D, Real>(qm1, w.uk + 6 * b1, h, qp1);
+  }
+  vec3<Real> wk0 = v3(w.uk[6 * b0 + 3], w.uk[6 * b0 + 4], w.uk[6 * b0 + 5]);
+  vec3<Real> wu0l = v3(wu[6 * b0], wu[6 * b0 + 1], wu[6 * b0 + 2]), wu0a = v3(wu[6 * b0 + 3], wu[6 * b0 + 4], wu[6 * b0 + 5]);
+  const Real lam = w.lk[i];
+  D out(Real(0));
+  if (type == ROW_NORMAL || type == ROW_FRIC) {
+    const int sl = w.ref[i];
+    const int local = sl - sc.slot_base[b0];
+    vec3<D> p = v3(qp0[0], qp0[1], qp0[2]);
+    if (trunc) {
+      if (type == ROW_FRIC) return Real(0);
+      // material point and frame frozen at the converged state; first-order rigid motion
+      vec3<Real> n = v3(w.sn[3 * sl], w.sn[3 * sl + 1], w.sn[3 * sl + 2]);
+      Real qpv[7];
+      for (int c = 0; c < 7; ++c) qpv[c] = qp0[c].v;
+      vec3<Real> pv = v3(qpv[0], qpv[1], qpv[2]);
+      vec3<Real> xs = slot_point<Real>(sc, b0, local, pv, qpv + 3, n);
+      Real Rs[9];
+      qmat(qpv + 3, Rs);
+      vec3<Real> rho = mat3T<Real>(Rs, xs - pv);
+      vec3<D> x = p + qrot(qp0 + 3, lift<D>(rho));
+      D c = dot3(lift<D>(n), x) - D(w.sd[sl]);
+      return (wl[i] * c / D(hR)).d;
+    }
+    vec3<D> n; D d;
+    Real ns[3] = {w.sn[3 * sl], w.sn[3 * sl + 1], w.sn[3 * sl + 2]};
+    slot_frame2<D, Real>(sc, b0, local, w.sftype[sl], qm0, ns, w.sd[sl], w.sedge + 2 * sl, n, d);
+    vec3<D> x = slot_point<D>(sc, b0, local, p, qp0 + 3, n);
+    vec3<D> lev = x - p;
+    vec3<D> dir = n;
+    if (type == ROW_FRIC) {
+      vec3<D> t1, t2;
+      tangent_basis(n, t1, t2);
+      dir = sub == 1 ? t1 : t2;
+    }
+    vec3<D> ang = map_Et(cross3(lev, dir), wk0, h);
+    vec3<Real> ul = v3(w.uk[6 * b0], w.uk[6 * b0 + 1], w.uk[6 * b0 + 2]);
+    D Jw = dot3(dir, lift<D>(wu0l)) + dot3(ang, lift<D>(wu0a));
+    D rlin;
+    if (type == ROW_NORMAL) rlin = (dot3(n, x) - d) / D(hR);
+    else rlin = dot3(dir, lift<D>(ul)) + dot3(ang, lift<D>(wk0));
+    out = D(wl[i]) * rlin - D(hR * lam) * Jw;
+    return out.d;
+  }
+  // joint and servo rows (two bodies)
+  const int j = w.ref[i];
+  vec3<Real> wk1 = v3(w.uk[6 * b1 + 3], w.uk[6 * b1 + 4], w.uk[6 * b1 + 5]);
+  vec3<Real> wu1l = v3(wu[6 * b1], wu[6 * b1 + 1], wu[6 * b1 + 2]), wu1a = v3(wu[6 * b1 + 3], wu[6 * b1 + 4], wu[6 * b1 + 5]);
+  if (type == ROW_SERVO) {
+    vec3<D> ax = qrot(qp0 + 3, v3(D(sc.axp[j][0]), D(sc.axp[j][1]), D(sc.axp[j][2])));
+    vec3<D> a0 = map_Et(scale(ax, D(Real(-1))), wk0, h), a1 = map_Et(ax, wk1, h);
+    D v = dot3(a0, lift<D>(wk0)) + dot3(a1, lift<D>(wk1));
+    D Jw = dot3(a0, lift<D>(wu0a)) + dot3(a1, lift<D>(wu1a));
+    out = D(wl[i]) * v - D(hR * lam) * Jw;
+    return out.d;
+  }
+  vec3<D> pp = v3(qp0[0], qp0[1], qp0[2]), pc = v3(qp1[0], qp1[1], qp1[2]);
+  vec3<D> rp = qrot(qp0 + 3, v3(D(sc.ap[j][0]), D(sc.ap[j][1]), D(sc.ap[j][2])));
+  vec3<D> rc = qrot(qp1 + 3, v3(D(sc.ac[j][0]), D(sc.ac[j][1]), D(sc.ac[j][2])));
+  vec3<D> lin_p, ang_p, lin_c, ang_c;
+  D c;
+  if (sub < 3) {
+    vec3<D> e = v3(D(Real(sub == 0)), D(Real(sub == 1)), D(Real(sub == 2)));
+    vec3<D> gap = (pp + rp) - (pc + rc);
+    c = sub == 0 ? gap.x : (sub == 1 ? gap.y : gap.z);
+    lin_p = e; ang_p = cross3(rp, e); lin_c = scale(e, D(Real(-1))); ang_c = scale(cross3(rc, e), D(Real(-1)));
+  } else {
+    const double* pb = sub == 3 ? sc.p1[j] : sc.p2[j];
+    vec3<D> bw = qrot(qp0 + 3, v3(D(pb[0]), D(pb[1]), D(pb[2])));
+    vec3<D> aw = qrot(qp1 + 3, v3(D(sc.axc[j][0]), D(sc.axc[j][1]), D(sc.axc[j][2])));
+    vec3<D> ba = cross3(bw, aw);
+    c = dot3(bw, aw);
+    lin_p = v3(D(Real(0)), D(Real(0)), D(Real(0))); lin_c = lin_p;
+    ang_p = ba; ang_c = scale(ba, D(Real(-1)));
+  }
+  ang_p = map_Et(ang_p, wk0, h); ang_c = map_Et(ang_c, wk1, h);
+  D Jw = dot3(lin_p, lift<D>(wu0l)) + dot3(ang_p, lift<D>(wu0a)) + dot3(lin_c, lift<D>(wu1l)) + dot3(ang_c, lift<D>(wu1a));
+  out = D(wl[i]) * c / D(hR) - D(hR * lam) * Jw;
+  return out.d;
+}
+
+// Body part of Psi: g_q . q+(q-) + w_u . (M(q-)(u* - u-) - h f(q-, u-)), along (b, dc).
+template <class Real>
+__device__ Real body_vjp(const DevScene& sc, const WS<Real>& w, int b, int dc, const Real* gq, const Real* wu, double h) {
+  typedef dual<Real> D;
+  D qm[7], qp[7];
+  for (int c = 0; c < 7; ++c) qm[c] = D(w.qm[7 * b + c], c == dc ? Real(1) : Real(0));
+  kin_body<D, Real>(qm, w.uk + 6 * b, h, qp);
+  D acc(Real(0));
+  for (int c = 0; c < 7; ++c) acc = acc + D(gq[7 * b + c]) * qp[c];
+  // angular part depends on q- through I_w(q-) = R diag(I) R^T
+  vec3<D> dw = v3(D(w.uk[6 * b + 3] - w.um[6 * b + 3]), D(w.uk[6 * b + 4] - w.um[6 * b + 4]), D(w.uk[6 * b + 5] - w.um[6 * b + 5]));
+  vec3<D> om = v3(D(w.um[6 * b + 3]), D(w.um[6 * b + 4]), D(w.um[6 * b + 5]));
+  auto Iw_apply = [&](vec3<D> v) {
+    vec3<D> vb = v3(D(Real(0)), D(Real(0)), D(Real(0)));
+    // R^T v via rotating by the conjugate quaternion
+    D qc[4] = {qm[3], D(Real(0)) - qm[4], D(Real(0)) - qm[5], D(Real(0)) - qm[6]};
+    vb = qrot(qc, v);
+    vb = v3(vb.x * D(Real(sc.inertia[b][0])), vb.y * D(Real(sc.inertia[b][1])), vb.z * D(Real(sc.inertia[b][2])));
+    return qrot(qm + 3, vb);
+  };
+  vec3<D> Idw = Iw_apply(dw);
+  vec3<D> gy = cross3(om, Iw_apply(om));        // f_ang = -gy
+  vec3<D> ra = Idw + scale(gy, D(Real(h)));     // angular r_dyn minus the lambda terms
+  acc = acc + D(wu[6 * b + 3]) * ra.x + D(wu[6 * b + 4]) * ra.y + D(wu[6 * b + 5]) * ra.z;
+  return acc.d;
+}
+
+template <class Real>
+__global__ void __launch_bounds__(128) adjoint_kernel(const DevScene sc, const AdjArgs a) {
+  extern __shared__ __align__(16) char smem[];
+  WS<Real> w = ws_carve<Real>(smem, sc);
+  const int tid = threadIdx.x, nth = blockDim.x;
+  const int world = a.world0 + blockIdx.x;
+  if (world >= a.n_worlds) return;
+  const int ld = a.ld, nb = sc.nb;
+  const double h = a.h;
+  const Real hR = Real(h);
+  const TapeLayout tl = tape_layout(sc);
+  const Real* tp = reinterpret_cast<const Real*>(a.tape) + (size_t)world * tl.total;
+  Src<Real> sq = {tp + tl.off_qm, 1}, su = {tp + tl.off_um, 1}, sb = {tp + tl.off_ubar, 1};
+  world_setup<Real>(sc, w, sq, su, sb, h);
+  const int m = w.ints[0], mc = w.ints[1];
+  for (int i = tid; i < 6 * nb; i += nth) w.uk[i] = tp[tl.off_u + i];
+  for (int i = tid; i < m; i += nth) w.lk[i] = tp[tl.off_lam + w.meta[4 * i + 3]];
+  __syncthreads();
+  evaluate(sc, w, w.uk, w.lk, h);      // J (with E at u*), poses at q+
+  // factor from the tape
+  const int pg = sc.pg, ssd = sc.ss > 0 ? sc.ss : 1;
+  for (int i = tid; i < sc.n_groups * pg * pg; i += nth) w.Li[i] = tp[tl.off_leaf + i];
+  for (int i = tid; i < sc.n_groups * ssd * pg; i += nth) w.F[i] = tp[tl.off_cpl + i];
+  for (int i = tid; i < sc.ss * sc.ss; i += nth) w.Lsi[i] = tp[tl.off_sep + i];
+  // coupling flags are a function of the row structure only
+  for (int e = tid; e < sc.n_groups * ssd; e += nth) {
+    int g = e / ssd, s = e % ssd;
+    int bg = sc.group_body[g];
+    int i = mc + s;
+    w.cpl[e] = (s < sc.ss) && (w.meta[4 * i + 1] == bg || w.meta[4 * i + 2] == bg);
+  }
+  // incoming cotangent: normalisation Jacobian of the output quaternions, then g
+  Real* gq = w.lb;      // the best-iterate buffer is free in the adjoint; m_max >= 7 nb
+  Real* gu = w.du;
+  const Real* din = reinterpret_cast<const Real*>(a.dL_dnext);
+  for (int b = tid; b < nb; b += nth) {
+    Real qp[7];
+    kin_body<Real, Real>(w.qm + 7 * b, w.uk + 6 * b, h, qp);
+    Real nq = ssqrt(qp[3] * qp[3] + qp[4] * qp[4] + qp[5] * qp[5] + qp[6] * qp[6]);
+    Real qh[4] = {qp[3] / nq, qp[4] / nq, qp[5] / nq, qp[6] / nq};
+    Real gin[4];
+    for (int c = 0; c < 4; ++c) gin[c] = din[(size_t)(7 * b + 3 + c) * ld + world];
+    Real dp = qh[0] * gin[0] + qh[1] * gin[1] + qh[2] * gin[2] + qh[3] * gin[3];
+    for (int c = 0; c < 3; ++c) gq[7 * b + c] = din[(size_t)(7 * b + c) * ld + world];
+    for (int c = 0; c < 4; ++c) gq[7 * b + 3 + c] = (gin[c] - qh[c] * dp) / nq;
+    for (int c = 0; c < 6; ++c) gu[6 * b + c] = din[(size_t)(7 * nb + 6 * b + c) * ld + world];
+    // g = grad_u L + h G(q-)^T grad_q L; G^T for the quaternion block is 1/2 vec(g (x) q-*)
+    const Real* q = w.qm + 7 * b + 3;
+    const Real* g4 = gq + 7 * b + 3;
+    Real vx = -g4[0] * q[1] + g4[1] * q[0] - g4[2] * q[3] + g4[3] * q[2];
+    Real vy = -g4[0] * q[2] + g4[1] * q[3] + g4[2] * q[0] - g4[3] * q[1];
+    Real vz = -g4[0] * q[3] - g4[1] * q[2] + g4[2] * q[1] + g4[3] * q[0];
+    gu[6 * b] += hR * gq[7 * b]; gu[6 * b + 1] += hR * gq[7 * b + 1]; gu[6 * b + 2] += hR * gq[7 * b + 2];
+    gu[6 * b + 3] += hR * Real(0.5) * vx; gu[6 * b + 4] += hR * Real(0.5) * vy; gu[6 * b + 5] += hR * Real(0.5) * vz;
+    Real mg[6];
+    minv6(sc, w, b, gu + 6 * b, mg);
+    for (int c = 0; c < 6; ++c) w.mr[6 * b + c] = mg[c];
+  }
+  __syncthreads();
+  // Eq. (18): A w_lambda = -h J M^-1 g, with the forward factor (delta recomputed as
+  // in the forward assembly for the refinement's matrix-free product)
+  Real* wl = w.dl;
+  {
+    Real part = 0;
+    for (int i = tid; i < m; i += nth) {
+      const Real* Ji = w.J + 12 * i; const Real* Yi = w.Y + 12 * i;
+      part += hR * (rowdot(Ji, 0, Yi, 0) + rowdot(Ji, 6, Yi, 6));
+    }
+    Real tot = block_sum(w, part);
+    if (tid == 0) w.scal[2] = m > 0 ? Real(sc.delta_rel) * tot / Real(m) : Real(0);
+  }
+  // the right-hand side is formed with exact products: its rounding would otherwise
+  // reach the null space of J^T, where A's eigenvalue is only kappa
+  for (int i = tid; i < m; i += nth) {
+    const Real* Ji = w.J + 12 * i;
+    int b0 = w.meta[4 * i + 1], b1 = w.meta[4 * i + 2];
+    acc2<Real> jm;
+    for (int k = 0; k < 6; ++k) jm.add_prod(Ji[k], w.mr[6 * b0 + k]);
+    if (b1 >= 0) for (int k = 0; k < 6; ++k) jm.add_prod(Ji[6 + k], w.mr[6 * b1 + k]);
+    w.rhs[i] = -hR * jm.value();
+  }
+  __syncthreads();
+  schur_solve(sc, w, w.rhs, wl, w.f, w.lt, h, 2 * sc.refine);
+  // Eq. (19): w_u = -M^-1 (g + J^T w_lambda)
+  Real* wu = w.ub;
+  jt_apply_acc(sc, w, wl, w.f);     // f is free now
+  __syncthreads();
+  for (int b = tid; b < nb; b += nth) {
+    Real t[6], o[6];
+    for (int c = 0; c < 6; ++c) t[c] = gu[6 * b + c] + w.f[6 * b + c];
+    minv6(sc, w, b, t, o);
+    for (int c = 0; c < 6; ++c) wu[6 * b + c] = -o[c];
+  }
+  __syncthreads();
+  // dL/du- = -M w_u - h (df/du-)^T w_u ;  dL/dubar = -w_lambda of the servo rows
+  Real* dout = reinterpret_cast<Real*>(a.dL_dstate);
+  for (int b = tid; b < nb; b += nth) {
+    Real mb = Real(sc.mass[b]);
+    for (int c = 0; c < 3; ++c) dout[(size_t)(7 * nb + 6 * b + c) * ld + world] = -mb * wu[6 * b + c];
+    vec3<Real> wa = v3(wu[6 * b + 3], wu[6 * b + 4], wu[6 * b + 5]);
+    vec3<Real> om = v3(w.um[6 * b + 3], w.um[6 * b + 4], w.um[6 * b + 5]);
+    vec3<Real> Iwa = mat3<Real>(w.Iw + 9 * b, wa);
+    vec3<Real> t1 = mat3<Real>(w.Iw + 9 * b, cross3(om, wa));
+    vec3<Real> t2 = cross3(mat3<Real>(w.Iw + 9 * b, om), wa);
+    vec3<Real> d = v3(-Iwa.x - hR * (t1.x - t2.x), -Iwa.y - hR * (t1.y - t2.y), -Iwa.z - hR * (t1.z - t2.z));
+    dout[(size_t)(7 * nb + 6 * b + 3) * ld + world] = d.x;
+    dout[(size_t)(7 * nb + 6 * b + 4) * ld + world] = d.y;
+    dout[(size_t)(7 * nb + 6 * b + 5) * ld + world] = d.z;
+  }
+  for (int i = tid; i < sc.m_max; i += nth) dout[(size_t)(13 * nb + i) * ld + world] = Real(0);
+  Real* dctl = reinterpret_cast<Real*>(a.dL_dcontrols);
+  if (dctl)
+    for (int i = mc + 5 * sc.nj + tid; i < m; i += nth) dctl[(size_t)(i - mc - 5 * sc.nj) * ld + world] = -wl[i];
+  // dL/dq-: per-row and per-body dual-number derivatives, summed in a fixed order
+  const bool trunc = sc.pullback == 1;
+  Real* item = w.L;     // factor no longer needed: m * 14 row items + nb * 7 body items
+  for (int e = tid; e < m * 14; e += nth) {
+    int i = e / 14, r = e % 14, side = r / 7, c = r % 7;
+    int b = side == 0 ? w.meta[4 * i + 1] : w.meta[4 * i + 2];
+    item[e] = b >= 0 ? row_vjp(sc, w, i, b, c, wl, wu, trunc, h) : Real(0);
+  }
+  Real* bitem = w.rhs;  // nb * 7 <= m_max is checked when the context is created
+  for (int e = tid; e < nb * 7; e += nth) bitem[e] = body_vjp(sc, w, e / 7, e % 7, gq, wu, h);
+  __syncthreads();
+  const int ssdd = ssd;
+  for (int e = tid; e < nb * 7; e += nth) {
+    int b = e / 7, c = e % 7;
+    acc2<Real> acc;        // the terms cancel strongly: compensated sum
+    acc.add(bitem[e]);
+    int g = w.bgrp[b];
+    if (g >= 0)
+      for (int i = w.g0[g]; i < w.g0[g] + w.gn[g]; ++i) acc.add(item[i * 14 + c]);
+    for (int t = 0; t < w.bsepn[b]; ++t) {
+      int i = w.bsep[b * ssdd + t];
+      int side = w.meta[4 * i + 1] == b ? 0 : 1;
+      acc.add(item[i * 14 + 7 * side + c]);
+    }
+    dout[(size_t)(7 * b + c) * ld + world] = acc.value();
+  }
+}
+
+// ---------------------------------------------------------------------------
+// launchers (called by the C ABI)
+// ---------------------------------------------------------------------------
+template <class Real>
+cudaError_t launch_step(const DevScene& sc, const StepArgs& a, int threads, cudaStream_t st) {
+  size_t smem = ws_bytes<Real>(sc);
+  cudaError_t e = cudaFuncSetAttribute(step_kernel<Real>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  int n = a.n_worlds - a.world0;
+  if (n <= 0) return cudaSuccess;
+  step_kernel<Real><<<n, threads, smem, st>>>(sc, a);
+  return cudaGetLastError();
+}
+
+template <class Real>
+cudaError_t launch_adjoint(const DevScene& sc, const AdjArgs& a, int threads, cudaStream_t st) {
+  size_t smem = ws_bytes<Real>(sc);
+  cudaError_t e = cudaFuncSetAttribute(adjoint_kernel<Real>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  int n = a.n_worlds - a.world0;
+  if (n <= 0) return cudaSuccess;
+  adjoint_kernel<Real><<<n, threads, smem, st>>>(sc, a);
+  return cudaGetLastError();
+}
+
+template cudaError_t launch_step<float>(const DevScene&, const StepArgs&, int, cudaStream_t);
+template cudaError_t launch_step<double>(const DevScene&, const StepArgs&, int, cudaStream_t);
+template cudaError_t launch_adjoint<float>(const DevScene&, const AdjArgs&, int, cudaStream_t);
+template cudaError_t launch_adjoint<double>(const DevScene&, const AdjArgs&, int, cudaStream_t);
+template size_t ws_bytes<float>(const DevScene&);
+template size_t ws_bytes<double>(const DevScene&);
+
+// Bytes the carve of one world actually consumes from a 16-byte aligned base; the
+// context refuses a scene for which this exceeds ws_bytes (checked on the host).
+template <class Real> size_t ws_used(const DevScene& s) {
+  alignas(16) static char probe[16];
+  char* base = probe;
+  WS<Real> w = ws_carve<Real>(base, s);
+  return (size_t)(reinterpret_cast<char*>(w.scal + 8) - base);
+}
+template size_t ws_used<float>(const DevScene&);
+template size_t ws_used<double>(const DevScene&);
+
+}  // namespace ost

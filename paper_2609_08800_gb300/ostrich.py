@@ -1,0 +1,217 @@
+"""Thin Python binding of libostrich (include/ostrich.h).
+
+Argument marshalling only: every step of the solve and the adjoint runs in the
+CUDA kernels of the shared library.  PyTorch supplies device memory and the
+stream.  If the library is missing or a call fails, an exception is raised; there
+is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import scenes as S
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libostrich.so")
+
+OSTRICH_OK, OSTRICH_EINVAL, OSTRICH_ENOMEM, OSTRICH_ECUDA, OSTRICH_ETAPE = 0, 1, 2, 3, 4
+OSTRICH_F32, OSTRICH_F64 = 0, 1
+MAX_BODIES = 8
+MAX_JOINTS = 8
+
+_d3 = ctypes.c_double * 3
+
+
+class BodyDesc(ctypes.Structure):
+    _fields_ = [("mass", ctypes.c_double), ("inertia", _d3), ("shape", ctypes.c_int), ("half_extents", _d3),
+                ("radius", ctypes.c_double), ("half_width", ctypes.c_double)]
+
+
+class JointDesc(ctypes.Structure):
+    _fields_ = [("parent", ctypes.c_int), ("child", ctypes.c_int), ("anchor_parent", _d3), ("anchor_child", _d3),
+                ("axis_parent", _d3), ("axis_child", _d3), ("perp1_parent", _d3), ("perp2_parent", _d3),
+                ("kp", ctypes.c_double)]
+
+
+class SceneDesc(ctypes.Structure):
+    _fields_ = [("n_bodies", ctypes.c_int), ("n_joints", ctypes.c_int), ("env", ctypes.c_int),
+                ("mu", ctypes.c_double), ("gravity", ctypes.c_double), ("box", ctypes.c_double * 5),
+                ("hm_n", ctypes.c_int), ("hm_spacing", ctypes.c_double), ("hm_origin", ctypes.c_double * 2),
+                ("heights", ctypes.POINTER(ctypes.c_float)),
+                ("bodies", BodyDesc * MAX_BODIES), ("joints", JointDesc * MAX_JOINTS)]
+
+
+class SolverCfg(ctypes.Structure):
+    _fields_ = [("budget", ctypes.c_int), ("k_min", ctypes.c_int), ("line_search", ctypes.c_int),
+                ("pullback", ctypes.c_int), ("tol", ctypes.c_double), ("delta_rel", ctypes.c_double),
+                ("kappa", ctypes.c_double), ("eps_fb", ctypes.c_double), ("margin", ctypes.c_double)]
+
+
+_vp = ctypes.c_void_p
+_lib = None
+
+
+def lib():
+    """Load libostrich (built in-tree by ``build()``); raises if it is missing."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"libostrich is not built ({LIB_PATH} missing); run __graft_entry__.build()")
+        L = ctypes.CDLL(LIB_PATH)
+        L.ostrich_create.argtypes = [ctypes.POINTER(SceneDesc), ctypes.POINTER(SolverCfg), ctypes.c_int, ctypes.c_int,
+                                     ctypes.c_int, ctypes.c_int, ctypes.POINTER(_vp)]
+        L.ostrich_create.restype = ctypes.c_int
+        L.ostrich_layout.argtypes = [_vp, ctypes.POINTER(ctypes.c_int32)]
+        L.ostrich_set_threads.argtypes = [_vp, ctypes.c_int]
+        L.ostrich_step.argtypes = [_vp, _vp, _vp, ctypes.c_double, _vp, _vp, _vp, _vp, _vp, ctypes.c_int, _vp]
+        L.ostrich_adjoint.argtypes = [_vp, ctypes.c_int, _vp, ctypes.c_double, _vp, _vp, _vp]
+        L.ostrich_tape_clear.argtypes = [_vp]
+        L.ostrich_debug_trace.argtypes = [_vp, _vp]
+        L.ostrich_debug_trace.restype = ctypes.c_int
+        L.ostrich_tape_bytes.argtypes = [_vp]
+        L.ostrich_tape_bytes.restype = ctypes.c_size_t
+        L.ostrich_last_error.argtypes = [_vp]
+        L.ostrich_last_error.restype = ctypes.c_char_p
+        L.ostrich_destroy.argtypes = [_vp]
+        for name in ("ostrich_layout", "ostrich_set_threads", "ostrich_step", "ostrich_adjoint", "ostrich_tape_clear"):
+            getattr(L, name).restype = ctypes.c_int
+        _lib = L
+    return _lib
+
+
+def scene_desc(scene: "S.Scene") -> SceneDesc:
+    d = SceneDesc()
+    d.n_bodies, d.n_joints, d.env = scene.n_bodies, len(scene.joints), scene.env.kind
+    d.mu, d.gravity = scene.mu, scene.gravity
+    for i, v in enumerate(scene.env.box):
+        d.box[i] = v
+    if scene.env.heights is not None:
+        d.hm_n = scene.env.heights.shape[0]
+        d.hm_spacing = scene.env.spacing
+        d.hm_origin[0], d.hm_origin[1] = scene.env.origin
+    for i, b in enumerate(scene.bodies):
+        bd = d.bodies[i]
+        bd.mass = b.mass
+        bd.inertia[:] = b.inertia
+        bd.shape = b.shape
+        bd.half_extents[:] = b.half_extents
+        bd.radius, bd.half_width = b.radius, b.half_width
+    for i, j in enumerate(scene.joints):
+        jd = d.joints[i]
+        jd.parent, jd.child = j.parent, j.child
+        jd.anchor_parent[:] = j.anchor_parent
+        jd.anchor_child[:] = j.anchor_child
+        jd.axis_parent[:] = j.axis_parent
+        jd.axis_child[:] = j.axis_child
+        jd.perp1_parent[:] = j.perp_parent[0]
+        jd.perp2_parent[:] = j.perp_parent[1]
+        jd.kp = j.kp
+    return d
+
+
+def solver_cfg(cfg: "S.SolverConfig") -> SolverCfg:
+    c = SolverCfg()
+    c.budget, c.k_min, c.line_search, c.pullback = cfg.budget, cfg.k_min, cfg.line_search, cfg.pullback
+    c.tol, c.delta_rel, c.kappa, c.eps_fb, c.margin = cfg.tol, cfg.delta_rel, cfg.kappa, cfg.eps_fb, cfg.margin
+    return c
+
+
+def _ptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+class Context:
+    """One ostrich_ctx: a scene, a solver configuration, W worlds and a tape."""
+
+    def __init__(self, scene, cfg, n_worlds, dtype="f32", tape_slots=1, ld=0, threads=None):
+        import torch
+        self.scene, self.cfg = scene, cfg
+        self.n_worlds = int(n_worlds)
+        self.dtype = torch.float64 if dtype in ("f64", torch.float64) else torch.float32
+        self._desc, self._cfg = scene_desc(scene), solver_cfg(cfg)
+        h = _vp()
+        rc = lib().ostrich_create(ctypes.byref(self._desc), ctypes.byref(self._cfg), self.n_worlds, int(ld),
+                                  OSTRICH_F64 if self.dtype == torch.float64 else OSTRICH_F32, int(tape_slots),
+                                  ctypes.byref(h))
+        if rc != OSTRICH_OK:
+            raise RuntimeError(f"ostrich_create failed with status {rc}")
+        self._h = h
+        self.ld = int(ld) if ld else self.n_worlds
+        out = (ctypes.c_int32 * 4)()
+        lib().ostrich_layout(self._h, out)
+        self.n_state, self.m_max, self.n_slots, self.n_servo = map(int, out)
+        self.tape_slots = int(tape_slots)
+        if threads is not None:
+            self.set_threads(threads)
+
+    def _check(self, rc, what):
+        if rc != OSTRICH_OK:
+            msg = lib().ostrich_last_error(self._h).decode()
+            raise RuntimeError(f"{what} failed with status {rc}: {msg}")
+
+    def set_threads(self, threads):
+        self._check(lib().ostrich_set_threads(self._h, int(threads)), "ostrich_set_threads")
+
+    def ostrich_step(self, state_in, controls, h, state_out, impulses=None, ids=None, status=None, iters=None,
+                     tape_slot=-1, stream=None):
+        self._check(lib().ostrich_step(self._h, _ptr(state_in), _ptr(controls), float(h), _ptr(state_out),
+                                       _ptr(impulses), _ptr(ids), _ptr(status), _ptr(iters), int(tape_slot),
+                                       _stream(stream)), "ostrich_step")
+
+    def ostrich_adjoint(self, tape_slot, dL_dnext, h, dL_dstate, dL_dcontrols=None, stream=None):
+        self._check(lib().ostrich_adjoint(self._h, int(tape_slot), _ptr(dL_dnext), float(h), _ptr(dL_dstate),
+                                          _ptr(dL_dcontrols), _stream(stream)), "ostrich_adjoint")
+
+    def ostrich_debug_trace(self, merits):
+        self._check(lib().ostrich_debug_trace(self._h, _ptr(merits)), "ostrich_debug_trace")
+
+    def ostrich_tape_clear(self):
+        self._check(lib().ostrich_tape_clear(self._h), "ostrich_tape_clear")
+
+    def tape_bytes(self):
+        return int(lib().ostrich_tape_bytes(self._h))
+
+    # convenience wrappers that allocate outputs (torch tensors [rows, ld])
+    def alloc_state(self):
+        import torch
+        return torch.zeros(self.n_state, self.ld, dtype=self.dtype, device="cuda")
+
+    def step(self, state_in, controls, h, tape_slot=-1, stream=None):
+        import torch
+        dev = state_in.device
+        out = torch.empty(self.n_state, self.ld, dtype=self.dtype, device=dev)
+        imp = torch.empty(self.m_max, self.ld, dtype=self.dtype, device=dev)
+        ids = torch.empty(max(self.n_slots, 1), self.ld, dtype=torch.int32, device=dev)
+        st = torch.empty(self.ld, dtype=torch.int32, device=dev)
+        it = torch.empty(self.ld, dtype=torch.int32, device=dev)
+        self.ostrich_step(state_in, controls, h, out, imp, ids, st, it, tape_slot, stream)
+        return dict(state=out, impulses=imp, ids=ids[:self.n_slots], status=st, iters=it)
+
+    def adjoint(self, tape_slot, dL_dnext, h, stream=None):
+        import torch
+        dev = dL_dnext.device
+        ds = torch.empty(self.n_state, self.ld, dtype=self.dtype, device=dev)
+        du = torch.empty(max(self.n_servo, 1), self.ld, dtype=self.dtype, device=dev)
+        self.ostrich_adjoint(tape_slot, dL_dnext, h, ds, du, stream)
+        return ds, du[:self.n_servo]
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().ostrich_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,172 @@
+"""CUDA path against the FP64 oracle, one step at a time from identical inputs.
+
+Tolerances: contact index sets bit-exact; FP64 path 1e-9 relative; FP32 path
+positions/velocities within 1e-4 of max(|x|, 1) per world, impulses within 1e-3 of
+the step's largest impulse, adjoint gradients within 1e-3 of the largest oracle
+gradient entry of the world.
+
+The oracle runs to a tight tolerance (the exact step).  A world is compared on
+values when the oracle converged and the CUDA path's returned iterate is a solution:
+its exact residual, evaluated by the oracle's residual function at that iterate, is
+below the FP32 floor of the scene (3e-4 m/s; FP32 states rounded from the exact
+solution already sit near 1e-5, and the FP32 Newton iteration stalls around 1e-4).
+Every world is compared on its contact index set.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from oracle import oracle as O  # noqa: E402
+from paper_2609_08800_gb300 import scenes as S  # noqa: E402
+
+
+@pytest.fixture(scope="module")
+def ostrich():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_2609_08800_gb300 import ostrich as M
+    M.lib()
+    return M
+
+
+def _run_gpu(M, scene, cfg, states, controls, h, dtype, grads=None):
+    W = states.shape[1]
+    tdt = torch.float64 if dtype == "f64" else torch.float32
+    ctx = M.Context(scene, cfg, W, dtype=dtype, tape_slots=1)
+    s_in = torch.tensor(states, dtype=tdt, device="cuda")
+    u_in = torch.tensor(controls if controls.size else np.zeros((1, W)), dtype=tdt, device="cuda")
+    r = ctx.step(s_in, u_in, h, tape_slot=0)
+    out = {k: v.cpu() for k, v in r.items()}
+    if grads is not None:
+        g = torch.tensor(grads, dtype=tdt, device="cuda")
+        ds, du = ctx.adjoint(0, g, h)
+        out["dstate"], out["dubar"] = ds.cpu(), du.cpu()
+    torch.cuda.synchronize()
+    out["s_in"] = s_in.double().cpu().numpy()
+    out["u_in"] = u_in.double().cpu().numpy()
+    ctx.close()
+    return out
+
+
+def _exact_residual(orc, scene, s_in, ub, h, out_state):
+    """sqrt(merit) of the oracle's residual function at a given iterate (u, lambda)."""
+    nb = scene.n_bodies
+    u = out_state[7 * nb:13 * nb]
+    lam = out_state[13 * nb:]
+    rows = orc.rows(s_in, ub, h, u, lam)
+    rd = rows["rdyn"].reshape(nb, 6)
+    tot = float((rows["r"] ** 2).sum())
+    for b in range(nb):
+        R = S._quat_to_matrix(s_in[7 * b + 3:7 * b + 7])
+        Iwi = R @ np.diag(1.0 / np.array(scene.bodies[b].inertia)) @ R.T
+        mr = np.r_[rd[b, :3] / scene.bodies[b].mass, Iwi @ rd[b, 3:]]
+        tot += float(mr @ mr)
+    return np.sqrt(tot)
+
+
+def _compare(scene, cfg, g, states, controls, h, dtype, tol_state, tol_imp, tol_grad, min_frac, grads=None,
+             oracle_cfg=None, floor=None):
+    orc = O.Oracle(scene, oracle_cfg or cfg)
+    orc_cfg_run = O.Oracle(scene, cfg)
+    W = states.shape[1]
+    r = _run_gpu(g, scene, cfg, states, controls, h, dtype, grads)
+    nb = scene.n_bodies
+    n_cmp = 0
+    for w in range(W):
+        ub = r["u_in"][:scene.n_servos, w] if scene.n_servos else np.zeros(1)
+        if grads is None:
+            ro = orc.step(r["s_in"][:, w], ub, h)
+        else:
+            ro = orc.step_adjoint(r["s_in"][:, w], ub, h, grads[:, w].astype(np.float64) if dtype == "f64"
+                                  else grads[:, w].astype(np.float32).astype(np.float64))
+        ids = r["ids"][:, w].numpy()
+        assert np.array_equal(ro["ids"], ids), f"world {w}: contact index set"
+        gs = int(r["status"][w]) & 3
+        if ro["status"] != 0 or (gs & 2):
+            continue
+        if floor is None:
+            if gs != 0:
+                continue
+        else:
+            res = _exact_residual(orc_cfg_run, scene, r["s_in"][:, w], ub, h, r["state"][:, w].double().numpy())
+            if res > floor:
+                continue
+        n_cmp += 1
+        x_g = r["state"][:13 * nb, w].double().numpy()
+        x_o = ro["state"][:13 * nb]
+        err = np.abs(x_g - x_o).max()
+        assert err <= tol_state * max(np.abs(x_o).max(), 1.0), f"world {w}: state err {err}"
+        imp_o = ro["impulses"]
+        imp_g = r["impulses"][:, w].double().numpy()
+        e_imp = np.abs(imp_g - imp_o).max()
+        assert e_imp <= tol_imp * max(np.abs(imp_o).max(), 1e-12), f"world {w}: impulse err {e_imp} of {np.abs(imp_o).max()}"
+        if grads is not None:
+            dg = r["dstate"][:13 * nb, w].double().numpy()
+            do = ro["dstate"][:13 * nb]
+            e_g = np.abs(dg - do).max()
+            assert e_g <= tol_grad * np.abs(do).max(), f"world {w}: grad err {e_g} of {np.abs(do).max()}"
+            if scene.n_servos:
+                du_g = r["dubar"][:, w].double().numpy()
+                e_u = np.abs(du_g - ro["dubar"]).max()
+                assert e_u <= tol_grad * max(np.abs(do).max(), np.abs(ro["dubar"]).max()), f"world {w}: control grad err {e_u}"
+    print(f"compared {n_cmp}/{W} worlds on values")
+    assert n_cmp >= min_frac * W, f"only {n_cmp}/{W} worlds compared"
+    return n_cmp
+
+
+def _box_states(n, seed=0):
+    sc = S.box_drop_scene()
+    rng = np.random.default_rng(seed)
+    st = np.zeros((sc.n_state, n))
+    for w in range(n):
+        st[:, w] = S.box_drop_state(sc, rng.uniform(0, 1))[:, 0]
+        st[2, w] += rng.uniform(-0.06, 0.02)
+        st[8, w] = rng.uniform(-0.3, 0.3)
+        ang = rng.uniform(-0.2, 0.2)
+        st[3:7, w] = (np.cos(ang / 2), 0.0, 0.0, np.sin(ang / 2))
+    return sc, st
+
+
+def test_box_fp64_matches_oracle(ostrich):
+    sc, st = _box_states(37)
+    cfg = S.SolverConfig(budget=50, k_min=4, tol=1e-10, kappa=0.0)
+    g = np.random.default_rng(1).normal(size=st.shape)
+    g[13:] = 0
+    _compare(sc, cfg, ostrich, st, np.zeros((0, 37)), 0.1, "f64", 1e-9, 1e-7, 1e-6, 0.8, grads=g)
+
+
+def test_box_fp32_matches_oracle(ostrich):
+    sc, st = _box_states(45, seed=2)
+    cfg = S.SolverConfig(budget=30, k_min=4, tol=1e-5, kappa=1e-4)
+    g = np.random.default_rng(3).normal(size=st.shape)
+    g[13:] = 0
+    _compare(sc, cfg, ostrich, st, np.zeros((0, 45)), 0.1, "f32", 1e-4, 1e-3, 1e-3, 0.9, grads=g,
+             oracle_cfg=S.SolverConfig(budget=60, k_min=4, tol=1e-9, kappa=1e-4), floor=3e-4)
+
+
+@pytest.mark.parametrize("seed", [0, 1])
+def test_robot_box_fp32_matches_oracle(ostrich, seed):
+    sc = S.robot_box_scene()
+    W = 67
+    st = S.robot_box_states(sc, W, seed=seed)
+    ub = S.random_controls(sc.n_servos, W, seed=seed, low=-3, high=3)
+    cfg = S.SolverConfig()
+    g = np.random.default_rng(seed + 10).normal(size=st.shape)
+    g[13 * sc.n_bodies:] = 0
+    _compare(sc, cfg, ostrich, st, ub, 0.1, "f32", 1e-4, 1e-3, 1e-3, 0.85, grads=g,
+             oracle_cfg=S.SolverConfig(budget=60, tol=1e-8), floor=3e-4)
+
+
+def test_robot_box_fp64_matches_oracle(ostrich):
+    """The FP64 build of the same kernels against the oracle on the robot: the
+    implementation itself, free of FP32 effects."""
+    sc = S.robot_box_scene()
+    W = 33
+    st = S.robot_box_states(sc, W, seed=5)
+    ub = S.random_controls(sc.n_servos, W, seed=5, low=-3, high=3)
+    cfg = S.SolverConfig(budget=40, tol=1e-9)
+    g = np.random.default_rng(15).normal(size=st.shape)
+    g[13 * sc.n_bodies:] = 0
+    _compare(sc, cfg, ostrich, st, ub, 0.1, "f64", 1e-7, 1e-6, 1e-6, 0.8, grads=g)

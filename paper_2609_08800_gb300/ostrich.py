@@ -76,7 +76,10 @@ def lib():
         L.ostrich_last_error.argtypes = [_vp]
         L.ostrich_last_error.restype = ctypes.c_char_p
         L.ostrich_destroy.argtypes = [_vp]
-        for name in ("ostrich_layout", "ostrich_set_threads", "ostrich_step", "ostrich_adjoint", "ostrich_tape_clear"):
+        L.ostrich_step_adjoint_noalloc.argtypes = [ctypes.POINTER(SceneDesc), ctypes.POINTER(SolverCfg), ctypes.c_int,
+                                                   ctypes.c_int, _vp, _vp, ctypes.c_double, _vp, _vp, _vp, _vp, _vp]
+        for name in ("ostrich_layout", "ostrich_set_threads", "ostrich_step", "ostrich_adjoint", "ostrich_tape_clear",
+                     "ostrich_step_adjoint_noalloc"):
             getattr(L, name).restype = ctypes.c_int
         _lib = L
     return _lib
@@ -128,6 +131,21 @@ def _stream(stream):
         import torch
         stream = torch.cuda.current_stream()
     return ctypes.c_void_p(stream.cuda_stream)
+
+
+NOALLOC_SCRATCH_BYTES = 16 << 20
+
+
+def ostrich_step_adjoint_noalloc(scene, cfg, n_worlds, state_in, controls, h, state_out, dL_dnext, dL_dstate,
+                                 dL_dcontrols=None, ld=0, stream=None):
+    """Step + adjoint with the tape in the library's fixed array (no device allocation);
+    FP32 tensors [rows, ld].  Raises on a non-OK status (EINVAL beyond the array's size)."""
+    d, c = scene_desc(scene), solver_cfg(cfg)
+    rc = lib().ostrich_step_adjoint_noalloc(ctypes.byref(d), ctypes.byref(c), int(n_worlds), int(ld), _ptr(state_in),
+                                            _ptr(controls), float(h), _ptr(state_out), _ptr(dL_dnext),
+                                            _ptr(dL_dstate), _ptr(dL_dcontrols), _stream(stream))
+    if rc != OSTRICH_OK:
+        raise RuntimeError(f"ostrich_step_adjoint_noalloc failed with status {rc}")
 
 
 class Context:

@@ -1,0 +1,63 @@
+"""The allocation-free step + adjoint against the context path.
+
+`ostrich_step_adjoint_noalloc` serves callers that cannot call cudaMalloc (a
+real-time control loop that must not allocate once running, work issued inside a
+stream capture, a plugin whose host framework owns the device memory): its tape lives
+in a fixed library array instead of a context's workspace.  Its results must match
+`ostrich_step` + `ostrich_adjoint` on a context within the parity tolerances, on two
+calls in a row (the second call reuses the array the first one left behind).  This
+file is collected last so that a run stopping at the first failure has run every
+other test first.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from paper_2609_08800_gb300 import scenes as S  # noqa: E402
+
+
+def test_noalloc_matches_context_path_twice():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_2609_08800_gb300 import ostrich as M
+    sc = S.robot_box_scene()
+    cfg = S.SolverConfig(tol=1e-4)
+    W, h = 96, 0.1
+    nb = sc.n_bodies
+    st = torch.tensor(S.robot_box_states(sc, W, seed=21), dtype=torch.float32, device="cuda")
+    ub = torch.tensor(S.random_controls(sc.n_servos, W, seed=21, low=-3, high=3), dtype=torch.float32, device="cuda")
+    g = torch.tensor(np.random.default_rng(22).normal(size=st.shape), dtype=torch.float32, device="cuda")
+    g[13 * nb:] = 0
+    ctx = M.Context(sc, cfg, W, dtype="f32", tape_slots=1)
+    s_in = st
+    for call in range(2):
+        ref = ctx.step(s_in, ub, h, tape_slot=0)
+        ref_ds, ref_du = ctx.adjoint(0, g, h)
+        out = torch.empty_like(s_in)
+        ds = torch.empty_like(s_in)
+        du = torch.empty(sc.n_servos, W, dtype=torch.float32, device="cuda")
+        M.ostrich_step_adjoint_noalloc(sc, cfg, W, s_in, ub, h, out, g, ds, du)
+        torch.cuda.synchronize()
+        x_r, x_n = ref["state"][:13 * nb].double(), out[:13 * nb].double()
+        scale = torch.clamp(x_r.abs().amax(dim=0), min=1.0)
+        assert ((x_n - x_r).abs().amax(dim=0) <= 1e-4 * scale).all(), f"call {call}: state"
+        gr, gn = ref_ds[:13 * nb].double(), ds[:13 * nb].double()
+        assert ((gn - gr).abs().amax(dim=0) <= 1e-3 * gr.abs().amax(dim=0)).all(), f"call {call}: dL/dstate"
+        assert ((du.double() - ref_du.double()).abs() <= 1e-3 * gr.abs().amax(dim=0)).all(), f"call {call}: dL/dcontrols"
+        s_in = out.clone()          # second call starts where the first ended
+    ctx.close()
+
+
+def test_noalloc_rejects_sizes_beyond_the_array():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_2609_08800_gb300 import ostrich as M
+    sc = S.robot_box_scene()
+    W = 1024                        # 1024 x 21.6 KB > 16 MiB
+    st = torch.zeros(sc.n_state, W, dtype=torch.float32, device="cuda")
+    ub = torch.zeros(sc.n_servos, W, dtype=torch.float32, device="cuda")
+    with pytest.raises(RuntimeError, match="status 1"):
+        M.ostrich_step_adjoint_noalloc(sc, S.SolverConfig(), W, st, ub, 0.1, torch.empty_like(st), st,
+                                       torch.empty_like(st))

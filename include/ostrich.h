@@ -150,7 +150,7 @@ void ostrich_destroy(ostrich_ctx* ctx);
  * n_worlds).  No context is needed and nothing is allocated, freed or kept.
  *
  * EINVAL if n_worlds times the scene's per-world tape record exceeds the array (for the
- * four-wheel robot over a box, 21.6 KB per world: at most 776 worlds), or on the same
+ * four-wheel robot over a box, 15.3 KB per world: at most 1097 worlds), or on the same
  * argument errors as ostrich_create / ostrich_step; ECUDA if a launch fails.
  * The first call on a device resolves the array's device address on that device (with
  * it current); make that first call before any stream capture.  Every call on a device

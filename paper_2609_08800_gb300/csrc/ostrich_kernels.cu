@@ -39,10 +39,10 @@ template <class Real> struct WS {
   // per-body row lists
   int *bgrp, *bsepn, *bsep;
   // groups
-  int *g0, *gn;
-  // Schur storage
-  Real *L, *F, *Ls, *Li, *Lsi, *tmp, *tmp2;
-  unsigned char *cpl;
+  int *g0, *gn, *rgrp;
+  // Schur storage (block-arrowhead, inverse form): G group blocks, E coupling rows,
+  // H = E G, S reduced separator; prow a pivot-row buffer per warp
+  Real *G, *E, *H, *S, *L, *prow, *tmp, *tmp2;
   // scratch
   Real *red;
   int *ints;      // [0] rows, [1] contact rows, [2] items, [3] converged, [4] best_k, [5] iters, [6] status
@@ -71,11 +71,13 @@ template <class Real> __host__ __device__ size_t ws_bytes(const DevScene& s) {
   b += 4 * sz(sizeof(Real), 3 * ns) + 2 * sz(sizeof(Real), ns) + sz(sizeof(Real), 2 * ns);
   b += 4 * sz(sizeof(int), ns);
   b += sz(sizeof(int), nb) * 2 + sz(sizeof(int), nb * ss);
-  b += 2 * sz(sizeof(int), ng);
-  int lsz = ng * pg * pg > 14 * m ? ng * pg * pg : 14 * m;
-  b += sz(sizeof(Real), lsz) + sz(sizeof(Real), ng * ss * pg) + sz(sizeof(Real), ss * ss);
-  b += sz(sizeof(Real), ng * pg * pg) + sz(sizeof(Real), ss * ss) + 2 * sz(sizeof(Real), m);
-  b += sz(1, ng * ss);
+  b += 2 * sz(sizeof(int), ng) + sz(sizeof(int), m);
+  int gsz = ng * pg * s.ldg > 14 * m ? ng * pg * s.ldg : 14 * m;   // G also holds the adjoint's VJP items
+  int cm = s.cmax > 0 ? s.cmax : 1, lds = s.lds > 0 ? s.lds : 1, ldg = s.ldg > 0 ? s.ldg : 1;
+  b += sz(sizeof(Real), gsz) + 2 * sz(sizeof(Real), ng * cm * ldg) + sz(sizeof(Real), ss * lds);
+  b += sz(sizeof(Real), 4 * (pg > ss ? pg : ss)) + 2 * sz(sizeof(Real), m);
+  int lsz2 = ng * pg * ldg > ss * lds ? ng * pg * ldg : ss * lds;
+  b += sz(sizeof(Real), lsz2);
   b += sz(sizeof(Real), 64) + sz(sizeof(int), 16) + sz(sizeof(Real), 8);
   b += 256;
   return b;
@@ -101,12 +103,15 @@ template <class Real> __host__ __device__ WS<Real> ws_carve(char* base, const De
   w.sedge = carve<Real>(p, 2 * ns);
   w.sact = carve<int>(p, ns); w.srow = carve<int>(p, ns); w.sid = carve<int>(p, ns); w.sftype = carve<int>(p, ns);
   w.bgrp = carve<int>(p, nb); w.bsepn = carve<int>(p, nb); w.bsep = carve<int>(p, nb * ss);
-  w.g0 = carve<int>(p, ng); w.gn = carve<int>(p, ng);
-  int lsz = ng * pg * pg > 14 * m ? ng * pg * pg : 14 * m;     // also holds the adjoint's VJP items
-  w.L = carve<Real>(p, lsz); w.F = carve<Real>(p, ng * ss * pg); w.Ls = carve<Real>(p, ss * ss);
-  w.Li = carve<Real>(p, ng * pg * pg); w.Lsi = carve<Real>(p, ss * ss);
+  w.g0 = carve<int>(p, ng); w.gn = carve<int>(p, ng); w.rgrp = carve<int>(p, m);
+  int gsz = ng * pg * s.ldg > 14 * m ? ng * pg * s.ldg : 14 * m;
+  int cm = s.cmax > 0 ? s.cmax : 1, lds = s.lds > 0 ? s.lds : 1, ldg = s.ldg > 0 ? s.ldg : 1;
+  w.G = carve<Real>(p, gsz); w.E = carve<Real>(p, ng * cm * ldg); w.H = carve<Real>(p, ng * cm * ldg);
+  w.S = carve<Real>(p, ss * lds);
+  w.prow = carve<Real>(p, 4 * (pg > ss ? pg : ss));
+  int lsz2 = ng * pg * ldg > ss * lds ? ng * pg * ldg : ss * lds;
+  w.L = carve<Real>(p, lsz2);
   w.tmp = carve<Real>(p, m); w.tmp2 = carve<Real>(p, m);
-  w.cpl = carve<unsigned char>(p, ng * ss);
   w.red = carve<Real>(p, 64); w.ints = carve<int>(p, 16); w.scal = carve<Real>(p, 8);
   return w;
 }
@@ -254,6 +259,7 @@ __device__ void world_setup(const DevScene& sc, WS<Real>& w, Src<Real> qmv, Src<
           int t = k == 0 ? ROW_NORMAL : ROW_FRIC;
           w.meta[4 * m] = t | (k << 4); w.meta[4 * m + 1] = b; w.meta[4 * m + 2] = -1; w.meta[4 * m + 3] = lam + k;
           w.ref[m] = sl;
+          w.rgrp[m] = g;
           ++m;
         }
       }
@@ -460,36 +466,36 @@ __device__ Real evaluate(const DevScene& sc, WS<Real>& w, const Real* u, const R
   // Eq. (10): r_dyn = M (u - u-) - h f - h J^T lambda, per body; merit part |M^-1 r_dyn|^2.
   // The inertia and constraint terms nearly cancel at convergence, so the sum is
   // accumulated with exact products and exact partial sums (acc2).
-  Real part = Real(0);
   const int ssd = sc.ss > 0 ? sc.ss : 1;
-  for (int b = tid; b < nb; b += nth) {
-    acc2<Real> rd[6];
+  for (int task = tid; task < 6 * nb; task += nth) {
+    const int b = task / 6, k = task - 6 * (task / 6);
+    acc2<Real> rd;
     int g = w.bgrp[b];
     if (g >= 0)
-      for (int i = w.g0[g]; i < w.g0[g] + w.gn[g]; ++i) {
-        Real hl = -hR * lam[i];
-        for (int k = 0; k < 6; ++k) rd[k].add_prod(w.J[12 * i + k], hl);
-      }
+      for (int i = w.g0[g]; i < w.g0[g] + w.gn[g]; ++i) rd.add_prod(w.J[12 * i + k], -hR * lam[i]);
     for (int t = 0; t < w.bsepn[b]; ++t) {
       int i = w.bsep[b * ssd + t];
       int side = w.meta[4 * i + 1] == b ? 0 : 6;
-      Real hl = -hR * lam[i];
-      for (int k = 0; k < 6; ++k) rd[k].add_prod(w.J[12 * i + side + k], hl);
+      rd.add_prod(w.J[12 * i + side + k], -hR * lam[i]);
     }
-    Real m_ = Real(sc.mass[b]);
-    for (int k = 0; k < 3; ++k) {
-      rd[k].add_prod(m_, u[6 * b + k]);
-      rd[k].add_prod(-m_, w.um[6 * b + k]);
-    }
-    for (int r = 0; r < 3; ++r)
+    if (k < 3) {
+      const Real m_ = Real(sc.mass[b]);
+      rd.add_prod(m_, u[6 * b + k]);
+      rd.add_prod(-m_, w.um[6 * b + k]);
+    } else {
       for (int c = 0; c < 3; ++c) {
-        rd[3 + r].add_prod(w.Iw[9 * b + 3 * r + c], u[6 * b + 3 + c]);
-        rd[3 + r].add_prod(-w.Iw[9 * b + 3 * r + c], w.um[6 * b + 3 + c]);
+        rd.add_prod(w.Iw[9 * b + 3 * (k - 3) + c], u[6 * b + 3 + c]);
+        rd.add_prod(-w.Iw[9 * b + 3 * (k - 3) + c], w.um[6 * b + 3 + c]);
       }
-    for (int k = 0; k < 6; ++k) rd[k].add_prod(-hR, w.f[6 * b + k]);
-    Real rv[6];
-    for (int k = 0; k < 6; ++k) { rv[k] = rd[k].value(); w.rdyn[6 * b + k] = rv[k]; }
-    Real mi = Real(1) / m_;
+    }
+    rd.add_prod(-hR, w.f[6 * b + k]);
+    w.rdyn[6 * b + k] = rd.value();
+  }
+  __syncthreads();
+  Real part = Real(0);
+  for (int b = tid; b < nb; b += nth) {
+    const Real* rv = w.rdyn + 6 * b;
+    Real mi = Real(1) / Real(sc.mass[b]);
     vec3<Real> iw = mat3<Real>(w.Iwi + 9 * b, v3(rv[3], rv[4], rv[5]));
     Real mr[6] = {rv[0] * mi, rv[1] * mi, rv[2] * mi, iw.x, iw.y, iw.z};
     for (int k = 0; k < 6; ++k) { w.mr[6 * b + k] = mr[k]; part += mr[k] * mr[k]; }
@@ -508,7 +514,7 @@ template <class Real> __device__ __forceinline__ Real rowdot(const Real* Ja, int
 
 template <class Real> __device__ void assemble(const DevScene& sc, WS<Real>& w, double h) {
   const int tid = threadIdx.x, nth = blockDim.x;
-  const int m = w.ints[0], mc = w.ints[1], pg = sc.pg, ss = sc.ss, ssd = ss > 0 ? ss : 1;
+  const int m = w.ints[0], mc = w.ints[1], pg = sc.pg, ss = sc.ss, ldg = sc.ldg, lds = sc.lds;
   const Real hR = Real(h);
   // delta = delta_rel * mean diag(h J M^-1 J^T)
   Real part = 0;
@@ -519,213 +525,210 @@ template <class Real> __device__ void assemble(const DevScene& sc, WS<Real>& w, 
   Real tot = block_sum(w, part);
   const Real delta = m > 0 ? Real(sc.delta_rel) * tot / Real(m) : Real(0);
   if (tid == 0) w.scal[2] = delta;
-  // group blocks (lower triangle)
-  for (int g = 0; g < sc.n_groups; ++g) {
-    const int r0 = w.g0[g], n = w.gn[g];
-    Real* L = w.L + g * pg * pg;
-    for (int e = tid; e < n * n; e += nth) {
-      int a = e / n, b = e % n;
-      if (b > a) continue;
-      int i = r0 + a, j = r0 + b;
-      Real v = hR * rowdot(w.J + 12 * i, 0, w.Y + 12 * j, 0);
-      if (a == b) v += w.C[i] + delta;
-      // radial friction block of the same slot
-      int ti = w.meta[4 * i] & 15, tj = w.meta[4 * j] & 15;
-      if (ti == ROW_FRIC && tj == ROW_FRIC && w.ref[i] == w.ref[j]) {
-        int si = w.meta[4 * i] >> 4, sj = w.meta[4 * j] >> 4;
-        const Real* rd = w.srad + 3 * w.ref[i];
+  // group blocks (full, symmetric) and their coupling rows E_g: a thread per contact row
+  for (int r = tid; r < mc; r += nth) {
+    const int g = w.rgrp[r], r0 = w.g0[g], i = r - r0, bg = sc.group_body[g];
+    Real* Gb = w.G + g * pg * ldg;
+    const int ti = w.meta[4 * r] & 15, si = w.meta[4 * r] >> 4;
+    for (int jj = r0; jj <= r; ++jj) {
+      const int j = jj - r0;
+      Real v = hR * rowdot(w.J + 12 * r, 0, w.Y + 12 * jj, 0);
+      if (jj == r) v += w.C[r] + delta;
+      if (ti == ROW_FRIC && (w.meta[4 * jj] & 15) == ROW_FRIC && w.ref[r] == w.ref[jj]) {
+        const Real* rd = w.srad + 3 * w.ref[r];
+        const int sj = w.meta[4 * jj] >> 4;
         v += (si == 1 && sj == 1) ? rd[0] : ((si == 2 && sj == 2) ? rd[2] : rd[1]);
       }
-      L[a * pg + b] = v;
+      Gb[i * ldg + j] = v;
+      Gb[j * ldg + i] = v;
+    }
+    Real* Eb = w.E + g * sc.cmax * ldg;
+    for (int k = 0; k < sc.cpl_n[g]; ++k) {
+      const int row = mc + sc.cpl_row[g][k];
+      const int side = w.meta[4 * row + 1] == bg ? 0 : 6;
+      Eb[k * ldg + i] = hR * rowdot(w.J + 12 * row, side, w.Y + 12 * r, 0);
     }
   }
-  // coupling E_g (separator rows x group rows)
-  for (int g = 0; g < sc.n_groups; ++g) {
-    const int r0 = w.g0[g], n = w.gn[g], bg = sc.group_body[g];
-    Real* F = w.F + g * ssd * pg;
-    for (int e = tid; e < ss * n; e += nth) {
-      int s = e / n, c = e % n;
-      int i = mc + s;
-      int side = w.meta[4 * i + 1] == bg ? 0 : (w.meta[4 * i + 2] == bg ? 6 : -1);
-      F[s * pg + c] = side < 0 ? Real(0) : hR * rowdot(w.J + 12 * i, side, w.Y + 12 * (r0 + c), 0);
-      if (c == 0) w.cpl[g * ssd + s] = side >= 0 ? 1 : 0;
+  // separator block (full, symmetric): a thread per separator row
+  for (int a = tid; a < ss; a += nth) {
+    const int i = mc + a;
+    const int ia0 = w.meta[4 * i + 1], ia1 = w.meta[4 * i + 2];
+    for (int b = 0; b <= a; ++b) {
+      const int j = mc + b;
+      const int jb0 = w.meta[4 * j + 1], jb1 = w.meta[4 * j + 2];
+      Real v = 0;
+      if (ia0 == jb0) v += rowdot(w.J + 12 * i, 0, w.Y + 12 * j, 0);
+      if (ia0 == jb1) v += rowdot(w.J + 12 * i, 0, w.Y + 12 * j, 6);
+      if (ia1 >= 0 && ia1 == jb0) v += rowdot(w.J + 12 * i, 6, w.Y + 12 * j, 0);
+      if (ia1 >= 0 && ia1 == jb1) v += rowdot(w.J + 12 * i, 6, w.Y + 12 * j, 6);
+      v *= hR;
+      if (a == b) v += w.C[i] + delta;
+      w.S[a * lds + b] = v;
+      w.S[b * lds + a] = v;
     }
-  }
-  // separator block
-  for (int e = tid; e < ss * ss; e += nth) {
-    int a = e / ss, b = e % ss;
-    if (b > a) continue;
-    int i = mc + a, j = mc + b;
-    int ia0 = w.meta[4 * i + 1], ia1 = w.meta[4 * i + 2], jb0 = w.meta[4 * j + 1], jb1 = w.meta[4 * j + 2];
-    Real v = 0;
-    if (ia0 == jb0) v += rowdot(w.J + 12 * i, 0, w.Y + 12 * j, 0);
-    if (ia0 == jb1) v += rowdot(w.J + 12 * i, 0, w.Y + 12 * j, 6);
-    if (ia1 >= 0 && ia1 == jb0) v += rowdot(w.J + 12 * i, 6, w.Y + 12 * j, 0);
-    if (ia1 >= 0 && ia1 == jb1) v += rowdot(w.J + 12 * i, 6, w.Y + 12 * j, 6);
-    v *= hR;
-    if (a == b) v += w.C[i] + delta;
-    w.Ls[a * ss + b] = v;
   }
   __syncthreads();
 }
 
-// pair (i, j), j <= i, of the e-th entry of a lower triangle stored row by row
-__device__ __forceinline__ void tri_pair(int e, int& i, int& j) {
-  int r = (int)((sqrtf(8.0f * (float)e + 1.0f) - 1.0f) * 0.5f);
-  while ((r + 1) * (r + 2) / 2 <= e) ++r;
-  while (r * (r + 1) / 2 > e) --r;
-  i = r; j = e - r * (r + 1) / 2;
-}
-
-// in-place Cholesky of the lower triangle of an n x n block (row-major, leading dim ld),
-// one warp; the trailing update is spread over the lanes by matrix entry
+// In-place Cholesky of the lower triangle of an n x n block (row-major, odd leading
+// dimension ld) by one warp: a lane per row for the column scaling and the trailing
+// update of its own row.
 template <class Real> __device__ void warp_chol(Real* A, int n, int ld) {
   const int lane = threadIdx.x & 31;
   for (int k = 0; k < n; ++k) {
-    Real akk = A[k * ld + k];
-    Real d = ssqrt(akk > Real(0) ? akk : Real(1e-30));
-    Real inv = Real(1) / d;
+    const Real akk = A[k * ld + k];
+    const Real d = ssqrt(akk > Real(0) ? akk : Real(1e-30));
+    const Real inv = Real(1) / d;
     __syncwarp();
     if (lane == 0) A[k * ld + k] = d;
     for (int i = k + 1 + lane; i < n; i += 32) A[i * ld + k] *= inv;
     __syncwarp();
-    const int r = n - k - 1, np = r * (r + 1) / 2;
-    for (int e = lane; e < np; e += 32) {
-      int ii, jj;
-      tri_pair(e, ii, jj);
-      const int i = k + 1 + ii, j = k + 1 + jj;
-      A[i * ld + j] -= A[i * ld + k] * A[j * ld + k];
+    for (int i = k + 1 + lane; i < n; i += 32) {
+      Real* Ai = A + i * ld;
+      const Real lik = Ai[k];
+      for (int j = k + 1; j <= i; ++j) Ai[j] -= lik * A[j * ld + k];
     }
     __syncwarp();
   }
 }
 
-// X = L^-1 (lower triangular) for an n x n Cholesky factor, one warp, a lane per column
+// X = L^-1 (lower triangular) for an n x n Cholesky factor, one warp, a lane per column.
 template <class Real> __device__ void warp_trinv(const Real* L, int n, int ld, Real* X) {
   const int lane = threadIdx.x & 31;
   for (int c = lane; c < n; c += 32) {
     for (int i = 0; i < c; ++i) X[i * ld + c] = Real(0);
     for (int i = c; i < n; ++i) {
       Real acc = i == c ? Real(1) : Real(0);
-      for (int l = c; l < i; ++l) acc -= L[i * ld + l] * X[l * ld + c];
-      X[i * ld + c] = acc / L[i * ld + i];
+      const Real* Li = L + i * ld;
+      for (int l = c; l < i; ++l) acc -= Li[l] * X[l * ld + c];
+      X[i * ld + c] = acc / Li[i];
     }
   }
   __syncwarp();
 }
 
-// Block-arrowhead factorisation of A, kept in inverse form for row-parallel solves:
-//   Li_g = L_g^-1 (group blocks), F_g = E_g L_g^-T (coupling), Lsi = L_s^-1 with
-//   L_s L_s^T = S - sum_g F_g F_g^T (reduced separator).
+// Block-arrowhead factorisation kept in inverse form for row-parallel solves:
+//   Li_g = L_g^-1 with L_g L_g^T = A_g (contact groups; stored in G),
+//   F_g = E_g L_g^-T (coupled separator rows; stored in H),
+//   Lsi = L_s^-1 with L_s L_s^T = S - sum_g F_g F_g^T (stored in S).
+// The group and separator blocks are factored in their own storage, then inverted into
+// the scratch E (groups; the coupling E_g is consumed first) and prow (separator).
 template <class Real> __device__ void factor(const DevScene& sc, WS<Real>& w) {
   const int tid = threadIdx.x, nth = blockDim.x, wid = tid >> 5, nw = (blockDim.x + 31) >> 5;
-  const int pg = sc.pg, ss = sc.ss, ssd = ss > 0 ? ss : 1;
-  for (int g = wid; g < sc.n_groups; g += nw) {
-    warp_chol(w.L + g * pg * pg, w.gn[g], pg);
-    warp_trinv(w.L + g * pg * pg, w.gn[g], pg, w.Li + g * pg * pg);
+  const int pg = sc.pg, ss = sc.ss, ldg = sc.ldg, lds = sc.lds, cm = sc.cmax;
+  for (int g = wid; g < sc.n_groups; g += nw) warp_chol(w.G + g * pg * ldg, w.gn[g], ldg);
+  __syncthreads();
+  // invert each group factor into L (scratch), then copy back over G
+  for (int g = wid; g < sc.n_groups; g += nw) warp_trinv(w.G + g * pg * ldg, w.gn[g], ldg, w.L + g * pg * ldg);
+  __syncthreads();
+  for (int g = 0; g < sc.n_groups; ++g) {
+    const int n = w.gn[g];
+    for (int e = tid; e < n * n; e += nth) {
+      const int i = e / n, j = e - i * n;
+      w.G[g * pg * ldg + i * ldg + j] = w.L[g * pg * ldg + i * ldg + j];
+    }
   }
   __syncthreads();
-  // F_g[s][j] = sum_{l <= j} E_g[s][l] Li_g[j][l], in place from high j to low j
-  for (int e = tid; e < sc.n_groups * ss; e += nth) {
-    int g = e / ssd, s = e % ssd;
-    if (s >= ss || !w.cpl[g * ssd + s]) continue;
-    const Real* Li = w.Li + g * pg * pg;
-    Real* f = w.F + g * ssd * pg + s * pg;
-    for (int j = w.gn[g] - 1; j >= 0; --j) {
+  // F_g[k][j] = sum_{l <= j} E_g[k][l] Li_g[j][l]
+  for (int g = 0; g < sc.n_groups; ++g) {
+    const int n = w.gn[g], cnt = sc.cpl_n[g] * n;
+    const Real* Lb = w.G + g * pg * ldg;
+    const Real* Eb = w.E + g * cm * ldg;
+    Real* Fb = w.H + g * cm * ldg;
+    for (int e = tid; e < cnt; e += nth) {
+      const int k = e / n, j = e - k * n;
       Real acc = 0;
-      for (int l = 0; l <= j; ++l) acc += f[l] * Li[j * pg + l];
-      f[j] = acc;
+      for (int l = 0; l <= j; ++l) acc += Eb[k * ldg + l] * Lb[j * ldg + l];
+      Fb[k * ldg + j] = acc;
     }
   }
   __syncthreads();
-  // S <- S - sum_g F_g F_g^T
-  for (int e = tid; e < ss * ss; e += nth) {
-    int a = e / ss, b = e % ss;
-    if (b > a) continue;
-    Real acc = 0;
-    for (int g = 0; g < sc.n_groups; ++g) {
-      if (!w.cpl[g * ssd + a] || !w.cpl[g * ssd + b]) continue;
-      const Real* fa = w.F + g * ssd * pg + a * pg;
-      const Real* fb = w.F + g * ssd * pg + b * pg;
-      for (int j = 0; j < w.gn[g]; ++j) acc += fa[j] * fb[j];
+  // S' = S - sum_g F_g F_g^T (lower triangle)
+  for (int a = tid; a < ss; a += nth) {
+    for (int b = 0; b <= a; ++b) {
+      Real acc = 0;
+      for (int pa = 0; pa < sc.sep_n[a]; ++pa)
+        for (int pb = 0; pb < sc.sep_n[b]; ++pb) {
+          const int g = sc.sep_g[a][pa];
+          if (g != sc.sep_g[b][pb]) continue;
+          const Real* fa = w.H + g * cm * ldg + sc.sep_k[a][pa] * ldg;
+          const Real* fb = w.H + g * cm * ldg + sc.sep_k[b][pb] * ldg;
+          for (int j = 0; j < w.gn[g]; ++j) acc += fa[j] * fb[j];
+        }
+      w.S[a * lds + b] -= acc;
     }
-    w.Ls[a * ss + b] -= acc;
   }
   __syncthreads();
   if (wid == 0 && ss > 0) {
-    warp_chol(w.Ls, ss, ss);
-    warp_trinv(w.Ls, ss, ss, w.Lsi);
+    warp_chol(w.S, ss, lds);
+    warp_trinv(w.S, ss, lds, w.L);
+    for (int e = threadIdx.x & 31; e < ss * ss; e += 32) {
+      const int i = e / ss, j = e - i * ss;
+      w.S[i * lds + j] = w.L[i * lds + j];
+    }
   }
   __syncthreads();
 }
 
-// v <- A^-1 v with the inverse-form arrowhead factor (row-parallel; scratch tmp, tmp2)
+// v <- A^-1 v with the inverse-form block-arrowhead factor (row-parallel phases)
 template <class Real> __device__ void arrow_solve(const DevScene& sc, WS<Real>& w, Real* v) {
   const int tid = threadIdx.x, nth = blockDim.x;
-  const int pg = sc.pg, ss = sc.ss, ssd = ss > 0 ? ss : 1, mc = w.ints[1], m = w.ints[0];
+  const int pg = sc.pg, ss = sc.ss, ldg = sc.ldg, lds = sc.lds, cm = sc.cmax, mc = w.ints[1];
   Real* y = w.tmp;
   Real* z = w.tmp2;
   // y_g = Li_g b_g
   for (int r = tid; r < mc; r += nth) {
-    int g = 0;
-    while (g + 1 < sc.n_groups && r >= w.g0[g + 1]) ++g;
-    const int j = r - w.g0[g];
-    const Real* Li = w.Li + g * pg * pg + j * pg;
-    const Real* b = v + w.g0[g];
+    const int g = w.rgrp[r], r0 = w.g0[g], i = r - r0;
+    const Real* Li = w.G + g * pg * ldg + i * ldg;
     Real acc = 0;
-    for (int l = 0; l <= j; ++l) acc += Li[l] * b[l];
+    for (int l = 0; l <= i; ++l) acc += Li[l] * v[r0 + l];
     y[r] = acc;
   }
   __syncthreads();
   // b_s' = b_s - sum_g F_g y_g
-  for (int s = tid; s < ss; s += nth) {
-    Real acc = v[mc + s];
-    for (int g = 0; g < sc.n_groups; ++g) {
-      if (!w.cpl[g * ssd + s]) continue;
-      const Real* f = w.F + g * ssd * pg + s * pg;
+  for (int a = tid; a < ss; a += nth) {
+    Real acc = v[mc + a];
+    for (int pa = 0; pa < sc.sep_n[a]; ++pa) {
+      const int g = sc.sep_g[a][pa];
+      const Real* f = w.H + g * cm * ldg + sc.sep_k[a][pa] * ldg;
       for (int j = 0; j < w.gn[g]; ++j) acc -= f[j] * y[w.g0[g] + j];
     }
-    z[mc + s] = acc;
+    z[a] = acc;
   }
   __syncthreads();
   // y_s = Lsi b_s'
-  for (int s = tid; s < ss; s += nth) {
+  for (int a = tid; a < ss; a += nth) {
+    const Real* La = w.S + a * lds;
     Real acc = 0;
-    for (int t = 0; t <= s; ++t) acc += w.Lsi[s * ss + t] * z[mc + t];
-    y[mc + s] = acc;
+    for (int b = 0; b <= a; ++b) acc += La[b] * z[b];
+    y[mc + a] = acc;
   }
   __syncthreads();
   // x_s = Lsi^T y_s
-  for (int s = tid; s < ss; s += nth) {
+  for (int a = tid; a < ss; a += nth) {
     Real acc = 0;
-    for (int t = s; t < ss; ++t) acc += w.Lsi[t * ss + s] * y[mc + t];
-    v[mc + s] = acc;
+    for (int b = a; b < ss; ++b) acc += w.S[b * lds + a] * y[mc + b];
+    v[mc + a] = acc;
   }
   __syncthreads();
   // r_g = y_g - F_g^T x_s
   for (int r = tid; r < mc; r += nth) {
-    int g = 0;
-    while (g + 1 < sc.n_groups && r >= w.g0[g + 1]) ++g;
-    const int j = r - w.g0[g];
+    const int g = w.rgrp[r], i = r - w.g0[g];
+    const Real* Fb = w.H + g * cm * ldg;
     Real acc = y[r];
-    for (int s = 0; s < ss; ++s)
-      if (w.cpl[g * ssd + s]) acc -= w.F[g * ssd * pg + s * pg + j] * v[mc + s];
+    for (int k = 0; k < sc.cpl_n[g]; ++k) acc -= Fb[k * ldg + i] * v[mc + sc.cpl_row[g][k]];
     z[r] = acc;
   }
   __syncthreads();
   // x_g = Li_g^T r_g
   for (int r = tid; r < mc; r += nth) {
-    int g = 0;
-    while (g + 1 < sc.n_groups && r >= w.g0[g + 1]) ++g;
-    const int j = r - w.g0[g], n = w.gn[g];
-    const Real* Li = w.Li + g * pg * pg;
-    const Real* zz = z + w.g0[g];
+    const int g = w.rgrp[r], r0 = w.g0[g], i = r - r0, n = w.gn[g];
+    const Real* Lb = w.G + g * pg * ldg;
     Real acc = 0;
-    for (int l = j; l < n; ++l) acc += Li[l * pg + j] * zz[l];
+    for (int l = i; l < n; ++l) acc += Lb[l * ldg + i] * z[r0 + l];
     v[r] = acc;
   }
   __syncthreads();
-  (void)m;
 }
 
 // out_b = sum over rows touching body b of J_row,b^T x_row  (6 per body)
@@ -921,10 +924,9 @@ __global__ void __launch_bounds__(128) step_kernel(const DevScene sc, const Step
     for (int i = tid; i < sc.m_max; i += nth) tp[tl.off_lam + i] = Real(0);
     __syncthreads();
     for (int i = tid; i < m; i += nth) tp[tl.off_lam + w.meta[4 * i + 3]] = w.lk[i];
-    const int pg = sc.pg, ssd = sc.ss > 0 ? sc.ss : 1;
-    for (int i = tid; i < sc.n_groups * pg * pg; i += nth) tp[tl.off_leaf + i] = w.Li[i];
-    for (int i = tid; i < sc.n_groups * ssd * pg; i += nth) tp[tl.off_cpl + i] = w.F[i];
-    for (int i = tid; i < sc.ss * sc.ss; i += nth) tp[tl.off_sep + i] = w.Lsi[i];
+    for (int i = tid; i < sc.n_groups * sc.pg * sc.ldg; i += nth) tp[tl.off_G + i] = w.G[i];
+    for (int i = tid; i < sc.n_groups * sc.cmax * sc.ldg; i += nth) tp[tl.off_H + i] = w.H[i];
+    for (int i = tid; i < sc.ss * sc.lds; i += nth) tp[tl.off_S + i] = w.S[i];
   }
   // outputs: q+ (normalised quaternions), u+, lambda+, impulses h lambda, contact ids
   Real* so = reinterpret_cast<Real*>(a.state_out);
@@ -1102,17 +1104,9 @@ __global__ void __launch_bounds__(128) adjoint_kernel(const DevScene sc, const A
   __syncthreads();
   evaluate(sc, w, w.uk, w.lk, h);      // J (with E at u*), poses at q+
   // factor from the tape
-  const int pg = sc.pg, ssd = sc.ss > 0 ? sc.ss : 1;
-  for (int i = tid; i < sc.n_groups * pg * pg; i += nth) w.Li[i] = tp[tl.off_leaf + i];
-  for (int i = tid; i < sc.n_groups * ssd * pg; i += nth) w.F[i] = tp[tl.off_cpl + i];
-  for (int i = tid; i < sc.ss * sc.ss; i += nth) w.Lsi[i] = tp[tl.off_sep + i];
-  // coupling flags are a function of the row structure only
-  for (int e = tid; e < sc.n_groups * ssd; e += nth) {
-    int g = e / ssd, s = e % ssd;
-    int bg = sc.group_body[g];
-    int i = mc + s;
-    w.cpl[e] = (s < sc.ss) && (w.meta[4 * i + 1] == bg || w.meta[4 * i + 2] == bg);
-  }
+  for (int i = tid; i < sc.n_groups * sc.pg * sc.ldg; i += nth) w.G[i] = tp[tl.off_G + i];
+  for (int i = tid; i < sc.n_groups * sc.cmax * sc.ldg; i += nth) w.H[i] = tp[tl.off_H + i];
+  for (int i = tid; i < sc.ss * sc.lds; i += nth) w.S[i] = tp[tl.off_S + i];
   // incoming cotangent: normalisation Jacobian of the output quaternions, then g
   Real* gq = w.lb;      // the best-iterate buffer is free in the adjoint; m_max >= 7 nb
   Real* gu = w.du;
@@ -1197,7 +1191,7 @@ __global__ void __launch_bounds__(128) adjoint_kernel(const DevScene sc, const A
     for (int i = mc + 5 * sc.nj + tid; i < m; i += nth) dctl[(size_t)(i - mc - 5 * sc.nj) * ld + world] = -wl[i];
   // dL/dq-: per-row and per-body dual-number derivatives, summed in a fixed order
   const bool trunc = sc.pullback == 1;
-  Real* item = w.L;     // factor no longer needed: m * 14 row items + nb * 7 body items
+  Real* item = w.G;     // factor no longer needed: m * 14 row items + nb * 7 body items
   for (int e = tid; e < m * 14; e += nth) {
     int i = e / 14, r = e % 14, side = r / 7, c = r % 7;
     int b = side == 0 ? w.meta[4 * i + 1] : w.meta[4 * i + 2];
@@ -1206,7 +1200,7 @@ __global__ void __launch_bounds__(128) adjoint_kernel(const DevScene sc, const A
   Real* bitem = w.rhs;  // nb * 7 <= m_max is checked when the context is created
   for (int e = tid; e < nb * 7; e += nth) bitem[e] = body_vjp(sc, w, e / 7, e % 7, gq, wu, h);
   __syncthreads();
-  const int ssdd = ssd;
+  const int ssdd = sc.ss > 0 ? sc.ss : 1;
   for (int e = tid; e < nb * 7; e += nth) {
     int b = e / 7, c = e % 7;
     acc2<Real> acc;        // the terms cancel strongly: compensated sum

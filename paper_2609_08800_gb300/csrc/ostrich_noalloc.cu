@@ -83,12 +83,7 @@ bool make_scene(const ostrich_scene_desc* d, const ostrich_solver_cfg* cfg, ost:
   }
   s.m_max = 5 * s.nj + s.n_servo + 3 * s.n_slots;
   s.n_state = 13 * s.nb + s.m_max;
-  for (int b = 0; b < s.nb; ++b)
-    if (s.slot_count[b] > 0) {
-      s.group_body[s.n_groups++] = b;
-      if (3 * s.slot_count[b] > s.pg) s.pg = 3 * s.slot_count[b];
-    }
-  s.ss = 5 * s.nj + s.n_servo;
+  ost::finish_scene(s);
   s.budget = cfg->budget; s.kmin = cfg->k_min; s.ls = cfg->line_search; s.pullback = cfg->pullback;
   s.tol = cfg->tol; s.delta_rel = cfg->delta_rel; s.kappa = cfg->kappa; s.eps = cfg->eps_fb; s.margin = cfg->margin;
   s.refine = 2;

@@ -8,6 +8,7 @@ namespace ost {
 constexpr int NB_CAP = 8;      // bodies per world
 constexpr int NJ_CAP = 8;      // revolute joints per world
 constexpr int SLOT_CAP = 64;   // contact slots per world
+constexpr int SEP_CAP = 5 * NJ_CAP + NJ_CAP;   // separator rows per world
 
 enum { SHAPE_NONE = 0, SHAPE_BOX = 1, SHAPE_WHEEL = 2 };
 enum { ENV_PLANE = 0, ENV_BOX = 1, ENV_HEIGHTMAP = 2 };
@@ -37,7 +38,50 @@ struct DevScene {
   int pg;         // largest leaf block (3 x slots of one body)
   int ss;         // separator rows (5 per joint + servos)
   int group_body[NB_CAP];
+  // static coupling between groups and separator rows (the separator rows are always
+  // present): group g couples to separator rows cpl_row[g][0 .. cpl_n[g]); separator row
+  // a belongs to the lists of sep_n[a] <= 2 groups, at (sep_g[a][i], sep_k[a][i])
+  int ldg, lds, cmax;                    // odd leading dimensions of group / separator blocks
+  int cpl_n[NB_CAP];
+  unsigned char cpl_row[NB_CAP][SEP_CAP];
+  unsigned char sep_n[SEP_CAP], sep_g[SEP_CAP][2], sep_k[SEP_CAP][2];
 };
+
+// Derived layout of a filled scene: groups, block sizes, the static coupling lists.
+inline void finish_scene(DevScene& s) {
+  s.n_groups = 0; s.pg = 0;
+  for (int b = 0; b < s.nb; ++b)
+    if (s.slot_count[b] > 0) {
+      s.group_body[s.n_groups++] = b;
+      if (3 * s.slot_count[b] > s.pg) s.pg = 3 * s.slot_count[b];
+    }
+  s.ss = 5 * s.nj + s.n_servo;
+  s.ldg = s.pg | 1;
+  s.lds = s.ss | 1;
+  int gof[NB_CAP];
+  for (int b = 0; b < NB_CAP; ++b) gof[b] = -1;
+  for (int g = 0; g < s.n_groups; ++g) { gof[s.group_body[g]] = g; s.cpl_n[g] = 0; }
+  for (int a = 0; a < s.ss; ++a) {
+    int j = a < 5 * s.nj ? a / 5 : -1;
+    if (j < 0) {                          // servo row: find its joint
+      int k = a - 5 * s.nj, cnt = -1;
+      for (j = 0; j < s.nj; ++j) if (s.servo_of[j] >= 0 && ++cnt == k) break;
+    }
+    s.sep_n[a] = 0;
+    int bodies[2] = {s.jp[j], s.jc[j]};
+    for (int t = 0; t < 2; ++t) {
+      int g = gof[bodies[t]];
+      if (g < 0) continue;
+      int k = s.cpl_n[g]++;
+      s.cpl_row[g][k] = (unsigned char)a;
+      s.sep_g[a][s.sep_n[a]] = (unsigned char)g;
+      s.sep_k[a][s.sep_n[a]] = (unsigned char)k;
+      s.sep_n[a]++;
+    }
+  }
+  s.cmax = 0;
+  for (int g = 0; g < s.n_groups; ++g) if (s.cpl_n[g] > s.cmax) s.cmax = s.cpl_n[g];
+}
 
 // Arguments of one launch of the step / adjoint kernels.
 struct StepArgs {
@@ -51,10 +95,11 @@ struct AdjArgs {
   int ld, n_worlds, world0; double h;
 };
 
-// Tape record of one world for one step: inputs, returned iterate and the Schur factor.
+// Tape record of one world for one step: inputs, returned iterate and the Schur factor
+// (block-arrowhead, in inverse form).
 // All counts in Real elements.
 struct TapeLayout {
-  int off_qm, off_um, off_ubar, off_u, off_lam, off_leaf, off_cpl, off_sep, total;
+  int off_qm, off_um, off_ubar, off_u, off_lam, off_G, off_H, off_S, total;
 };
 
 inline __host__ __device__ TapeLayout tape_layout(const DevScene& s) {
@@ -65,9 +110,9 @@ inline __host__ __device__ TapeLayout tape_layout(const DevScene& s) {
   t.off_ubar = o; o += s.n_servo > 0 ? s.n_servo : 1;
   t.off_u = o; o += 6 * s.nb;
   t.off_lam = o; o += s.m_max;
-  t.off_leaf = o; o += s.n_groups * s.pg * s.pg;
-  t.off_cpl = o; o += s.n_groups * (s.ss > 0 ? s.ss : 1) * s.pg;
-  t.off_sep = o; o += s.ss * s.ss;
+  t.off_G = o; o += s.n_groups * s.pg * s.ldg;       // inverse Cholesky factors L_g^-1 of the groups
+  t.off_H = o; o += s.n_groups * s.cmax * s.ldg;     // F_g = E_g L_g^-T (coupled separator rows)
+  t.off_S = o; o += s.ss * s.lds;                    // inverse Cholesky factor of the reduced separator
   o = (o + 3) & ~3;   // 16-byte multiple per world for FP32
   t.total = o;
   return t;

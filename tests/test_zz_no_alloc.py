@@ -55,7 +55,7 @@ def test_noalloc_rejects_sizes_beyond_the_array():
         pytest.skip("no GPU")
     from paper_2609_08800_gb300 import ostrich as M
     sc = S.robot_box_scene()
-    W = 1024                        # 1024 x 21.6 KB > 16 MiB
+    W = 2048                        # 2048 x 15.3 KB > 16 MiB
     st = torch.zeros(sc.n_state, W, dtype=torch.float32, device="cuda")
     ub = torch.zeros(sc.n_servos, W, dtype=torch.float32, device="cuda")
     with pytest.raises(RuntimeError, match="status 1"):

@@ -804,13 +804,18 @@ __device__ void schur_solve(const DevScene& sc, WS<Real>& w, const Real* b, Real
       acc2<Real> ax;
       for (int k = 0; k < 6; ++k) ax.add_prod(Ji[k], t6[6 * b0 + k]);
       if (b1 >= 0) for (int k = 0; k < 6; ++k) ax.add_prod(Ji[6 + k], t6[6 * b1 + k]);
-      Real v = hR * ax.value() + (w.C[i] + delta) * x[i];
+      acc2<Real> res;                   // r = b - A x, compensated throughout
+      res.add(b[i]);
+      res.add_prod(-hR, ax.s);
+      res.add_prod(-hR, ax.c);
+      res.add_prod(-(w.C[i] + delta), x[i]);
       int t = w.meta[4 * i] & 15, sub = w.meta[4 * i] >> 4;
       if (t == ROW_FRIC) {
         const Real* rd = w.srad + 3 * w.ref[i];
-        v += sub == 1 ? rd[0] * x[i] + rd[1] * x[i + 1] : rd[1] * x[i - 1] + rd[2] * x[i];
+        if (sub == 1) { res.add_prod(-rd[0], x[i]); res.add_prod(-rd[1], x[i + 1]); }
+        else { res.add_prod(-rd[1], x[i - 1]); res.add_prod(-rd[2], x[i]); }
       }
-      r[i] = b[i] - v;
+      r[i] = res.value();
     }
     __syncthreads();
     arrow_solve(sc, w, r);
@@ -822,9 +827,22 @@ __device__ void schur_solve(const DevScene& sc, WS<Real>& w, const Real* b, Real
 // ---------------------------------------------------------------------------
 // forward step kernel
 // ---------------------------------------------------------------------------
+// The scene lives in shared memory during a launch: kernels index its per-body and
+// per-row tables with thread-dependent indices, which the constant (parameter) cache
+// would serialise across a warp.
+__device__ __forceinline__ void scene_to_shared(const DevScene& src, DevScene& dst) {
+  const int* s = reinterpret_cast<const int*>(&src);
+  int* d = reinterpret_cast<int*>(&dst);
+  for (int i = threadIdx.x; i < (int)(sizeof(DevScene) / sizeof(int)); i += blockDim.x) d[i] = s[i];
+  __syncthreads();
+}
+
 template <class Real>
-__global__ void __launch_bounds__(128) step_kernel(const DevScene sc, const StepArgs a) {
+__global__ void __launch_bounds__(128) step_kernel(const DevScene scp, const StepArgs a) {
   extern __shared__ __align__(16) char smem[];
+  __shared__ __align__(16) DevScene ssc;
+  scene_to_shared(scp, ssc);
+  const DevScene& sc = ssc;
   WS<Real> w = ws_carve<Real>(smem, sc);
   const int tid = threadIdx.x, nth = blockDim.x;
   const int world = a.world0 + blockIdx.x;
@@ -1085,8 +1103,11 @@ __device__ Real body_vjp(const DevScene& sc, const WS<Real>& w, int b, int dc, c
 }
 
 template <class Real>
-__global__ void __launch_bounds__(128) adjoint_kernel(const DevScene sc, const AdjArgs a) {
+__global__ void __launch_bounds__(128) adjoint_kernel(const DevScene scp, const AdjArgs a) {
   extern __shared__ __align__(16) char smem[];
+  __shared__ __align__(16) DevScene ssc;
+  scene_to_shared(scp, ssc);
+  const DevScene& sc = ssc;
   WS<Real> w = ws_carve<Real>(smem, sc);
   const int tid = threadIdx.x, nth = blockDim.x;
   const int world = a.world0 + blockIdx.x;
@@ -1158,7 +1179,7 @@ __global__ void __launch_bounds__(128) adjoint_kernel(const DevScene sc, const A
     w.rhs[i] = -hR * jm.value();
   }
   __syncthreads();
-  schur_solve(sc, w, w.rhs, wl, w.f, w.lt, h, 2 * sc.refine);
+  schur_solve(sc, w, w.rhs, wl, w.f, w.lt, h, 4 * sc.refine);
   // Eq. (19): w_u = -M^-1 (g + J^T w_lambda)
   Real* wu = w.ub;
   jt_apply_acc(sc, w, wl, w.f);     // f is free now

@@ -152,7 +152,10 @@ def test_robot_box_fp32_matches_oracle(ostrich, seed):
     W = 67
     st = S.robot_box_states(sc, W, seed=seed)
     ub = S.random_controls(sc.n_servos, W, seed=seed, low=-3, high=3)
-    cfg = S.SolverConfig()
+    # The IFT adjoint assumes r = 0: the FP32 comparison gives the Newton loop a budget
+    # of 40 so the returned iterate reaches the FP32 floor (with the paper's 16 a few
+    # worlds stop short of it and their gradients differ by up to ~1e-3).
+    cfg = S.SolverConfig(budget=40)
     g = np.random.default_rng(seed + 10).normal(size=st.shape)
     g[13 * sc.n_bodies:] = 0
     _compare(sc, cfg, ostrich, st, ub, 0.1, "f32", 1e-4, 1e-3, 1e-3, 0.85, grads=g,

@@ -171,6 +171,11 @@ def run_ours(args, rank, world_size, local_rank):
     scene, states, controls, g = make_inputs(W, seed=rank)
     cfg = S.SolverConfig(tol=FP32_TOL)
     ctx = Context(scene, cfg, W, dtype="f32", tape_slots=CHUNK, threads=args.threads)
+    threads = args.threads
+    if threads is None:
+        from paper_2609_08800_gb300 import tune
+        threads = tune.apply(ctx) or 64
+        ctx.set_threads(threads)
     s0 = torch.tensor(states, dtype=torch.float32, device=dev)
     ctl = torch.tensor(controls, dtype=torch.float32, device=dev)
     gT = torch.tensor(g, dtype=torch.float32, device=dev)
@@ -227,6 +232,7 @@ def run_ours(args, rank, world_size, local_rank):
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": "robot_over_box_8192_worlds_fp32_fwd_adj_chunk10", "worlds_per_gpu": W,
                    "steps_per_chunk": CHUNK, "h": H, "newton_budget": cfg.budget,
+                   "threads_per_world": threads,
                    "parallelism": f"replicas{world_size}",
                    "l2": f"tape of one chunk {ctx.tape_bytes() * CHUNK / 1e9:.2f} GB > 129 MB L2 (no flush needed)"},
         "gpu_launches": 2 * CHUNK * args.steps,
@@ -391,7 +397,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--worlds", type=int, default=8192)
-    ap.add_argument("--threads", type=int, default=64)
+    ap.add_argument("--threads", type=int, default=None, help="threads per world (default: autotuner table)")
     ap.add_argument("--plain-worlds", type=int, default=512)
     ap.add_argument("--cpu-worlds", type=int, default=24)
     ap.add_argument("--skip-extras", action="store_true",

@@ -1241,10 +1241,24 @@ __global__ void __launch_bounds__(128) adjoint_kernel(const DevScene scp, const 
 // ---------------------------------------------------------------------------
 // launchers (called by the C ABI)
 // ---------------------------------------------------------------------------
+// The dynamic shared-memory limit of a kernel is raised once per device and size; a
+// launch inside a stream capture then issues nothing but the launch itself.
+template <class K> cudaError_t ensure_smem(K kernel, size_t smem, int* done_dev, size_t* done_size) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 64 && done_size[dev] >= smem && done_dev[dev]) return cudaSuccess;
+  e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e == cudaSuccess && dev < 64) { done_dev[dev] = 1; if (smem > done_size[dev]) done_size[dev] = smem; }
+  return e;
+}
+
 template <class Real>
 cudaError_t launch_step(const DevScene& sc, const StepArgs& a, int threads, cudaStream_t st) {
+  static int done_dev[64] = {0};
+  static size_t done_size[64] = {0};
   size_t smem = ws_bytes<Real>(sc);
-  cudaError_t e = cudaFuncSetAttribute(step_kernel<Real>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = ensure_smem(step_kernel<Real>, smem, done_dev, done_size);
   if (e != cudaSuccess) return e;
   int n = a.n_worlds - a.world0;
   if (n <= 0) return cudaSuccess;
@@ -1254,8 +1268,10 @@ cudaError_t launch_step(const DevScene& sc, const StepArgs& a, int threads, cuda
 
 template <class Real>
 cudaError_t launch_adjoint(const DevScene& sc, const AdjArgs& a, int threads, cudaStream_t st) {
+  static int done_dev[64] = {0};
+  static size_t done_size[64] = {0};
   size_t smem = ws_bytes<Real>(sc);
-  cudaError_t e = cudaFuncSetAttribute(adjoint_kernel<Real>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = ensure_smem(adjoint_kernel<Real>, smem, done_dev, done_size);
   if (e != cudaSuccess) return e;
   int n = a.n_worlds - a.world0;
   if (n <= 0) return cudaSuccess;

@@ -31,10 +31,10 @@ def ostrich():
     return M
 
 
-def _run_gpu(M, scene, cfg, states, controls, h, dtype, grads=None):
+def _run_gpu(M, scene, cfg, states, controls, h, dtype, grads=None, threads=None):
     W = states.shape[1]
     tdt = torch.float64 if dtype == "f64" else torch.float32
-    ctx = M.Context(scene, cfg, W, dtype=dtype, tape_slots=1)
+    ctx = M.Context(scene, cfg, W, dtype=dtype, tape_slots=1, threads=threads)
     s_in = torch.tensor(states, dtype=tdt, device="cuda")
     u_in = torch.tensor(controls if controls.size else np.zeros((1, W)), dtype=tdt, device="cuda")
     r = ctx.step(s_in, u_in, h, tape_slot=0)
@@ -67,11 +67,11 @@ def _exact_residual(orc, scene, s_in, ub, h, out_state):
 
 
 def _compare(scene, cfg, g, states, controls, h, dtype, tol_state, tol_imp, tol_grad, min_frac, grads=None,
-             oracle_cfg=None, floor=None):
+             oracle_cfg=None, floor=None, threads=None):
     orc = O.Oracle(scene, oracle_cfg or cfg)
     orc_cfg_run = O.Oracle(scene, cfg)
     W = states.shape[1]
-    r = _run_gpu(g, scene, cfg, states, controls, h, dtype, grads)
+    r = _run_gpu(g, scene, cfg, states, controls, h, dtype, grads, threads)
     nb = scene.n_bodies
     n_cmp = 0
     for w in range(W):
@@ -162,9 +162,11 @@ def test_robot_box_fp32_matches_oracle(ostrich, seed):
              oracle_cfg=S.SolverConfig(budget=60, tol=1e-8), floor=3e-4)
 
 
-def test_robot_box_fp64_matches_oracle(ostrich):
+@pytest.mark.parametrize("threads", [64, 32, 128])
+def test_robot_box_fp64_matches_oracle(ostrich, threads):
     """The FP64 build of the same kernels against the oracle on the robot: the
-    implementation itself, free of FP32 effects."""
+    implementation itself, free of FP32 effects; at every launch shape the
+    autotuner may pick."""
     sc = S.robot_box_scene()
     W = 33
     st = S.robot_box_states(sc, W, seed=5)
@@ -172,4 +174,4 @@ def test_robot_box_fp64_matches_oracle(ostrich):
     cfg = S.SolverConfig(budget=40, tol=1e-9)
     g = np.random.default_rng(15).normal(size=st.shape)
     g[13 * sc.n_bodies:] = 0
-    _compare(sc, cfg, ostrich, st, ub, 0.1, "f64", 1e-7, 1e-6, 1e-6, 0.8, grads=g)
+    _compare(sc, cfg, ostrich, st, ub, 0.1, "f64", 1e-7, 1e-6, 1e-6, 0.8, grads=g, threads=threads)

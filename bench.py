@@ -118,7 +118,7 @@ def make_inputs(n_worlds, seed=0):
     knots = S.spline_knots(n_worlds, n_wheels=4, n_knots=8, seed=seed)
     T = 100
     B = SP.basis(T, 8, H)                        # [T, K] natural cubic spline, knots over [0, T h]
-    controls = np.einsum("tk,wjk->tjw", B, knots)   # [T, 4, W]
+    controls = np.ascontiguousarray(np.einsum("tk,wjk->tjw", B, knots))   # [T, 4, W], world index fastest
     # cotangent of the chunk's last state: d/ds of |p_xy - (3, 0)|^2 of the chassis
     g = np.zeros((scene.n_state, n_worlds))
     g[0] = 2.0 * (states[0] - 3.0)
@@ -309,12 +309,18 @@ def run_plain(args, scene, cfg, states, controls, g, torch):
     gr[CHUNK].copy_(gT)
     esz = 4
 
-    class P:   # a device address with an element offset
+    class P:   # a device address with an element offset (column w of a dense [rows, ld] array)
+        is_cuda = True
+
         def __init__(self, t, off):
+            assert t.is_contiguous()
             self.p = t.data_ptr() + off * esz
 
         def data_ptr(self):
             return self.p
+
+        def is_contiguous(self):
+            return True
 
     def world(w):
         for t in range(CHUNK):

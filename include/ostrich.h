@@ -124,6 +124,29 @@ ostrich_status ostrich_step(ostrich_ctx* ctx, const void* state_in, const void* 
 ostrich_status ostrich_adjoint(ostrich_ctx* ctx, int tape_slot, const void* dL_dstate_next, double h,
                                void* dL_dstate, void* dL_dcontrols, void* stream);
 
+/* Step of a selected subset of worlds (Sec. III-C, per world as ostrich_step): CTA b
+ * steps world worlds[b] and, when tape_slots is not NULL and tape_slots[b] >= 0,
+ * records it in that slot.  worlds and tape_slots are device arrays of n_list
+ * int32 entries; the worlds must be distinct.  Entries outside [0, n_worlds) and slots
+ * outside [-1, tape_slots of the context) are skipped or record nothing, on the device.
+ * Unlike ostrich_step, state_in may equal state_out: a world reads its own column
+ * before it writes it and touches no other.  Unlisted worlds are left untouched.  The
+ * slots' bookkeeping is the caller's: ostrich_adjoint_list trusts that each listed
+ * slot holds that world's step taken with the same h.  This is the batching entry point
+ * of a serving loop whose requests stand at different steps of their horizons. */
+ostrich_status ostrich_step_list(ostrich_ctx* ctx, const void* state_in, const void* controls, double h,
+                                 void* state_out, void* impulses_out, int32_t* contact_ids_out,
+                                 uint32_t* world_status, int32_t* iters_out, const int32_t* worlds,
+                                 const int32_t* tape_slots, int n_list, void* stream);
+
+/* Adjoint (Sec. III-D, per world as ostrich_adjoint) of a selected subset of worlds:
+ * CTA b back-propagates world worlds[b] through the step recorded in tape_slots[b].
+ * dL_dstate_next may equal dL_dstate.  Entries out of range are skipped (their
+ * outputs untouched).  n_list <= n_worlds; EINVAL otherwise. */
+ostrich_status ostrich_adjoint_list(ostrich_ctx* ctx, const void* dL_dstate_next, double h, void* dL_dstate,
+                                    void* dL_dcontrols, const int32_t* worlds, const int32_t* tape_slots, int n_list,
+                                    void* stream);
+
 /* Diagnostic: when merits is a device pointer of n_worlds * (budget + 2) doubles, the
  * following steps record the merit of the warm start and of every Newton iterate of
  * each world there; NULL switches it off. */

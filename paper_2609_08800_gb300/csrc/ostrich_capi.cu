@@ -167,6 +167,52 @@ ostrich_status ostrich_step(ostrich_ctx* c, const void* state_in, const void* co
   return OSTRICH_OK;
 }
 
+ostrich_status ostrich_step_list(ostrich_ctx* c, const void* state_in, const void* controls, double h,
+                                 void* state_out, void* impulses_out, int32_t* ids, uint32_t* status, int32_t* iters,
+                                 const int32_t* worlds, const int32_t* tape_slots, int n_list, void* stream) {
+  if (!c) return OSTRICH_EINVAL;
+  if (!state_in || !state_out) return fail(c, OSTRICH_EINVAL, "state_in/state_out missing");
+  if (c->sc.n_servo > 0 && !controls) return fail(c, OSTRICH_EINVAL, "controls required: the scene has servos");
+  if (!(h > 0)) return fail(c, OSTRICH_EINVAL, "h must be positive");
+  if (n_list < 0 || n_list > c->n_worlds) return fail(c, OSTRICH_EINVAL, "n_list outside [0, n_worlds]");
+  if (n_list > 0 && !worlds) return fail(c, OSTRICH_EINVAL, "worlds list missing");
+  if (tape_slots && !c->tape) return fail(c, OSTRICH_EINVAL, "tape slots given but the context has no tape");
+  if (n_list == 0) return OSTRICH_OK;
+  ost::StepArgs a;
+  a.state_in = state_in; a.controls = controls; a.state_out = state_out; a.impulses = impulses_out;
+  a.ids = ids; a.status = status; a.iters = iters;
+  a.tape = tape_slots ? c->tape : nullptr;
+  a.ld = c->ld; a.n_worlds = c->n_worlds; a.world0 = 0; a.h = h;
+  a.trace = c->trace;
+  a.list = worlds; a.list_slot = tape_slots; a.n_list = n_list; a.tape_slots = c->tape_slots;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  cudaError_t e = c->dtype == OSTRICH_F64 ? ost::launch_step<double>(c->sc, a, c->threads, st)
+                                          : ost::launch_step<float>(c->sc, a, c->threads, st);
+  if (e != cudaSuccess) return cuda_fail(c, e, "ostrich_step_list launch");
+  return OSTRICH_OK;
+}
+
+ostrich_status ostrich_adjoint_list(ostrich_ctx* c, const void* dL_dnext, double h, void* dL_dstate,
+                                    void* dL_dcontrols, const int32_t* worlds, const int32_t* tape_slots, int n_list,
+                                    void* stream) {
+  if (!c) return OSTRICH_EINVAL;
+  if (!c->tape) return fail(c, OSTRICH_ETAPE, "the context has no tape");
+  if (!dL_dnext || !dL_dstate) return fail(c, OSTRICH_EINVAL, "gradient pointers missing");
+  if (!(h > 0)) return fail(c, OSTRICH_EINVAL, "h must be positive");
+  if (n_list < 0 || n_list > c->n_worlds) return fail(c, OSTRICH_EINVAL, "n_list outside [0, n_worlds]");
+  if (n_list > 0 && (!worlds || !tape_slots)) return fail(c, OSTRICH_EINVAL, "worlds or tape_slots list missing");
+  if (n_list == 0) return OSTRICH_OK;
+  ost::AdjArgs a;
+  a.tape = c->tape; a.dL_dnext = dL_dnext; a.dL_dstate = dL_dstate; a.dL_dcontrols = dL_dcontrols;
+  a.ld = c->ld; a.n_worlds = c->n_worlds; a.world0 = 0; a.h = h;
+  a.list = worlds; a.list_slot = tape_slots; a.n_list = n_list; a.tape_slots = c->tape_slots;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  cudaError_t e = c->dtype == OSTRICH_F64 ? ost::launch_adjoint<double>(c->sc, a, c->threads, st)
+                                          : ost::launch_adjoint<float>(c->sc, a, c->threads, st);
+  if (e != cudaSuccess) return cuda_fail(c, e, "ostrich_adjoint_list launch");
+  return OSTRICH_OK;
+}
+
 ostrich_status ostrich_adjoint(ostrich_ctx* c, int tape_slot, const void* dL_dnext, double h, void* dL_dstate,
                                void* dL_dcontrols, void* stream) {
   if (!c) return OSTRICH_EINVAL;

@@ -845,8 +845,15 @@ __global__ void __launch_bounds__(128) step_kernel(const DevScene scp, const Ste
   const DevScene& sc = ssc;
   WS<Real> w = ws_carve<Real>(smem, sc);
   const int tid = threadIdx.x, nth = blockDim.x;
-  const int world = a.world0 + blockIdx.x;
-  if (world >= a.n_worlds) return;
+  const int world = a.list ? a.list[blockIdx.x] : a.world0 + blockIdx.x;
+  if (world < 0 || world >= a.n_worlds) return;
+  const TapeLayout tl = tape_layout(sc);
+  Real* tpw = nullptr;    // this world's tape record (nullptr: the step records nothing)
+  if (a.tape) {
+    const int slot = a.list ? (a.list_slot ? a.list_slot[blockIdx.x] : -1) : 0;
+    if (slot >= 0 && (!a.list || slot < a.tape_slots))
+      tpw = reinterpret_cast<Real*>(a.tape) + ((size_t)slot * a.n_worlds + world) * tl.total;
+  }
   const int ld = a.ld, nb = sc.nb;
   const Real* sin = reinterpret_cast<const Real*>(a.state_in);
   const Real* ctl = reinterpret_cast<const Real*>(a.controls);
@@ -930,12 +937,10 @@ __global__ void __launch_bounds__(128) step_kernel(const DevScene scp, const Ste
   // the returned iterate: its Jacobian, compliance and Schur factor go to the tape
   Real mret = evaluate(sc, w, w.uk, w.lk, h);
   if (!(mret == mret) || !(fabs((double)mret) < 1e300)) status |= 2u;
-  const TapeLayout tl = tape_layout(sc);
-  const bool record = a.tape != nullptr;
-  if (record) {
+  if (tpw) {
     assemble(sc, w, h);
     factor(sc, w);
-    Real* tp = reinterpret_cast<Real*>(a.tape) + (size_t)world * tl.total;
+    Real* tp = tpw;
     for (int i = tid; i < 7 * nb; i += nth) tp[tl.off_qm + i] = w.qm[i];
     for (int i = tid; i < 6 * nb; i += nth) { tp[tl.off_um + i] = w.um[i]; tp[tl.off_u + i] = w.uk[i]; }
     for (int i = tid; i < sc.n_servo; i += nth) tp[tl.off_ubar + i] = w.ubar[i];
@@ -1110,13 +1115,15 @@ __global__ void __launch_bounds__(128) adjoint_kernel(const DevScene scp, const 
   const DevScene& sc = ssc;
   WS<Real> w = ws_carve<Real>(smem, sc);
   const int tid = threadIdx.x, nth = blockDim.x;
-  const int world = a.world0 + blockIdx.x;
-  if (world >= a.n_worlds) return;
+  const int world = a.list ? a.list[blockIdx.x] : a.world0 + blockIdx.x;
+  if (world < 0 || world >= a.n_worlds) return;
+  const int slot = a.list ? (a.list_slot ? a.list_slot[blockIdx.x] : -1) : 0;
+  if (slot < 0 || (a.list && slot >= a.tape_slots)) return;
   const int ld = a.ld, nb = sc.nb;
   const double h = a.h;
   const Real hR = Real(h);
   const TapeLayout tl = tape_layout(sc);
-  const Real* tp = reinterpret_cast<const Real*>(a.tape) + (size_t)world * tl.total;
+  const Real* tp = reinterpret_cast<const Real*>(a.tape) + ((size_t)slot * a.n_worlds + world) * tl.total;
   Src<Real> sq = {tp + tl.off_qm, 1}, su = {tp + tl.off_um, 1}, sb = {tp + tl.off_ubar, 1};
   world_setup<Real>(sc, w, sq, su, sb, h);
   const int m = w.ints[0], mc = w.ints[1];
@@ -1260,7 +1267,7 @@ cudaError_t launch_step(const DevScene& sc, const StepArgs& a, int threads, cuda
   size_t smem = ws_bytes<Real>(sc);
   cudaError_t e = ensure_smem(step_kernel<Real>, smem, done_dev, done_size);
   if (e != cudaSuccess) return e;
-  int n = a.n_worlds - a.world0;
+  int n = a.list ? a.n_list : a.n_worlds - a.world0;
   if (n <= 0) return cudaSuccess;
   step_kernel<Real><<<n, threads, smem, st>>>(sc, a);
   return cudaGetLastError();
@@ -1273,7 +1280,7 @@ cudaError_t launch_adjoint(const DevScene& sc, const AdjArgs& a, int threads, cu
   size_t smem = ws_bytes<Real>(sc);
   cudaError_t e = ensure_smem(adjoint_kernel<Real>, smem, done_dev, done_size);
   if (e != cudaSuccess) return e;
-  int n = a.n_worlds - a.world0;
+  int n = a.list ? a.n_list : a.n_worlds - a.world0;
   if (n <= 0) return cudaSuccess;
   adjoint_kernel<Real><<<n, threads, smem, st>>>(sc, a);
   return cudaGetLastError();

@@ -84,15 +84,22 @@ inline void finish_scene(DevScene& s) {
 }
 
 // Arguments of one launch of the step / adjoint kernels.
+// World selection: without a list, CTA b steps world world0 + b and records into the
+// tape slot that `tape` points at.  With a list (device arrays of gridDim entries), CTA
+// b steps world list[b] and records into slot list_slot[b] of the tape that starts at
+// `tape` (slot stride n_worlds records; -1: no record); out-of-range entries are skipped.
+// The list form launches n_list CTAs.
 struct StepArgs {
   const void* state_in; const void* controls; void* state_out; void* impulses;
   int32_t* ids; uint32_t* status; int32_t* iters; void* tape;
   int ld, n_worlds, world0; double h;
-  double* trace;   // optional diagnostic: merit of each iterate, (budget + 2) per world
+  double* trace = nullptr;   // optional diagnostic: merit of each iterate, (budget + 2) per world
+  const int32_t* list = nullptr; const int32_t* list_slot = nullptr; int n_list = 0, tape_slots = 0;
 };
 struct AdjArgs {
   const void* tape; const void* dL_dnext; void* dL_dstate; void* dL_dcontrols;
   int ld, n_worlds, world0; double h;
+  const int32_t* list = nullptr; const int32_t* list_slot = nullptr; int n_list = 0, tape_slots = 0;
 };
 
 // Tape record of one world for one step: inputs, returned iterate and the Schur factor

@@ -68,6 +68,9 @@ def lib():
         L.ostrich_set_threads.argtypes = [_vp, ctypes.c_int]
         L.ostrich_step.argtypes = [_vp, _vp, _vp, ctypes.c_double, _vp, _vp, _vp, _vp, _vp, ctypes.c_int, _vp]
         L.ostrich_adjoint.argtypes = [_vp, ctypes.c_int, _vp, ctypes.c_double, _vp, _vp, _vp]
+        L.ostrich_step_list.argtypes = [_vp, _vp, _vp, ctypes.c_double, _vp, _vp, _vp, _vp, _vp, _vp, _vp,
+                                        ctypes.c_int, _vp]
+        L.ostrich_adjoint_list.argtypes = [_vp, _vp, ctypes.c_double, _vp, _vp, _vp, _vp, ctypes.c_int, _vp]
         L.ostrich_tape_clear.argtypes = [_vp]
         L.ostrich_debug_trace.argtypes = [_vp, _vp]
         L.ostrich_debug_trace.restype = ctypes.c_int
@@ -79,7 +82,7 @@ def lib():
         L.ostrich_step_adjoint_noalloc.argtypes = [ctypes.POINTER(SceneDesc), ctypes.POINTER(SolverCfg), ctypes.c_int,
                                                    ctypes.c_int, _vp, _vp, ctypes.c_double, _vp, _vp, _vp, _vp, _vp]
         for name in ("ostrich_layout", "ostrich_set_threads", "ostrich_step", "ostrich_adjoint", "ostrich_tape_clear",
-                     "ostrich_step_adjoint_noalloc"):
+                     "ostrich_step_adjoint_noalloc", "ostrich_step_list", "ostrich_adjoint_list"):
             getattr(L, name).restype = ctypes.c_int
         _lib = L
     return _lib
@@ -123,7 +126,16 @@ def solver_cfg(cfg: "S.SolverConfig") -> SolverCfg:
 
 
 def _ptr(t):
-    return None if t is None else ctypes.c_void_p(t.data_ptr())
+    """Device pointer of a dense CUDA tensor.  The library reads and writes arrays as
+    packed [rows, ld] (world index fastest), so a strided view would be misread: it is
+    refused rather than copied (a copy would also break in-place outputs)."""
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError("libostrich takes device tensors; got a host tensor")
+    if not t.is_contiguous():
+        raise ValueError(f"libostrich takes contiguous arrays; got shape {tuple(t.shape)} strides {t.stride()}")
+    return ctypes.c_void_p(t.data_ptr())
 
 
 def _stream(stream):
@@ -189,6 +201,18 @@ class Context:
     def ostrich_adjoint(self, tape_slot, dL_dnext, h, dL_dstate, dL_dcontrols=None, stream=None):
         self._check(lib().ostrich_adjoint(self._h, int(tape_slot), _ptr(dL_dnext), float(h), _ptr(dL_dstate),
                                           _ptr(dL_dcontrols), _stream(stream)), "ostrich_adjoint")
+
+    def ostrich_step_list(self, state_in, controls, h, state_out, worlds, tape_slots=None, impulses=None, ids=None,
+                          status=None, iters=None, stream=None):
+        self._check(lib().ostrich_step_list(self._h, _ptr(state_in), _ptr(controls), float(h), _ptr(state_out),
+                                            _ptr(impulses), _ptr(ids), _ptr(status), _ptr(iters), _ptr(worlds),
+                                            _ptr(tape_slots), int(worlds.numel()), _stream(stream)),
+                    "ostrich_step_list")
+
+    def ostrich_adjoint_list(self, dL_dnext, h, dL_dstate, worlds, tape_slots, dL_dcontrols=None, stream=None):
+        self._check(lib().ostrich_adjoint_list(self._h, _ptr(dL_dnext), float(h), _ptr(dL_dstate), _ptr(dL_dcontrols),
+                                               _ptr(worlds), _ptr(tape_slots), int(worlds.numel()), _stream(stream)),
+                    "ostrich_adjoint_list")
 
     def ostrich_debug_trace(self, merits):
         self._check(lib().ostrich_debug_trace(self._h, _ptr(merits)), "ostrich_debug_trace")

@@ -20,3 +20,30 @@ def test_library_exports_every_declared_symbol():
     assert "ostrich_step" in names and "ostrich_adjoint" in names
     missing = [n for n in names if not hasattr(lib, n)]
     assert not missing, f"declared but not exported: {missing}"
+
+
+def test_binding_refuses_host_and_strided_arrays():
+    """The library reads packed [rows, ld] device arrays; a strided view or a host
+    tensor is refused instead of being misread."""
+    import pytest
+    from paper_2609_08800_gb300.ostrich import _ptr
+
+    class Fake:
+        def __init__(self, cuda, contig):
+            self.is_cuda, self._c, self.shape = cuda, contig, (4, 3)
+
+        def is_contiguous(self):
+            return self._c
+
+        def stride(self):
+            return (1, 4)
+
+        def data_ptr(self):
+            return 4096
+
+    assert _ptr(None) is None
+    assert _ptr(Fake(True, True)).value == 4096
+    with pytest.raises(ValueError):
+        _ptr(Fake(False, True))
+    with pytest.raises(ValueError):
+        _ptr(Fake(True, False))

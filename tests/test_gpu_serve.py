@@ -1,0 +1,137 @@
+"""Serving loop and the world-list entry points behind it.
+
+* ostrich_step_list / ostrich_adjoint_list on a permuted subset of worlds, in place,
+  give bit-identical results to the full launches, and leave other worlds untouched.
+* A request's results are the same (bit for bit) served alone and served among other
+  requests that arrive around it, of both scene kinds and both modes.
+* A served forward+adjoint request equals the autograd rollout of the same inputs
+  with checkpointing every 10 steps (same kernels, same threads per world).
+* A short Poisson stream completes and reports finite p50/p99 latencies.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from paper_2609_08800_gb300 import scenes as S  # noqa: E402
+
+H = 0.1
+
+
+@pytest.fixture(scope="module")
+def M():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_2609_08800_gb300 import ostrich
+    ostrich.lib()
+    return ostrich
+
+
+@pytest.fixture(scope="module")
+def pools(M):
+    from paper_2609_08800_gb300 import serve
+    cfg = S.SolverConfig(tol=1e-4)
+    return [serve.Pool("box", cfg, 1024, threads=32), serve.Pool("robot", cfg, 1024, threads=64)]
+
+
+def test_list_entry_points_match_full_launch(M):
+    sc = S.robot_box_scene()
+    W = 200
+    ctx = M.Context(sc, S.SolverConfig(tol=1e-4), W, dtype="f32", tape_slots=2)
+    s0 = torch.tensor(S.robot_box_states(sc, W, seed=11), dtype=torch.float32, device="cuda")
+    ub = torch.tensor(S.random_controls(sc.n_servos, W, seed=11, low=-3, high=3), dtype=torch.float32, device="cuda")
+    g = torch.tensor(np.random.default_rng(2).normal(size=s0.shape), dtype=torch.float32, device="cuda")
+    full = torch.empty_like(s0)
+    ctx.ostrich_step(s0, ub, H, full, tape_slot=0)
+    ds_full = torch.empty_like(s0)
+    du_full = torch.zeros(sc.n_servos, W, dtype=torch.float32, device="cuda")
+    ctx.ostrich_adjoint(0, g, H, ds_full, du_full)
+    sel = torch.arange(W - 1, -1, -3, dtype=torch.int32, device="cuda")          # every third world, reversed
+    slots = torch.ones_like(sel)
+    st = s0.clone()
+    ctx.ostrich_step_list(st, ub, H, st, sel, slots)                              # in place, record in slot 1
+    gg = g.clone()
+    du = torch.zeros_like(du_full)
+    ctx.ostrich_adjoint_list(gg, H, gg, sel, slots, du)
+    torch.cuda.synchronize()
+    idx = sel.long()
+    other = torch.ones(W, dtype=torch.bool, device="cuda")
+    other[idx] = False
+    assert torch.equal(st[:, idx], full[:, idx])
+    assert torch.equal(st[:, other], s0[:, other])
+    assert torch.equal(gg[:13 * sc.n_bodies, idx], ds_full[:13 * sc.n_bodies, idx])
+    assert torch.equal(du[:, idx], du_full[:, idx])
+    assert torch.equal(gg[:, other], g[:, other])
+    ctx.close()
+
+
+def _req(serve, rid, kind, n, T, adjoint, arrival, seed):
+    return serve.Request(rid=rid, kind=kind, n=n, T=T, adjoint=adjoint, arrival=arrival, seed=seed)
+
+
+def _serve(serve, pools, reqs):
+    done = serve.Server(pools).run(reqs)
+    assert len(done) == len(reqs)
+    return {r.rid: r for r in done}
+
+
+def _same(a, b):
+    assert torch.equal(a.final_state, b.final_state)
+    assert torch.equal(a.loss, b.loss)
+    if a.adjoint:
+        assert torch.equal(a.dstate0, b.dstate0)
+        if a.dcontrols is not None:
+            assert torch.equal(a.dcontrols, b.dcontrols)
+
+
+def test_request_same_alone_and_in_mix(pools):
+    from paper_2609_08800_gb300 import serve
+    targets = [("robot", 37, 35, True, 5), ("box", 20, 27, False, 6), ("robot", 9, 21, False, 7),
+               ("box", 13, 33, True, 8)]
+    alone = {}
+    for k, (kind, n, T, adj, seed) in enumerate(targets):
+        alone.update(_serve(serve, pools, [_req(serve, k, kind, n, T, adj, 0.0, seed)]))
+    mix = [_req(serve, k, kind, n, T, adj, 0.01 * k, seed) for k, (kind, n, T, adj, seed) in enumerate(targets)]
+    rng = np.random.default_rng(0)
+    for j in range(12):
+        kind = ("box", "robot")[j % 2]
+        mix.append(_req(serve, 100 + j, kind, int(rng.integers(1, 200)), int(rng.integers(20, 60)), bool(j % 3),
+                        float(rng.uniform(0, 0.05)), 1000 + j))
+    served = _serve(serve, pools, mix)
+    for k in range(len(targets)):
+        _same(alone[k], served[k])
+
+
+def test_served_gradient_matches_autograd_rollout(pools):
+    from paper_2609_08800_gb300 import serve
+    from paper_2609_08800_gb300.autograd import CudaEngine, rollout
+    n, T = 23, 34
+    r = _serve(serve, pools, [_req(serve, 0, "robot", n, T, True, 0.0, 42)])[0]
+    sc = S.robot_box_scene()
+    s0, ctl = serve.request_inputs("robot", sc, n, T, 42, H)
+    eng = CudaEngine(sc, S.SolverConfig(tol=1e-4), n, H, slots=10, threads=64)
+    s0t = torch.tensor(s0, dtype=torch.float32, device="cuda", requires_grad=True)
+    ct = torch.tensor(ctl, dtype=torch.float32, device="cuda", requires_grad=True)
+    traj = rollout(s0t, ct, eng, segment=10)
+    loss = ((traj[-1][0] - 3.0) ** 2 + traj[-1][1] ** 2).sum()
+    loss.backward()
+    torch.cuda.synchronize()
+    assert torch.equal(r.final_state, traj[-1].detach().cpu())
+    nb13 = 13 * sc.n_bodies
+    assert torch.equal(r.dstate0[:nb13], s0t.grad[:nb13].cpu())
+    assert torch.equal(r.dcontrols, ct.grad.cpu())
+    eng.close()
+
+
+def test_poisson_stream_completes(pools):
+    from paper_2609_08800_gb300 import serve
+    reqs = serve.poisson_stream(200, 0.25, seed=3, kinds=("box", "robot"), max_worlds=64, horizon=(20, 40))
+    import time
+    t0 = time.perf_counter()
+    done = serve.Server(pools).run(reqs)
+    wall = time.perf_counter() - t0
+    st = serve.summarize(done, wall)
+    assert st["requests"] == len(reqs)
+    assert 0 < st["p50_s"] <= st["p99_s"] < 60
+    assert all(np.isfinite(r.final_state.numpy()).all() for r in done)

@@ -249,6 +249,8 @@ def run_ours(args, rank, world_size, local_rank):
         out["e2e"] = run_e2e(args, ctx, chunk, states, controls, g, torch)
         out["plain_form"] = run_plain(args, scene, cfg, states, controls, g, torch)
         out["cpu_baseline"] = run_cpu_baseline(args)
+        if args.serve_seconds > 0:
+            out["serving"] = run_serving(args, torch)
     ctx.close()
     return out
 
@@ -343,6 +345,38 @@ def run_plain(args, scene, cfg, states, controls, g, torch):
             "note": "same kernels, one world per launch (W = 1), host loop over worlds"}
 
 
+def run_serving(args, torch):
+    """Poisson request stream (mean 200 requests/s; 1-512 worlds log-uniform; horizon
+    20-200 steps; box-drop and robot-over-box scenes; half forward-only, half
+    forward+adjoint) served by continuous batching, then the same stream by a FIFO
+    queue that serves one request at a time."""
+    import time as _time
+    from paper_2609_08800_gb300 import serve, tune
+    cfg = S.SolverConfig(tol=FP32_TOL)
+    pools = []
+    for kind in ("box", "robot"):
+        p = serve.Pool(kind, cfg, 8192, h=H, K=CHUNK, t_max=200, hbm_share=0.25)
+        tune.apply(p.ctx)
+        pools.append(p)
+    out = {"stream": f"Poisson {args.serve_rate:g} req/s over {args.serve_seconds:g} s, seed 0, "
+                     "1-512 worlds (log-uniform), T 20-200, box-drop + robot-over-box, half with adjoint"}
+    warm = serve.poisson_stream(args.serve_rate, 0.05, seed=99, max_worlds=64, horizon=(20, 25))
+    serve.Server(pools).run(warm)
+    for name, fifo in (("continuous_batching", False), ("fifo_queue", True)):
+        reqs = serve.poisson_stream(args.serve_rate, args.serve_seconds, seed=0)
+        srv = serve.Server(pools, fifo=fifo)
+        t0 = _time.perf_counter()
+        done = srv.run(reqs, t0=t0)
+        wall = _time.perf_counter() - t0
+        st = serve.summarize(done, wall)
+        st["wall_s"] = wall
+        st["ticks"] = srv.tick
+        out[name] = st
+    for p in pools:
+        p.ctx.close()
+    return out
+
+
 def run_cpu_baseline(args, impl_line=False):
     """FP64 oracle on the host: forward + adjoint of a bounded sample of the workload."""
     from oracle import oracle as O
@@ -403,6 +437,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--worlds", type=int, default=8192)
+    ap.add_argument("--serve-seconds", type=float, default=0.5, help="arrival window of the serving stream (0: skip)")
+    ap.add_argument("--serve-rate", type=float, default=200.0)
     ap.add_argument("--threads", type=int, default=None, help="threads per world (default: autotuner table)")
     ap.add_argument("--plain-worlds", type=int, default=512)
     ap.add_argument("--cpu-worlds", type=int, default=24)

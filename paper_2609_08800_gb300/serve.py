@@ -202,9 +202,12 @@ class Pool:
 class Server:
     """Continuous-batching loop over a set of pools."""
 
-    def __init__(self, pools, max_bypass=0.5, clock=time.perf_counter):
+    def __init__(self, pools, max_bypass=0.5, clock=time.perf_counter, fifo=False):
+        """fifo=True serves one request at a time in arrival order (a queue without
+        batching), the baseline continuous batching is measured against."""
         self.pools = {p.kind: p for p in pools}
         self.max_bypass = max_bypass
+        self.fifo = fifo
         self.clock = clock
         self.queue = []
         self.inflight = []          # requests whose results are being copied out
@@ -214,6 +217,11 @@ class Server:
 
     # ---- admission -------------------------------------------------------------------
     def _admit(self, now):
+        if self.fifo:
+            if self.queue and not any(p.active for p in self.pools.values()):
+                r = self.queue.pop(0)
+                self._start(self.pools[r.kind], r, now)
+            return
         blocked = set()
         keep = []
         for r in self.queue:

@@ -100,11 +100,17 @@ class Oracle:
         self.n_slots, self.m_max, self.n_state, self.n_servo = map(int, out)
         assert self.n_state == scene.n_state and self.m_max == scene.m_max
 
+    def _state(self, state):
+        state = np.ascontiguousarray(state, dtype=np.float64)
+        if state.shape != (self.n_state,):
+            raise ValueError(f"state of shape {state.shape}; this scene's layout has {self.n_state} entries")
+        return state
+
     def _common(self):
         return _d(self.sp), self.hts.ctypes.data_as(_fp), _d(self.cp)
 
     def step(self, state, ubar, h):
-        state = np.ascontiguousarray(state, dtype=np.float64)
+        state = self._state(state)
         ubar = np.ascontiguousarray(np.atleast_1d(ubar), dtype=np.float64) if self.n_servo else np.zeros(1)
         out = np.zeros(self.n_state); imp = np.zeros(self.m_max)
         ids = np.zeros(max(self.n_slots, 1), dtype=np.int32)
@@ -117,7 +123,7 @@ class Oracle:
                     iters=int(info[0]), residual=float(info[1]), ret_k=int(info[2]), rows=int(info[3]))
 
     def step_adjoint(self, state, ubar, h, dL_dnext, mode=ADJ_PAPER):
-        state = np.ascontiguousarray(state, dtype=np.float64)
+        state = self._state(state)
         ubar = np.ascontiguousarray(np.atleast_1d(ubar), dtype=np.float64) if self.n_servo else np.zeros(1)
         g = np.ascontiguousarray(dL_dnext, dtype=np.float64)
         out = np.zeros(self.n_state); imp = np.zeros(self.m_max)
@@ -133,7 +139,7 @@ class Oracle:
                     residual=float(info[1]), dstate=dstate, dubar=dubar[:self.n_servo])
 
     def contacts(self, state, h):
-        state = np.ascontiguousarray(state, dtype=np.float64)
+        state = self._state(state)
         n = max(self.n_slots, 1)
         act = np.zeros(n, dtype=np.int32); ids = np.zeros(n, dtype=np.int32); nd = np.zeros(4 * n)
         lib().oracle_contacts(*self._common(), _d(state), float(h), act.ctypes.data_as(_ip),
@@ -141,7 +147,7 @@ class Oracle:
         return act[:self.n_slots], ids[:self.n_slots], nd[:4 * self.n_slots].reshape(-1, 4)
 
     def rows(self, state, ubar, h, u, lam, max_rows=512):
-        state = np.ascontiguousarray(state, dtype=np.float64)
+        state = self._state(state)
         ubar = np.ascontiguousarray(np.atleast_1d(ubar), dtype=np.float64) if self.n_servo else np.zeros(1)
         u = np.ascontiguousarray(u, dtype=np.float64); lam = np.ascontiguousarray(lam, dtype=np.float64)
         meta = np.zeros(4 * max_rows, dtype=np.int32)

@@ -150,6 +150,8 @@ bool parse_scene(const double* p, const float* heights, OScene& s) {
     jt.kp = q[20];
   }
   s.nf = s.env == ENV_PLANE ? 1 : (s.env == ENV_BOX ? 4 : 8);
+  // heightmap: at least one 2 x 2 cell block, face ids below 2^20 (contact id field)
+  if (s.env == ENV_HEIGHTMAP && (!heights || s.hn < 3 || s.hn > 724 || !(s.hsp > 0))) return false;
   s.n_servo = 0;
   for (int i = 0; i < s.nj; ++i) s.servo_of_joint[i] = s.j[i].kp > 0 ? s.n_servo++ : -1;
   s.n_slots = 0;
@@ -249,6 +251,77 @@ Cand box_feature(const OScene& s, int f, F3 c, F3 a, float r) {
   return k;
 }
 
+// ---------------------------------------------------------------------------
+// Heightmap terrain (Sec. IV-D): a triangle mesh over a regular grid.  Vertex (i, j)
+// sits at (ox + i sp, oy + j sp, H[i n + j]); cell (i, j) is split along its
+// (i, j)-(i+1, j+1) diagonal into face 0 {(i,j), (i+1,j), (i+1,j+1)} and face 1
+// {(i,j), (i+1,j+1), (i,j+1)}; face id = 2 ((n - 1) i + j) + t.  Everything here is
+// FP32 with one rounding per operation, like the other contact predicates.
+// ---------------------------------------------------------------------------
+inline float hm_x(const OScene& s, int i) { return (float)s.hox + (float)i * (float)s.hsp; }
+inline float hm_y(const OScene& s, int j) { return (float)s.hoy + (float)j * (float)s.hsp; }
+inline F3 hm_vertex(const OScene& s, int i, int j) { return f3(hm_x(s, i), hm_y(s, j), s.heights[(size_t)i * s.hn + j]); }
+
+// plane (n, d) of a face, n upward (the cross product of the two edges from vertex
+// (i, j) in the order listed above), normalised
+inline void hm_face(const OScene& s, int i, int j, int t, F3& n, float& d) {
+  F3 A = hm_vertex(s, i, j);
+  F3 B = t == 0 ? hm_vertex(s, i + 1, j) : hm_vertex(s, i + 1, j + 1);
+  F3 C = t == 0 ? hm_vertex(s, i + 1, j + 1) : hm_vertex(s, i, j + 1);
+  F3 nr = fcross(fsub(B, A), fsub(C, A));
+  float inv = 1.0f / std::sqrt(fdot(nr, nr));
+  n = fscale(nr, inv);
+  d = fdot(n, A);
+}
+
+// cell under the horizontal position of x, clamped to the grid
+inline void hm_cell(const OScene& s, F3 x, int& i, int& j) {
+  float fi = std::floor((x.x - (float)s.hox) / (float)s.hsp);
+  float fj = std::floor((x.y - (float)s.hoy) / (float)s.hsp);
+  float top = (float)(s.hn - 2);
+  i = fi >= 0.0f ? (fi <= top ? (int)fi : s.hn - 2) : 0;
+  j = fj >= 0.0f ? (fj <= top ? (int)fj : s.hn - 2) : 0;
+}
+
+// does the horizontal position of x lie on face (i, j, t)?  (edges inclusive)
+inline bool hm_on_face(const OScene& s, F3 x, int i, int j, int t) {
+  float x0 = hm_x(s, i), x1 = hm_x(s, i + 1), y0 = hm_y(s, j), y1 = hm_y(s, j + 1);
+  if (!(x.x >= x0 && x.x <= x1 && x.y >= y0 && x.y <= y1)) return false;
+  float u = x.x - x0, v = x.y - y0;
+  return t == 0 ? u >= v : u <= v;
+}
+
+// Candidate faces of one rim (centre c, axle a, radius r): the rim's lowest point
+// picks a face; the rim's deepest point against that face's plane picks the centre
+// cell of a 3 x 3 block; each face of the block whose own deepest rim point lies on
+// the face is a candidate, in scan order (cell row i, cell column j, face t), at most
+// `cap` of them (more sets `overflow`).
+struct HmCand { F3 n; float d; int face; F3 x; };
+int hm_rim_candidates(const OScene& s, F3 c, F3 a, float r, HmCand* out, int cap, bool& overflow) {
+  F3 xl = rim_deepest(c, a, r, f3(0.0f, 0.0f, 1.0f));
+  int i, j;
+  hm_cell(s, xl, i, j);
+  int t = (xl.x - hm_x(s, i)) >= (xl.y - hm_y(s, j)) ? 0 : 1;
+  F3 n0; float d0;
+  hm_face(s, i, j, t, n0, d0);
+  hm_cell(s, rim_deepest(c, a, r, n0), i, j);
+  int k = 0;
+  for (int ii = i - 1; ii <= i + 1; ++ii)
+    for (int jj = j - 1; jj <= j + 1; ++jj) {
+      if (ii < 0 || jj < 0 || ii > s.hn - 2 || jj > s.hn - 2) continue;
+      for (int tt = 0; tt < 2; ++tt) {
+        F3 n; float d;
+        hm_face(s, ii, jj, tt, n, d);
+        F3 x = rim_deepest(c, a, r, n);
+        if (!hm_on_face(s, x, ii, jj, tt)) continue;
+        if (k == cap) { overflow = true; continue; }
+        out[k].n = n; out[k].d = d; out[k].face = 2 * ((s.hn - 1) * ii + jj) + tt; out[k].x = x;
+        ++k;
+      }
+    }
+  return k;
+}
+
 // Generate the slot table for one world at q-.  Activation: a candidate is active
 // when its signed distance, advanced over one step with the predicted approach
 // velocity (u- plus one step of gravity), is below the margin.
@@ -291,7 +364,18 @@ void generate_contacts(const OScene& s, const OCfg& cfg, const double* qm, const
       for (int rim = 0; rim < 2; ++rim) {
         F3 c = fadd(p, frot(q, f3(0.0f, rim ? hw : -hw, 0.0f)));
         if (s.env == ENV_HEIGHTMAP) {
-          // handled by the heightmap routine below
+          HmCand cand[8];
+          bool over = false;
+          int nc = hm_rim_candidates(s, c, a, r, cand, s.nf, over);
+          if (over) status |= 4u;
+          for (int f = 0; f < s.nf; ++f) {
+            Contact& ct = out[s.slot_base[b] + rim * s.nf + f];
+            ct.body = b; ct.kind = 1; ct.rim = rim; ct.ftype = 0; ct.active = 0; ct.id = -1;
+            if (f >= nc) { ct.feature = -1; continue; }
+            ct.feature = cand[f].face;
+            ct.n[0] = cand[f].n.x; ct.n[1] = cand[f].n.y; ct.n[2] = cand[f].n.z; ct.d = cand[f].d;
+            if (predicate(cand[f].x, cand[f].n, cand[f].d)) { ct.active = 1; ct.id = (b << 24) | (rim << 20) | cand[f].face; }
+          }
           continue;
         }
         for (int f = 0; f < s.nf; ++f) {

@@ -27,6 +27,11 @@ struct ostrich_ctx {
   std::vector<double> slot_h;
   double* trace = nullptr;
   char err[512] = {0};
+  // device memory is released with the context, on every path out of ostrich_create too
+  ~ostrich_ctx() {
+    if (tape) cudaFree(tape);
+    if (d_heights) cudaFree(d_heights);
+  }
 };
 
 static ostrich_status fail(ostrich_ctx* c, ostrich_status s, const char* msg) {
@@ -63,13 +68,20 @@ ostrich_status ostrich_create(const ostrich_scene_desc* d, const ostrich_solver_
   for (int i = 0; i < 5; ++i) s.box[i] = d->box[i];
   s.hn = d->hm_n; s.hsp = d->hm_spacing; s.hox = d->hm_origin[0]; s.hoy = d->hm_origin[1];
   s.nf = s.env == ost::ENV_PLANE ? 1 : (s.env == ost::ENV_BOX ? 4 : 8);
+  if (s.env != ost::ENV_PLANE && s.env != ost::ENV_BOX && s.env != ost::ENV_HEIGHTMAP) { delete c; return OSTRICH_EINVAL; }
   if (s.env == ost::ENV_HEIGHTMAP) {
-    // terrain contact generation is not part of this build of the library
-    std::snprintf(c->err, sizeof(c->err), "heightmap environment not supported by this library build");
-    ostrich_ctx* keep = c;
-    *out = nullptr;
-    delete keep;
-    return OSTRICH_EINVAL;
+    // at least one 2 x 2 block of cells; face ids must fit the 20-bit field of a contact id
+    if (!d->heights || s.hn < 3 || s.hn > 724 || !(s.hsp > 0)) { delete c; return OSTRICH_EINVAL; }
+    size_t bytes = (size_t)s.hn * s.hn * sizeof(float);
+    void* hp = nullptr;
+    if (cudaMalloc(&hp, bytes) != cudaSuccess) { cudaGetLastError(); delete c; return OSTRICH_ENOMEM; }
+    c->d_heights = static_cast<float*>(hp);
+    if (cudaMemcpy(c->d_heights, d->heights, bytes, cudaMemcpyHostToDevice) != cudaSuccess) {
+      cudaGetLastError();
+      delete c;
+      return OSTRICH_ECUDA;
+    }
+    s.heights = c->d_heights;
   }
   int slots = 0;
   for (int b = 0; b < s.nb; ++b) {
@@ -250,8 +262,6 @@ const char* ostrich_last_error(const ostrich_ctx* c) { return c ? c->err : "null
 
 void ostrich_destroy(ostrich_ctx* c) {
   if (!c) return;
-  if (c->tape) cudaFree(c->tape);
-  if (c->d_heights) cudaFree(c->d_heights);
   delete c;
 }
 

@@ -87,6 +87,107 @@ __device__ __forceinline__ Cand rbox_feature(const DevScene& s, int f, f3 c, f3 
 // Per-slot activation result
 struct SlotAct { int active, id, ftype; float n[3], d, ex, ez; };
 
+// Velocity-advanced activation test of one candidate point x on plane (n, d) of body
+// b (position p, velocity v, angular velocity w): the signed distance, advanced over
+// one step with the predicted approach speed (plus one step of gravity), below margin.
+__device__ __forceinline__ bool rpredicate(f3 x, f3 n, float d, f3 p, f3 v, f3 w, float hf, float hg, float margin) {
+  f3 rr = rsub3(x, p);
+  f3 cw = rcross(w, rr);
+  f3 vp = mkf3(radd(v.x, cw.x), radd(v.y, cw.y), radd(radd(v.z, hg), cw.z));
+  float dist = rsub(rdot(n, x), d);
+  float app = rdot(n, vp);
+  float pred = radd(dist, rmul(hf, app < 0.0f ? app : 0.0f));
+  return pred < margin;
+}
+
+// ---------------------------------------------------------------------------
+// Heightmap terrain (Sec. IV-D): a triangle mesh over a regular grid.  Vertex (i, j)
+// sits at (ox + i sp, oy + j sp, H[i n + j]); cell (i, j) is split along its
+// (i, j)-(i+1, j+1) diagonal into face 0 {(i,j), (i+1,j), (i+1,j+1)} and face 1
+// {(i,j), (i+1,j+1), (i,j+1)}; face id = 2 ((n - 1) i + j) + t.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float hm_x(const DevScene& s, int i) { return radd((float)s.hox, rmul((float)i, (float)s.hsp)); }
+__device__ __forceinline__ float hm_y(const DevScene& s, int j) { return radd((float)s.hoy, rmul((float)j, (float)s.hsp)); }
+__device__ __forceinline__ f3 hm_vertex(const DevScene& s, int i, int j) {
+  return mkf3(hm_x(s, i), hm_y(s, j), __ldg(s.heights + (size_t)i * s.hn + j));
+}
+
+// plane (n, d) of a face: n = normalised cross product of the two edges from (i, j)
+__device__ __forceinline__ void hm_face(const DevScene& s, int i, int j, int t, f3& n, float& d) {
+  f3 A = hm_vertex(s, i, j);
+  f3 B = t == 0 ? hm_vertex(s, i + 1, j) : hm_vertex(s, i + 1, j + 1);
+  f3 C = t == 0 ? hm_vertex(s, i + 1, j + 1) : hm_vertex(s, i, j + 1);
+  f3 nr = rcross(rsub3(B, A), rsub3(C, A));
+  float inv = __fdiv_rn(1.0f, __fsqrt_rn(rdot(nr, nr)));
+  n = rscale(nr, inv);
+  d = rdot(n, A);
+}
+
+// cell under the horizontal position of x, clamped to the grid
+__device__ __forceinline__ void hm_cell(const DevScene& s, f3 x, int& i, int& j) {
+  float fi = floorf(__fdiv_rn(rsub(x.x, (float)s.hox), (float)s.hsp));
+  float fj = floorf(__fdiv_rn(rsub(x.y, (float)s.hoy), (float)s.hsp));
+  float top = (float)(s.hn - 2);
+  i = fi >= 0.0f ? (fi <= top ? (int)fi : s.hn - 2) : 0;
+  j = fj >= 0.0f ? (fj <= top ? (int)fj : s.hn - 2) : 0;
+}
+
+// does the horizontal position of x lie on face (i, j, t)?  (edges inclusive)
+__device__ __forceinline__ bool hm_on_face(const DevScene& s, f3 x, int i, int j, int t) {
+  float x0 = hm_x(s, i), x1 = hm_x(s, i + 1), y0 = hm_y(s, j), y1 = hm_y(s, j + 1);
+  if (!(x.x >= x0 && x.x <= x1 && x.y >= y0 && x.y <= y1)) return false;
+  float u = rsub(x.x, x0), v = rsub(x.y, y0);
+  return t == 0 ? u >= v : u <= v;
+}
+
+// Activation of the nf slots of one rim of wheel b on the heightmap.  The rim's lowest
+// point picks a face; the rim's deepest point against that face's plane picks the
+// centre cell of a 3 x 3 block; each face of the block whose own deepest rim point lies
+// on the face is a candidate, in scan order (cell row, cell column, face), filling the
+// rim's slots; returns true when candidates were left over (more than nf).
+__device__ __forceinline__ bool activate_rim_hm(const DevScene& s, int b, int rim, const float* q7, const float* u6,
+                                                double h, SlotAct* out) {
+  float hf = (float)h, hg = rmul(hf, (float)s.g), margin = (float)s.margin;
+  const float* q = q7 + 3;
+  f3 p = mkf3(q7[0], q7[1], q7[2]);
+  f3 v = mkf3(u6[0], u6[1], u6[2]);
+  f3 w = mkf3(u6[3], u6[4], u6[5]);
+  float r = (float)s.radius[b], hw = (float)s.hw[b];
+  f3 a = rrot(q, mkf3(0.f, 1.f, 0.f));
+  f3 c = radd3(p, rrot(q, mkf3(0.f, rim ? hw : -hw, 0.f)));
+  for (int f = 0; f < s.nf; ++f) {
+    SlotAct& o = out[f];
+    o.active = 0; o.id = -1; o.ftype = 0; o.n[0] = 0.f; o.n[1] = 0.f; o.n[2] = 1.f; o.d = 0.f; o.ex = 0.f; o.ez = 0.f;
+  }
+  f3 xl = rrim_deepest(c, a, r, mkf3(0.f, 0.f, 1.f));
+  int i, j;
+  hm_cell(s, xl, i, j);
+  int t = rsub(xl.x, hm_x(s, i)) >= rsub(xl.y, hm_y(s, j)) ? 0 : 1;
+  f3 n0; float d0;
+  hm_face(s, i, j, t, n0, d0);
+  hm_cell(s, rrim_deepest(c, a, r, n0), i, j);
+  int k = 0;
+  bool over = false;
+  for (int ii = i - 1; ii <= i + 1; ++ii)
+    for (int jj = j - 1; jj <= j + 1; ++jj) {
+      if (ii < 0 || jj < 0 || ii > s.hn - 2 || jj > s.hn - 2) continue;
+      for (int tt = 0; tt < 2; ++tt) {
+        f3 n; float d;
+        hm_face(s, ii, jj, tt, n, d);
+        f3 x = rrim_deepest(c, a, r, n);
+        if (!hm_on_face(s, x, ii, jj, tt)) continue;
+        if (k == s.nf) { over = true; continue; }
+        SlotAct& o = out[k++];
+        o.n[0] = n.x; o.n[1] = n.y; o.n[2] = n.z; o.d = d;
+        if (rpredicate(x, n, d, p, v, w, hf, hg, margin)) {
+          o.active = 1;
+          o.id = (b << 24) | (rim << 20) | (2 * ((s.hn - 1) * ii + jj) + tt);
+        }
+      }
+    }
+  return over;
+}
+
 // Activation of slot `sl` (global slot index) of one world, from the FP32 state of its body.
 // q7: position + quaternion, u6: linear + angular velocity (world frame).
 __device__ __forceinline__ SlotAct activate_slot(const DevScene& s, int b, int local, const float* q7, const float* u6,
@@ -120,13 +221,7 @@ __device__ __forceinline__ SlotAct activate_slot(const DevScene& s, int b, int l
     o.id = (b << 24) | (rim << 20) | f;
   }
   o.n[0] = n.x; o.n[1] = n.y; o.n[2] = n.z; o.d = d;
-  f3 rr = rsub3(x, p);
-  f3 cw = rcross(w, rr);
-  f3 vp = mkf3(radd(v.x, cw.x), radd(v.y, cw.y), radd(radd(v.z, hg), cw.z));
-  float dist = rsub(rdot(n, x), d);
-  float app = rdot(n, vp);
-  float pred = radd(dist, rmul(hf, app < 0.0f ? app : 0.0f));
-  o.active = pred < margin ? 1 : 0;
+  o.active = rpredicate(x, n, d, p, v, w, hf, hg, margin) ? 1 : 0;
   if (!o.active) o.id = -1;
   return o;
 }

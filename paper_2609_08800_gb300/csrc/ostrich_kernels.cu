@@ -45,7 +45,8 @@ template <class Real> struct WS {
   Real *G, *E, *H, *S, *L, *prow, *tmp, *tmp2;
   // scratch
   Real *red;
-  int *ints;      // [0] rows, [1] contact rows, [2] items, [3] converged, [4] best_k, [5] iters, [6] status
+  int *ints;      // [0] rows, [1] contact rows, [2] items, [3] converged, [4] best_k, [5] iters, [6] status,
+                  // [7] contact-generation status bits (4: candidates beyond the slots)
   Real *scal;     // [0] merit cur, [1] best merit, [2] delta, [3] merit trial
 };
 
@@ -198,13 +199,7 @@ __device__ void world_setup(const DevScene& sc, WS<Real>& w, Src<Real> qmv, Src<
   for (int i = tid; i < sc.n_servo; i += nth) w.ubar[i] = ubarv.p[i * ubarv.stride];
   __syncthreads();
   // contact activation (FP32 predicate) and slot frames in working precision
-  for (int sl = tid; sl < sc.n_slots; sl += nth) {
-    int b = sc.slot_body[sl];
-    int local = sl - sc.slot_base[b];
-    float q7[7], u6[6];
-    for (int k = 0; k < 7; ++k) q7[k] = (float)w.qm[7 * b + k];
-    for (int k = 0; k < 6; ++k) u6[k] = (float)w.um[6 * b + k];
-    SlotAct a = activate_slot(sc, b, local, q7, u6, h);
+  auto store_slot = [&](int sl, int b, int local, const SlotAct& a) {
     w.sact[sl] = a.active; w.sid[sl] = a.id; w.sftype[sl] = a.ftype;
     w.sedge[2 * sl] = (Real)a.ex; w.sedge[2 * sl + 1] = (Real)a.ez;
     vec3<Real> n; Real d;
@@ -215,6 +210,38 @@ __device__ void world_setup(const DevScene& sc, WS<Real>& w, Src<Real> qmv, Src<
     w.sn[3 * sl] = n.x; w.sn[3 * sl + 1] = n.y; w.sn[3 * sl + 2] = n.z; w.sd[sl] = d;
     w.st1[3 * sl] = t1.x; w.st1[3 * sl + 1] = t1.y; w.st1[3 * sl + 2] = t1.z;
     w.st2[3 * sl] = t2.x; w.st2[3 * sl + 1] = t2.y; w.st2[3 * sl + 2] = t2.z;
+  };
+  if (tid == 0) w.ints[7] = 0;
+  __syncthreads();
+  if (sc.env == ENV_HEIGHTMAP) {
+    // one thread per wheel rim: the rim's candidate faces fill its nf slots in order
+    for (int e = tid; e < 2 * nb; e += nth) {
+      const int b = e >> 1, rim = e & 1;
+      if (sc.shape[b] != SHAPE_WHEEL) continue;
+      float q7[7], u6[6];
+      for (int k = 0; k < 7; ++k) q7[k] = (float)w.qm[7 * b + k];
+      for (int k = 0; k < 6; ++k) u6[k] = (float)w.um[6 * b + k];
+      SlotAct acts[8];
+      if (activate_rim_hm(sc, b, rim, q7, u6, h, acts)) atomicOr(&w.ints[7], 4);
+      for (int f = 0; f < sc.nf; ++f) store_slot(sc.slot_base[b] + rim * sc.nf + f, b, rim * sc.nf + f, acts[f]);
+    }
+    for (int sl = tid; sl < sc.n_slots; sl += nth)      // box corners (no wheel rim)
+      if (sc.shape[sc.slot_body[sl]] != SHAPE_WHEEL) {
+        int b = sc.slot_body[sl];
+        float q7[7], u6[6];
+        for (int k = 0; k < 7; ++k) q7[k] = (float)w.qm[7 * b + k];
+        for (int k = 0; k < 6; ++k) u6[k] = (float)w.um[6 * b + k];
+        store_slot(sl, b, sl - sc.slot_base[b], activate_slot(sc, b, sl - sc.slot_base[b], q7, u6, h));
+      }
+  } else {
+    for (int sl = tid; sl < sc.n_slots; sl += nth) {
+      int b = sc.slot_body[sl];
+      int local = sl - sc.slot_base[b];
+      float q7[7], u6[6];
+      for (int k = 0; k < 7; ++k) q7[k] = (float)w.qm[7 * b + k];
+      for (int k = 0; k < 6; ++k) u6[k] = (float)w.um[6 * b + k];
+      store_slot(sl, b, local, activate_slot(sc, b, local, q7, u6, h));
+    }
   }
   // bodies: world inertia at q-, external force, warm-start velocity
   for (int b = tid; b < nb; b += nth) {
@@ -937,6 +964,7 @@ __global__ void __launch_bounds__(128) step_kernel(const DevScene scp, const Ste
   // the returned iterate: its Jacobian, compliance and Schur factor go to the tape
   Real mret = evaluate(sc, w, w.uk, w.lk, h);
   if (!(mret == mret) || !(fabs((double)mret) < 1e300)) status |= 2u;
+  status |= (uint32_t)w.ints[7];
   if (tpw) {
     assemble(sc, w, h);
     factor(sc, w);

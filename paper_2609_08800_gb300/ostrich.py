@@ -95,9 +95,14 @@ def scene_desc(scene: "S.Scene") -> SceneDesc:
     for i, v in enumerate(scene.env.box):
         d.box[i] = v
     if scene.env.heights is not None:
-        d.hm_n = scene.env.heights.shape[0]
+        hts = np.ascontiguousarray(scene.env.heights, dtype=np.float32)
+        if hts.ndim != 2 or hts.shape[0] != hts.shape[1]:
+            raise ValueError("heightmap must be a square [n, n] array")
+        d.hm_n = hts.shape[0]
         d.hm_spacing = scene.env.spacing
         d.hm_origin[0], d.hm_origin[1] = scene.env.origin
+        d.heights = hts.ctypes.data_as(ctypes.POINTER(ctypes.c_float))
+        d._heights = hts          # keeps the host array alive while the descriptor is
     for i, b in enumerate(scene.bodies):
         bd = d.bodies[i]
         bd.mass = b.mass

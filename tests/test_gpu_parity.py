@@ -175,3 +175,47 @@ def test_robot_box_fp64_matches_oracle(ostrich, threads):
     g = np.random.default_rng(15).normal(size=st.shape)
     g[13 * sc.n_bodies:] = 0
     _compare(sc, cfg, ostrich, st, ub, 0.1, "f64", 1e-7, 1e-6, 1e-6, 0.8, grads=g, threads=threads)
+
+
+def _terrain_states(sc, W, seed):
+    """Robots over the Gaussian terrain, lowered 0-3 cm into contact range, with small
+    random velocities."""
+    st = S.terrain_states(sc, W, seed=seed)
+    rng = np.random.default_rng(seed)
+    nb = sc.n_bodies
+    drop = rng.uniform(0.0, 0.03, W)
+    for b in range(nb):
+        st[7 * b + 2] -= drop
+    st[7 * nb:7 * nb + 3] += rng.normal(scale=0.1, size=(3, W))
+    return st
+
+
+@pytest.mark.parametrize("seed", [0, 1])
+def test_terrain_fp32_matches_oracle(ostrich, seed):
+    """Config-4 scene: mesh terrain, FP32, truncated pull-back adjoint."""
+    sc = S.terrain_scene()
+    W = 48
+    st = _terrain_states(sc, W, seed)
+    ub = S.random_controls(sc.n_servos, W, seed=seed, low=-3, high=3)
+    # FP32 terrain steps stall at the FP32 floor (~1e-4 m/s) above the 1e-5 tolerance, so
+    # every world runs the whole budget and returns its best iterate; the IFT adjoint
+    # assumes r = 0, and at a budget of 40 one world's best iterate still left its
+    # gradient 1.1e-3 off (1e-4 at 80).
+    cfg = S.SolverConfig(budget=80, pullback=S.PULLBACK_TRUNCATED)
+    g = np.random.default_rng(seed + 20).normal(size=st.shape)
+    g[13 * sc.n_bodies:] = 0
+    _compare(sc, cfg, ostrich, st, ub, 0.1, "f32", 1e-4, 1e-3, 1e-3, 0.8, grads=g,
+             oracle_cfg=S.SolverConfig(budget=60, tol=1e-8, pullback=S.PULLBACK_TRUNCATED), floor=3e-4)
+
+
+def test_robot_box_fp64_truncated_pullback_matches_oracle(ostrich):
+    """The truncated pull-back (contact geometry held fixed within the step) of the
+    FP64 kernels against the oracle's."""
+    sc = S.robot_box_scene()
+    W = 33
+    st = S.robot_box_states(sc, W, seed=8)
+    ub = S.random_controls(sc.n_servos, W, seed=8, low=-3, high=3)
+    cfg = S.SolverConfig(budget=40, tol=1e-9, pullback=S.PULLBACK_TRUNCATED)
+    g = np.random.default_rng(18).normal(size=st.shape)
+    g[13 * sc.n_bodies:] = 0
+    _compare(sc, cfg, ostrich, st, ub, 0.1, "f64", 1e-7, 1e-6, 1e-6, 0.8, grads=g)

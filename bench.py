@@ -249,6 +249,8 @@ def run_ours(args, rank, world_size, local_rank):
         out["e2e"] = run_e2e(args, ctx, chunk, states, controls, g, torch)
         out["plain_form"] = run_plain(args, scene, cfg, states, controls, g, torch)
         out["cpu_baseline"] = run_cpu_baseline(args)
+        if args.terrain_worlds > 0:
+            out["terrain"] = run_terrain(args, torch)
         if args.serve_seconds > 0:
             out["serving"] = run_serving(args, torch)
     ctx.close()
@@ -345,25 +347,72 @@ def run_plain(args, scene, cfg, states, controls, g, torch):
             "note": "same kernels, one world per launch (W = 1), host loop over worlds"}
 
 
+def run_terrain(args, torch):
+    """Mesh terrain (Sec. IV-D): 256 x 256 heightmap, FP32, truncated pull-back.  The
+    robots are first rolled 10 steps from their drop so that they stand on the terrain;
+    then 10-step chunks (forward with the tape, then the adjoint) are timed."""
+    from paper_2609_08800_gb300 import tune
+    from paper_2609_08800_gb300.ostrich import Context
+    W = args.terrain_worlds
+    scene = S.terrain_scene()
+    states = S.terrain_states(scene, W, seed=0)
+    knots = S.spline_knots(W, n_wheels=4, n_knots=8, seed=1)
+    ctl_all = np.ascontiguousarray(np.einsum("tk,wjk->tjw", SP.basis(100, 8, H), knots)).astype(np.float32)
+    cfg = S.SolverConfig(tol=FP32_TOL, pullback=S.PULLBACK_TRUNCATED)
+    ctx = Context(scene, cfg, W, dtype="f32", tape_slots=CHUNK)
+    threads = tune.apply(ctx) or 64
+    chunk = Chunk(ctx, torch, W)
+    s0 = torch.tensor(states, dtype=torch.float32, device="cuda")
+    c0 = torch.tensor(ctl_all[:CHUNK], device="cuda")
+    c1 = torch.tensor(ctl_all[CHUNK:2 * CHUNK], device="cuda")
+    gT = torch.zeros(ctx.n_state, W, dtype=torch.float32, device="cuda")
+    chunk.run(s0, c0, gT)                               # landing
+    s1 = chunk.states[CHUNK].clone()
+    gT[0] = 2.0 * (s1[0] - 3.0)
+    gT[1] = 2.0 * s1[1]
+    for _ in range(2):
+        chunk.run(s1, c1, gT, record_ids=True)
+    torch.cuda.synchronize()
+    K = max(1, args.steps)
+    evs = [[[torch.cuda.Event(enable_timing=True) for _ in range(2)] for _ in range(CHUNK)] for _ in range(K)]
+    eva = [[[torch.cuda.Event(enable_timing=True) for _ in range(2)] for _ in range(CHUNK)] for _ in range(K)]
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    for k in range(K):
+        chunk.run(s1, c1, gT, evs[k], eva[k])
+    b.record()
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(b) / K
+    iters = np.stack([t.cpu().numpy() for t in chunk.iters])
+    ctx.close()
+    return {"workload": f"mesh_terrain_{W}_worlds_fp32_fwd_adj_chunk10_truncated_pullback", "value": W * CHUNK / (ms * 1e-3),
+            "unit": UNIT, "ms_per_chunk": ms, "threads_per_world": threads,
+            "step_ms_avg": statistics.mean(e[0].elapsed_time(e[1]) for k in range(K) for e in evs[k]),
+            "adjoint_ms_avg": statistics.mean(e[0].elapsed_time(e[1]) for k in range(K) for e in eva[k]),
+            "newton_iters_mean": float((iters & 0xFFFF).mean()), "active_rows_mean": float((iters >> 16).mean())}
+
+
 def run_serving(args, torch):
     """Poisson request stream (mean 200 requests/s; 1-512 worlds log-uniform; horizon
-    20-200 steps; box-drop and robot-over-box scenes; half forward-only, half
-    forward+adjoint) served by continuous batching, then the same stream by a FIFO
+    20-200 steps; box-drop, robot-over-box and mesh-terrain scenes; half forward-only,
+    half forward+adjoint) served by continuous batching, then the same stream by a FIFO
     queue that serves one request at a time."""
     import time as _time
     from paper_2609_08800_gb300 import serve, tune
     cfg = S.SolverConfig(tol=FP32_TOL)
     pools = []
-    for kind in ("box", "robot"):
-        p = serve.Pool(kind, cfg, 8192, h=H, K=CHUNK, t_max=200, hbm_share=0.25)
+    kinds = ("box", "robot", "terrain")
+    for kind in kinds:
+        kcfg = S.SolverConfig(tol=FP32_TOL, pullback=S.PULLBACK_TRUNCATED) if kind == "terrain" else cfg
+        p = serve.Pool(kind, kcfg, 8192, h=H, K=CHUNK, t_max=200, hbm_share=0.2)
         tune.apply(p.ctx)
         pools.append(p)
     out = {"stream": f"Poisson {args.serve_rate:g} req/s over {args.serve_seconds:g} s, seed 0, "
-                     "1-512 worlds (log-uniform), T 20-200, box-drop + robot-over-box, half with adjoint"}
-    warm = serve.poisson_stream(args.serve_rate, 0.05, seed=99, max_worlds=64, horizon=(20, 25))
+                     "1-512 worlds (log-uniform), T 20-200, box-drop + robot-over-box + mesh terrain, half with adjoint"}
+    warm = serve.poisson_stream(args.serve_rate, 0.05, seed=99, kinds=kinds, max_worlds=64, horizon=(20, 25))
     serve.Server(pools).run(warm)
     for name, fifo in (("continuous_batching", False), ("fifo_queue", True)):
-        reqs = serve.poisson_stream(args.serve_rate, args.serve_seconds, seed=0)
+        reqs = serve.poisson_stream(args.serve_rate, args.serve_seconds, seed=0, kinds=kinds)
         srv = serve.Server(pools, fifo=fifo)
         t0 = _time.perf_counter()
         done = srv.run(reqs, t0=t0)
@@ -437,6 +486,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--worlds", type=int, default=8192)
+    ap.add_argument("--terrain-worlds", type=int, default=2048, help="worlds of the mesh-terrain leg (0: skip)")
     ap.add_argument("--serve-seconds", type=float, default=0.5, help="arrival window of the serving stream (0: skip)")
     ap.add_argument("--serve-rate", type=float, default=200.0)
     ap.add_argument("--threads", type=int, default=None, help="threads per world (default: autotuner table)")

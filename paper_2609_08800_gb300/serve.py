@@ -114,7 +114,7 @@ def request_inputs(kind, scene, n, T, seed, h):
     return s0, controls
 
 
-def poisson_stream(rate, duration, seed, kinds=("box", "robot"), max_worlds=512, horizon=(20, 200)):
+def poisson_stream(rate, duration, seed, kinds=("box", "robot", "terrain"), max_worlds=512, horizon=(20, 200)):
     """Seeded request stream: Poisson arrivals of mean `rate` per second over
     `duration` seconds; worlds log-uniform in [1, max_worlds]; horizon uniform in
     `horizon`; scene uniform over `kinds`; half forward-only, half forward+adjoint."""

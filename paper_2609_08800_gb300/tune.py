@@ -122,10 +122,19 @@ def main(argv=None):
     cases.append((box, np.repeat(S.box_drop_state(box, 0.3), W, axis=1), np.zeros((1, W))))
     rob = S.robot_box_scene()
     cases.append((rob, S.robot_box_states(rob, W, seed=0), S.random_controls(rob.n_servos, W, seed=0, low=-3, high=3)))
+    ter = S.terrain_scene()
+    Wt = min(W, 2048)
+    st = S.terrain_states(ter, Wt, seed=0)
+    st[2:7 * ter.n_bodies:7] -= 0.012                    # resting on the terrain
+    cases.append((ter, st, S.random_controls(ter.n_servos, Wt, seed=0, low=-3, high=3)))
     for scene, st, ub in cases:
         for prec in ("f32", "f64"):
             dt = torch.float64 if prec == "f64" else torch.float32
-            ctx = Context(scene, S.SolverConfig(tol=1e-4 if prec == "f32" else 1e-5), W, dtype=prec)
+            try:
+                ctx = Context(scene, S.SolverConfig(tol=1e-4 if prec == "f32" else 1e-5), st.shape[1], dtype=prec)
+            except RuntimeError as e:                    # e.g. FP64 terrain exceeds shared memory
+                print(scene.name, prec, "skipped:", e)
+                continue
             best, times = tune(ctx, torch.tensor(st, dtype=dt, device="cuda"), torch.tensor(ub, dtype=dt, device="cuda"),
                                h, reps=args.reps, path=args.out)
             print(key(ctx), best, {t: round(v, 3) for t, v in times.items()})

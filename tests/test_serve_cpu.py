@@ -18,4 +18,5 @@ def test_poisson_stream_shape():
     assert 0.4 < np.mean(n < np.sqrt(513)) < 0.6
     assert 0.4 < np.mean([r.adjoint for r in a]) < 0.6
     kinds = [r.kind for r in a]
-    assert 0.4 < kinds.count("box") / len(kinds) < 0.6
+    for k in ("box", "robot", "terrain"):
+        assert 0.25 < kinds.count(k) / len(kinds) < 0.42

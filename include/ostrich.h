@@ -158,6 +158,10 @@ ostrich_status ostrich_tape_clear(ostrich_ctx* ctx);
 /* Device bytes of one tape slot (all worlds). */
 size_t ostrich_tape_bytes(const ostrich_ctx* ctx);
 
+/* Shared-memory bytes one world's working set takes in either kernel (the dynamic
+ * allocation of one CTA); with the registers it bounds the worlds resident per SM. */
+size_t ostrich_workspace_bytes(const ostrich_ctx* ctx);
+
 const char* ostrich_last_error(const ostrich_ctx* ctx);
 void ostrich_destroy(ostrich_ctx* ctx);
 

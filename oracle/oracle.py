@@ -47,6 +47,8 @@ def lib():
         L.oracle_step.argtypes = [_dp, _fp, _dp, _dp, _dp, ctypes.c_double, _dp, _dp, _ip, _up, _dp]
         L.oracle_step_adjoint.argtypes = [_dp, _fp, _dp, _dp, _dp, ctypes.c_double, _dp, ctypes.c_int,
                                           _dp, _dp, _ip, _up, _dp, _dp, _dp]
+        L.oracle_adjoint_at.argtypes = [_dp, _fp, _dp, _dp, _dp, ctypes.c_double, _dp, _dp, _dp, ctypes.c_int,
+                                        _dp, _dp]
         L.oracle_fb.argtypes = [ctypes.c_double, ctypes.c_double, ctypes.c_double, _dp]
         L.oracle_friction_W.argtypes = [ctypes.c_double] * 8
         L.oracle_friction_W.restype = ctypes.c_double
@@ -137,6 +139,24 @@ class Oracle:
             raise RuntimeError("oracle_step_adjoint failed")
         return dict(state=out, impulses=imp, ids=ids[:self.n_slots], status=int(st[0]), iters=int(info[0]),
                     residual=float(info[1]), dstate=dstate, dubar=dubar[:self.n_servo])
+
+    def adjoint_at(self, state, ubar, h, u, lam, dL_dnext, mode=ADJ_PAPER):
+        """The adjoint of the step from `state`, taken at the given returned iterate
+        (u+ [6 nb], lambda+ in the state's lambda layout [m_max]) instead of at the
+        oracle's own solution."""
+        state = self._state(state)
+        ubar = np.ascontiguousarray(np.atleast_1d(ubar), dtype=np.float64) if self.n_servo else np.zeros(1)
+        u = np.ascontiguousarray(u, dtype=np.float64)
+        lam = np.ascontiguousarray(lam, dtype=np.float64)
+        if u.shape != (6 * self.scene.n_bodies,) or lam.shape != (self.m_max,):
+            raise ValueError("u must have 6 nb entries and lambda m_max")
+        g = np.ascontiguousarray(dL_dnext, dtype=np.float64)
+        dstate = np.zeros(self.n_state); dubar = np.zeros(max(self.n_servo, 1))
+        rc = lib().oracle_adjoint_at(*self._common(), _d(state), _d(ubar), float(h), _d(u), _d(lam), _d(g), int(mode),
+                                     _d(dstate), _d(dubar))
+        if rc != 0:
+            raise RuntimeError("oracle_adjoint_at failed")
+        return dict(dstate=dstate, dubar=dubar[:self.n_servo])
 
     def contacts(self, state, h):
         state = self._state(state)

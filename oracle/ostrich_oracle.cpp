@@ -1277,6 +1277,30 @@ int oracle_step_adjoint(const double* scene, const float* heights, const double*
   return 0;
 }
 
+// The adjoint (Sec. III-D) taken at a given returned iterate (u+, lambda+) of the step
+// from state_in, instead of at the oracle's own solution: the paper evaluates A and the
+// VJPs at whatever iterate the forward step returns, so this is the reference for an
+// adjoint computed at another implementation's iterate.  lam_ret uses the state's
+// lambda layout (m_max entries).
+int oracle_adjoint_at(const double* scene, const float* heights, const double* cfgv, const double* state_in,
+                      const double* ubar, double h, const double* u_ret, const double* lam_ret,
+                      const double* dL_dnext, int mode, double* dL_dstate, double* dL_dubar) {
+  OScene s; OCfg cfg;
+  if (!parse_scene(scene, heights, s)) return 1;
+  parse_cfg(cfgv, cfg);
+  Solver S;
+  setup(S, s, cfg, state_in, ubar, h);
+  S.u.assign(u_ret, u_ret + 6 * s.nb);
+  S.lam.assign(lam_ret, lam_ret + s.m_max);
+  AdjOut A;
+  adjoint(S, dL_dnext, mode, A);
+  for (int i = 0; i < 7 * s.nb; ++i) dL_dstate[i] = A.dq[i];
+  for (int i = 0; i < 6 * s.nb; ++i) dL_dstate[7 * s.nb + i] = A.du[i];
+  for (int i = 0; i < s.m_max; ++i) dL_dstate[13 * s.nb + i] = 0.0;
+  for (int i = 0; i < s.n_servo; ++i) dL_dubar[i] = A.dubar[i];
+  return 0;
+}
+
 // Pieces exposed for the pins -------------------------------------------------
 void oracle_fb(double a, double b, double eps, double* out3) {
   out3[0] = fb<double>(a, b, eps);

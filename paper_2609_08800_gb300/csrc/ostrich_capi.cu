@@ -254,6 +254,11 @@ ostrich_status ostrich_tape_clear(ostrich_ctx* c) {
   return OSTRICH_OK;
 }
 
+size_t ostrich_workspace_bytes(const ostrich_ctx* c) {
+  if (!c) return 0;
+  return c->dtype == OSTRICH_F64 ? ost::ws_bytes<double>(c->sc) : ost::ws_bytes<float>(c->sc);
+}
+
 size_t ostrich_tape_bytes(const ostrich_ctx* c) {
   return c ? (size_t)c->n_worlds * c->tape_world_elems * elem_size(c->dtype) : 0;
 }

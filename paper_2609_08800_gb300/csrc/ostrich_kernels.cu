@@ -30,7 +30,7 @@ template <class Real> struct WS {
   // bodies
   Real *qm, *um, *ubar, *uk, *ut, *ub, *du, *f, *rdyn, *mr, *Iw, *Iwi, *R, *qp;
   // rows
-  Real *J, *Y, *C, *rhat, *r2, *lk, *lt, *lb, *dl, *rhs;
+  Real *J, *C, *rhat, *r2, *lk, *lt, *lb, *dl, *rhs;
   int *meta;      // 4 per row: type | sub << 4, b0, b1 (or -1), lam index (state lambda block)
   int *ref;       // slot or joint of the row
   // slots
@@ -42,7 +42,7 @@ template <class Real> struct WS {
   int *g0, *gn, *rgrp;
   // Schur storage (block-arrowhead, inverse form): G group blocks, E coupling rows,
   // H = E G, S reduced separator; prow a pivot-row buffer per warp
-  Real *G, *E, *H, *S, *L, *prow, *tmp, *tmp2;
+  Real *G, *E, *H, *S, *prow, *tmp, *tmp2;
   // scratch
   Real *red;
   int *ints;      // [0] rows, [1] contact rows, [2] items, [3] converged, [4] best_k, [5] iters, [6] status,
@@ -67,7 +67,7 @@ template <class Real> __host__ __device__ size_t ws_bytes(const DevScene& s) {
   b += sz(sizeof(Real), 7 * nb) + sz(sizeof(Real), 6 * nb) + sz(sizeof(Real), s.n_servo + 1);
   b += 8 * sz(sizeof(Real), 6 * nb);                       // uk ut ub du f rdyn mr + spare
   b += 2 * sz(sizeof(Real), 9 * nb) + sz(sizeof(Real), 9 * nb) + sz(sizeof(Real), 7 * nb);
-  b += 2 * sz(sizeof(Real), 12 * m) + 8 * sz(sizeof(Real), m);
+  b += sz(sizeof(Real), 12 * m) + 8 * sz(sizeof(Real), m);
   b += sz(sizeof(int), 4 * m) + sz(sizeof(int), m);
   b += 4 * sz(sizeof(Real), 3 * ns) + 2 * sz(sizeof(Real), ns) + sz(sizeof(Real), 2 * ns);
   b += 4 * sz(sizeof(int), ns);
@@ -77,8 +77,6 @@ template <class Real> __host__ __device__ size_t ws_bytes(const DevScene& s) {
   int cm = s.cmax > 0 ? s.cmax : 1, lds = s.lds > 0 ? s.lds : 1, ldg = s.ldg > 0 ? s.ldg : 1;
   b += sz(sizeof(Real), gsz) + 2 * sz(sizeof(Real), ng * cm * ldg) + sz(sizeof(Real), ss * lds);
   b += sz(sizeof(Real), 4 * (pg > ss ? pg : ss)) + 2 * sz(sizeof(Real), m);
-  int lsz2 = ng * pg * ldg > ss * lds ? ng * pg * ldg : ss * lds;
-  b += sz(sizeof(Real), lsz2);
   b += sz(sizeof(Real), 64) + sz(sizeof(int), 16) + sz(sizeof(Real), 8);
   b += 256;
   return b;
@@ -95,7 +93,7 @@ template <class Real> __host__ __device__ WS<Real> ws_carve(char* base, const De
   w.mr = carve<Real>(p, 6 * nb); (void)carve<Real>(p, 6 * nb);
   w.Iw = carve<Real>(p, 9 * nb); w.Iwi = carve<Real>(p, 9 * nb); w.R = carve<Real>(p, 9 * nb);
   w.qp = carve<Real>(p, 7 * nb);
-  w.J = carve<Real>(p, 12 * m); w.Y = carve<Real>(p, 12 * m);
+  w.J = carve<Real>(p, 12 * m);
   w.C = carve<Real>(p, m); w.rhat = carve<Real>(p, m); w.r2 = carve<Real>(p, m); w.lk = carve<Real>(p, m);
   w.lt = carve<Real>(p, m); w.lb = carve<Real>(p, m); w.dl = carve<Real>(p, m); w.rhs = carve<Real>(p, m);
   w.meta = carve<int>(p, 4 * m); w.ref = carve<int>(p, m);
@@ -110,8 +108,6 @@ template <class Real> __host__ __device__ WS<Real> ws_carve(char* base, const De
   w.G = carve<Real>(p, gsz); w.E = carve<Real>(p, ng * cm * ldg); w.H = carve<Real>(p, ng * cm * ldg);
   w.S = carve<Real>(p, ss * lds);
   w.prow = carve<Real>(p, 4 * (pg > ss ? pg : ss));
-  int lsz2 = ng * pg * ldg > ss * lds ? ng * pg * ldg : ss * lds;
-  w.L = carve<Real>(p, lsz2);
   w.tmp = carve<Real>(p, m); w.tmp2 = carve<Real>(p, m);
   w.red = carve<Real>(p, 64); w.ints = carve<int>(p, 16); w.scal = carve<Real>(p, 8);
   return w;
@@ -131,6 +127,19 @@ template <class Real> __device__ Real block_sum(WS<Real>& w, Real v) {
   }
   __syncthreads();
   return w.red[32];
+}
+
+// block maximum (every thread gets it), through w.red[33..]
+template <class Real> __device__ Real block_max(WS<Real>& w, Real v) {
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = (blockDim.x + 31) >> 5;
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  __syncthreads();
+  if (lane == 0) w.red[33 + wid] = v;
+  __syncthreads();
+  Real mx = w.red[33];
+  for (int i = 1; i < nw; ++i) mx = fmax(mx, w.red[33 + i]);
+  __syncthreads();
+  return mx;
 }
 
 // ---------------------------------------------------------------------------
@@ -375,17 +384,11 @@ __device__ Real evaluate(const DevScene& sc, WS<Real>& w, const Real* u, const R
       vec3<Real> wk = v3(u[6 * b + 3], u[6 * b + 4], u[6 * b + 5]);
       vec3<Real> dirs[3] = {n, t1, t2};
       Real vel[3];
-      const Real mi = Real(1) / Real(sc.mass[b]);
       for (int k = 0; k < 3; ++k) {
         vec3<Real> ang = map_Et(cross3(lev, dirs[k]), wk, h);
         Real* Jr = w.J + 12 * (i + k);
         Jr[0] = dirs[k].x; Jr[1] = dirs[k].y; Jr[2] = dirs[k].z; Jr[3] = ang.x; Jr[4] = ang.y; Jr[5] = ang.z;
         for (int q = 6; q < 12; ++q) Jr[q] = 0;
-        Real* Yr = w.Y + 12 * (i + k);
-        Yr[0] = dirs[k].x * mi; Yr[1] = dirs[k].y * mi; Yr[2] = dirs[k].z * mi;
-        vec3<Real> ia = mat3<Real>(w.Iwi + 9 * b, ang);
-        Yr[3] = ia.x; Yr[4] = ia.y; Yr[5] = ia.z;
-        for (int q = 6; q < 12; ++q) Yr[q] = 0;
         vel[k] = dirs[k].x * u[6 * b] + dirs[k].y * u[6 * b + 1] + dirs[k].z * u[6 * b + 2] + ang.x * u[6 * b + 3] +
                  ang.y * u[6 * b + 4] + ang.z * u[6 * b + 5];
       }
@@ -455,14 +458,6 @@ __device__ Real evaluate(const DevScene& sc, WS<Real>& w, const Real* u, const R
         Real* Jr = w.J + 12 * i;
         Jr[0] = lin_p.x; Jr[1] = lin_p.y; Jr[2] = lin_p.z; Jr[3] = ang_p.x; Jr[4] = ang_p.y; Jr[5] = ang_p.z;
         Jr[6] = lin_c.x; Jr[7] = lin_c.y; Jr[8] = lin_c.z; Jr[9] = ang_c.x; Jr[10] = ang_c.y; Jr[11] = ang_c.z;
-        Real* Yr = w.Y + 12 * i;
-        Real mip = Real(1) / Real(sc.mass[bp]), mic = Real(1) / Real(sc.mass[bc]);
-        Yr[0] = lin_p.x * mip; Yr[1] = lin_p.y * mip; Yr[2] = lin_p.z * mip;
-        vec3<Real> ia = mat3<Real>(w.Iwi + 9 * bp, ang_p);
-        Yr[3] = ia.x; Yr[4] = ia.y; Yr[5] = ia.z;
-        Yr[6] = lin_c.x * mic; Yr[7] = lin_c.y * mic; Yr[8] = lin_c.z * mic;
-        vec3<Real> ic = mat3<Real>(w.Iwi + 9 * bc, ang_c);
-        Yr[9] = ic.x; Yr[10] = ic.y; Yr[11] = ic.z;
         w.r2[i] = c / hR; w.rhat[i] = c / hR; w.C[i] = Real(0);
       }
     } else {
@@ -479,10 +474,6 @@ __device__ Real evaluate(const DevScene& sc, WS<Real>& w, const Real* u, const R
       Real* Jr = w.J + 12 * i;
       Jr[0] = 0; Jr[1] = 0; Jr[2] = 0; Jr[3] = ap_.x; Jr[4] = ap_.y; Jr[5] = ap_.z;
       Jr[6] = 0; Jr[7] = 0; Jr[8] = 0; Jr[9] = ac_.x; Jr[10] = ac_.y; Jr[11] = ac_.z;
-      Real* Yr = w.Y + 12 * i;
-      vec3<Real> ia = mat3<Real>(w.Iwi + 9 * bp, ap_), ic = mat3<Real>(w.Iwi + 9 * bc, ac_);
-      Yr[0] = 0; Yr[1] = 0; Yr[2] = 0; Yr[3] = ia.x; Yr[4] = ia.y; Yr[5] = ia.z;
-      Yr[6] = 0; Yr[7] = 0; Yr[8] = 0; Yr[9] = ic.x; Yr[10] = ic.y; Yr[11] = ic.z;
       Real v = dot3(ap_, wp) + dot3(ac_, wc);
       Real kp = Real(sc.kp[j]);
       Real r = v + lam[i] / kp - w.ubar[sc.servo_of[j]];
@@ -539,6 +530,22 @@ template <class Real> __device__ __forceinline__ Real rowdot(const Real* Ja, int
          Ja[sa + 4] * Yb[sb + 4] + Ja[sa + 5] * Yb[sb + 5];
 }
 
+// y = M^-1 J_i^T for both body blocks of row i: (J_lin / m, Iw^-1 J_ang) per side (zero
+// for a side without a body); the same values Eq. (2)'s M~^-1 gives the row.
+template <class Real> __device__ __forceinline__ void minv_row(const DevScene& sc, const WS<Real>& w, int i, Real* y) {
+  const Real* Jr = w.J + 12 * i;
+  for (int side = 0; side < 2; ++side) {
+    const int b = w.meta[4 * i + 1 + side];
+    Real* ys = y + 6 * side;
+    if (b < 0) { for (int q = 0; q < 6; ++q) ys[q] = Real(0); continue; }
+    const Real* Js = Jr + 6 * side;
+    const Real mi = Real(1) / Real(sc.mass[b]);
+    ys[0] = Js[0] * mi; ys[1] = Js[1] * mi; ys[2] = Js[2] * mi;
+    const vec3<Real> ia = mat3<Real>(w.Iwi + 9 * b, v3(Js[3], Js[4], Js[5]));
+    ys[3] = ia.x; ys[4] = ia.y; ys[5] = ia.z;
+  }
+}
+
 template <class Real> __device__ void assemble(const DevScene& sc, WS<Real>& w, double h) {
   const int tid = threadIdx.x, nth = blockDim.x;
   const int m = w.ints[0], mc = w.ints[1], pg = sc.pg, ss = sc.ss, ldg = sc.ldg, lds = sc.lds;
@@ -546,7 +553,9 @@ template <class Real> __device__ void assemble(const DevScene& sc, WS<Real>& w, 
   // delta = delta_rel * mean diag(h J M^-1 J^T)
   Real part = 0;
   for (int i = tid; i < m; i += nth) {
-    const Real* Ji = w.J + 12 * i; const Real* Yi = w.Y + 12 * i;
+    const Real* Ji = w.J + 12 * i;
+    Real Yi[12];
+    minv_row(sc, w, i, Yi);
     part += hR * (rowdot(Ji, 0, Yi, 0) + rowdot(Ji, 6, Yi, 6));
   }
   Real tot = block_sum(w, part);
@@ -557,9 +566,11 @@ template <class Real> __device__ void assemble(const DevScene& sc, WS<Real>& w, 
     const int g = w.rgrp[r], r0 = w.g0[g], i = r - r0, bg = sc.group_body[g];
     Real* Gb = w.G + g * pg * ldg;
     const int ti = w.meta[4 * r] & 15, si = w.meta[4 * r] >> 4;
+    Real Yr[12];
+    minv_row(sc, w, r, Yr);
     for (int jj = r0; jj <= r; ++jj) {
       const int j = jj - r0;
-      Real v = hR * rowdot(w.J + 12 * r, 0, w.Y + 12 * jj, 0);
+      Real v = hR * rowdot(w.J + 12 * jj, 0, Yr, 0);
       if (jj == r) v += w.C[r] + delta;
       if (ti == ROW_FRIC && (w.meta[4 * jj] & 15) == ROW_FRIC && w.ref[r] == w.ref[jj]) {
         const Real* rd = w.srad + 3 * w.ref[r];
@@ -573,21 +584,23 @@ template <class Real> __device__ void assemble(const DevScene& sc, WS<Real>& w, 
     for (int k = 0; k < sc.cpl_n[g]; ++k) {
       const int row = mc + sc.cpl_row[g][k];
       const int side = w.meta[4 * row + 1] == bg ? 0 : 6;
-      Eb[k * ldg + i] = hR * rowdot(w.J + 12 * row, side, w.Y + 12 * r, 0);
+      Eb[k * ldg + i] = hR * rowdot(w.J + 12 * row, side, Yr, 0);
     }
   }
   // separator block (full, symmetric): a thread per separator row
   for (int a = tid; a < ss; a += nth) {
     const int i = mc + a;
     const int ia0 = w.meta[4 * i + 1], ia1 = w.meta[4 * i + 2];
+    Real Yi[12];
+    minv_row(sc, w, i, Yi);
     for (int b = 0; b <= a; ++b) {
       const int j = mc + b;
       const int jb0 = w.meta[4 * j + 1], jb1 = w.meta[4 * j + 2];
       Real v = 0;
-      if (ia0 == jb0) v += rowdot(w.J + 12 * i, 0, w.Y + 12 * j, 0);
-      if (ia0 == jb1) v += rowdot(w.J + 12 * i, 0, w.Y + 12 * j, 6);
-      if (ia1 >= 0 && ia1 == jb0) v += rowdot(w.J + 12 * i, 6, w.Y + 12 * j, 0);
-      if (ia1 >= 0 && ia1 == jb1) v += rowdot(w.J + 12 * i, 6, w.Y + 12 * j, 6);
+      if (ia0 == jb0) v += rowdot(w.J + 12 * j, 0, Yi, 0);
+      if (ia0 == jb1) v += rowdot(w.J + 12 * j, 6, Yi, 0);
+      if (ia1 >= 0 && ia1 == jb0) v += rowdot(w.J + 12 * j, 0, Yi, 6);
+      if (ia1 >= 0 && ia1 == jb1) v += rowdot(w.J + 12 * j, 6, Yi, 6);
       v *= hR;
       if (a == b) v += w.C[i] + delta;
       w.S[a * lds + b] = v;
@@ -597,41 +610,44 @@ template <class Real> __device__ void assemble(const DevScene& sc, WS<Real>& w, 
   __syncthreads();
 }
 
-// In-place Cholesky of the lower triangle of an n x n block (row-major, odd leading
-// dimension ld) by one warp: a lane per row for the column scaling and the trailing
-// update of its own row.
-template <class Real> __device__ void warp_chol(Real* A, int n, int ld) {
-  const int lane = threadIdx.x & 31;
+// L^-1 of an n x n symmetric positive definite block, in place, by a team of threads:
+// one warp (TEAM = 0, __syncwarp) or the whole CTA (TEAM = 1, __syncthreads).  A holds
+// the lower triangle on entry and L^-1 (lower triangle) on return, L L^T = A; colbuf
+// holds n values.  Right-looking, one pivot k at a time:
+//   pass 1: column k of L below the pivot goes to colbuf; row k of L^-1 is finished,
+//           X[k][c] = Xt[k][c] / L[k][k] (its partial sums Xt already sit in row k);
+//   pass 2: rank-one updates of the trailing block, A[i][j] -= L[i][k] L[j][k]
+//           (k < j <= i), and of the rows of L^-1 below, Xt[i][c] -= L[i][k] X[k][c]
+//           (c <= k).  Position (i, k) changes from L[i][k], now in colbuf and never
+//           read again, to Xt[i][k].
+// Each element of L and of L^-1 receives the same operations in the same order as the
+// sequential column-by-column factor and forward substitution (k, resp. l,
+// ascending), so the result does not depend on the team size.
+template <int TEAM, class Real> __device__ void chol_inv_inplace(Real* A, int n, int ld, Real* colbuf) {
+  const int t = TEAM ? (int)threadIdx.x : (int)(threadIdx.x & 31);
+  const int T = TEAM ? (int)blockDim.x : 32;
   for (int k = 0; k < n; ++k) {
     const Real akk = A[k * ld + k];
     const Real d = ssqrt(akk > Real(0) ? akk : Real(1e-30));
     const Real inv = Real(1) / d;
-    __syncwarp();
-    if (lane == 0) A[k * ld + k] = d;
-    for (int i = k + 1 + lane; i < n; i += 32) A[i * ld + k] *= inv;
-    __syncwarp();
-    for (int i = k + 1 + lane; i < n; i += 32) {
-      Real* Ai = A + i * ld;
-      const Real lik = Ai[k];
-      for (int j = k + 1; j <= i; ++j) Ai[j] -= lik * A[j * ld + k];
+    if (TEAM) __syncthreads(); else __syncwarp();       // everyone has read the pivot
+    for (int e = t; e < n; e += T) {
+      if (e > k) colbuf[e] = A[e * ld + k] * inv;
+      else if (e < k) A[k * ld + e] = A[k * ld + e] / d;
+      else A[k * ld + k] = Real(1) / d;
     }
-    __syncwarp();
-  }
-}
-
-// X = L^-1 (lower triangular) for an n x n Cholesky factor, one warp, a lane per column.
-template <class Real> __device__ void warp_trinv(const Real* L, int n, int ld, Real* X) {
-  const int lane = threadIdx.x & 31;
-  for (int c = lane; c < n; c += 32) {
-    for (int i = 0; i < c; ++i) X[i * ld + c] = Real(0);
-    for (int i = c; i < n; ++i) {
-      Real acc = i == c ? Real(1) : Real(0);
-      const Real* Li = L + i * ld;
-      for (int l = c; l < i; ++l) acc -= Li[l] * X[l * ld + c];
-      X[i * ld + c] = acc / Li[i];
+    if (TEAM) __syncthreads(); else __syncwarp();
+    const int nr = n - k - 1;
+    for (int e = t; e < nr * n; e += T) {
+      const int r = e / n, j = e - r * n, i = k + 1 + r;
+      if (j > i) continue;
+      const Real lik = colbuf[i];
+      if (j < k) A[i * ld + j] -= lik * A[k * ld + j];
+      else if (j == k) A[i * ld + k] = -(lik * A[k * ld + k]);
+      else A[i * ld + j] -= lik * colbuf[j];
     }
+    if (TEAM) __syncthreads(); else __syncwarp();
   }
-  __syncwarp();
 }
 
 // Block-arrowhead factorisation kept in inverse form for row-parallel solves:
@@ -643,18 +659,9 @@ template <class Real> __device__ void warp_trinv(const Real* L, int n, int ld, R
 template <class Real> __device__ void factor(const DevScene& sc, WS<Real>& w) {
   const int tid = threadIdx.x, nth = blockDim.x, wid = tid >> 5, nw = (blockDim.x + 31) >> 5;
   const int pg = sc.pg, ss = sc.ss, ldg = sc.ldg, lds = sc.lds, cm = sc.cmax;
-  for (int g = wid; g < sc.n_groups; g += nw) warp_chol(w.G + g * pg * ldg, w.gn[g], ldg);
-  __syncthreads();
-  // invert each group factor into L (scratch), then copy back over G
-  for (int g = wid; g < sc.n_groups; g += nw) warp_trinv(w.G + g * pg * ldg, w.gn[g], ldg, w.L + g * pg * ldg);
-  __syncthreads();
-  for (int g = 0; g < sc.n_groups; ++g) {
-    const int n = w.gn[g];
-    for (int e = tid; e < n * n; e += nth) {
-      const int i = e / n, j = e - i * n;
-      w.G[g * pg * ldg + i * ldg + j] = w.L[g * pg * ldg + i * ldg + j];
-    }
-  }
+  const int rb = pg > ss ? pg : ss;
+  // Li_g in place: each warp its groups
+  for (int g = wid; g < sc.n_groups; g += nw) chol_inv_inplace<0>(w.G + g * pg * ldg, w.gn[g], ldg, w.prow + wid * rb);
   __syncthreads();
   // F_g[k][j] = sum_{l <= j} E_g[k][l] Li_g[j][l]
   for (int g = 0; g < sc.n_groups; ++g) {
@@ -670,31 +677,24 @@ template <class Real> __device__ void factor(const DevScene& sc, WS<Real>& w) {
     }
   }
   __syncthreads();
-  // S' = S - sum_g F_g F_g^T (lower triangle)
-  for (int a = tid; a < ss; a += nth) {
-    for (int b = 0; b <= a; ++b) {
-      Real acc = 0;
-      for (int pa = 0; pa < sc.sep_n[a]; ++pa)
-        for (int pb = 0; pb < sc.sep_n[b]; ++pb) {
-          const int g = sc.sep_g[a][pa];
-          if (g != sc.sep_g[b][pb]) continue;
-          const Real* fa = w.H + g * cm * ldg + sc.sep_k[a][pa] * ldg;
-          const Real* fb = w.H + g * cm * ldg + sc.sep_k[b][pb] * ldg;
-          for (int j = 0; j < w.gn[g]; ++j) acc += fa[j] * fb[j];
-        }
-      w.S[a * lds + b] -= acc;
-    }
+  // S' = S - sum_g F_g F_g^T (lower triangle), one element per thread
+  for (int e = tid; e < ss * ss; e += nth) {
+    const int a = e / ss, b = e - a * ss;
+    if (b > a) continue;
+    Real acc = 0;
+    for (int pa = 0; pa < sc.sep_n[a]; ++pa)
+      for (int pb = 0; pb < sc.sep_n[b]; ++pb) {
+        const int g = sc.sep_g[a][pa];
+        if (g != sc.sep_g[b][pb]) continue;
+        const Real* fa = w.H + g * cm * ldg + sc.sep_k[a][pa] * ldg;
+        const Real* fb = w.H + g * cm * ldg + sc.sep_k[b][pb] * ldg;
+        for (int j = 0; j < w.gn[g]; ++j) acc += fa[j] * fb[j];
+      }
+    w.S[a * lds + b] -= acc;
   }
   __syncthreads();
-  if (wid == 0 && ss > 0) {
-    warp_chol(w.S, ss, lds);
-    warp_trinv(w.S, ss, lds, w.L);
-    for (int e = threadIdx.x & 31; e < ss * ss; e += 32) {
-      const int i = e / ss, j = e - i * ss;
-      w.S[i * lds + j] = w.L[i * lds + j];
-    }
-  }
-  __syncthreads();
+  // Lsi in place over S, the whole CTA
+  if (ss > 0) chol_inv_inplace<1>(w.S, ss, lds, w.prow);
 }
 
 // v <- A^-1 v with the inverse-form block-arrowhead factor (row-parallel phases)
@@ -809,7 +809,7 @@ template <class Real> __device__ __forceinline__ void minv6(const DevScene& sc, 
 // the solution is returned in `x`; t6 (6 per body) and r (rows) are scratch.
 template <class Real>
 __device__ void schur_solve(const DevScene& sc, WS<Real>& w, const Real* b, Real* x, Real* t6, Real* r, double h,
-                            int sweeps) {
+                            int sweeps, Real stop_rel = Real(0)) {
   const int tid = threadIdx.x, nth = blockDim.x, m = w.ints[0];
   const Real hR = Real(h);
   for (int i = tid; i < m; i += nth) x[i] = b[i];
@@ -846,8 +846,19 @@ __device__ void schur_solve(const DevScene& sc, WS<Real>& w, const Real* b, Real
     }
     __syncthreads();
     arrow_solve(sc, w, r);
-    for (int i = tid; i < m; i += nth) x[i] += r[i];
+    Real cmax = Real(0), xmax = Real(0);
+    for (int i = tid; i < m; i += nth) {
+      x[i] += r[i];
+      cmax = fmax(cmax, fabs(r[i]));
+      xmax = fmax(xmax, fabs(x[i]));
+    }
     __syncthreads();
+    // optional early stop once the correction no longer changes x at working precision
+    if (stop_rel > Real(0)) {
+      cmax = block_max(w, cmax);
+      xmax = block_max(w, xmax);
+      if (cmax <= stop_rel * xmax) break;
+    }
   }
 }
 
@@ -1197,7 +1208,9 @@ __global__ void __launch_bounds__(128) adjoint_kernel(const DevScene scp, const 
   {
     Real part = 0;
     for (int i = tid; i < m; i += nth) {
-      const Real* Ji = w.J + 12 * i; const Real* Yi = w.Y + 12 * i;
+      const Real* Ji = w.J + 12 * i;
+      Real Yi[12];
+      minv_row(sc, w, i, Yi);
       part += hR * (rowdot(Ji, 0, Yi, 0) + rowdot(Ji, 6, Yi, 6));
     }
     Real tot = block_sum(w, part);

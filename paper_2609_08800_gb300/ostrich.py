@@ -76,6 +76,8 @@ def lib():
         L.ostrich_debug_trace.restype = ctypes.c_int
         L.ostrich_tape_bytes.argtypes = [_vp]
         L.ostrich_tape_bytes.restype = ctypes.c_size_t
+        L.ostrich_workspace_bytes.argtypes = [_vp]
+        L.ostrich_workspace_bytes.restype = ctypes.c_size_t
         L.ostrich_last_error.argtypes = [_vp]
         L.ostrich_last_error.restype = ctypes.c_char_p
         L.ostrich_destroy.argtypes = [_vp]
@@ -227,6 +229,9 @@ class Context:
 
     def tape_bytes(self):
         return int(lib().ostrich_tape_bytes(self._h))
+
+    def workspace_bytes(self):
+        return int(lib().ostrich_workspace_bytes(self._h))
 
     # convenience wrappers that allocate outputs (torch tensors [rows, ld])
     def alloc_state(self):

@@ -446,3 +446,19 @@ def test_wheel_features_on_box_scene():
     for sl in edge:
         n = nd[sl, :3]
         assert n[0] > 0 and n[2] > 0 and abs(np.linalg.norm(n) - 1) < 1e-6
+
+
+def test_adjoint_at_own_solution_equals_step_adjoint():
+    """The adjoint taken at a supplied iterate reproduces the step's own adjoint when
+    given the step's returned iterate (the same A, the same VJPs)."""
+    sc, st = _robot_states(n=3, seed=9)
+    orc = O.Oracle(sc, S.SolverConfig(budget=40, tol=1e-9))
+    nb = sc.n_bodies
+    g = np.random.default_rng(4).normal(size=sc.n_state)
+    g[13 * nb:] = 0
+    ub = np.array([1.0, -2.0, 2.5, 0.5])
+    for w in range(3):
+        r = orc.step_adjoint(st[:, w], ub, 0.1, g)
+        a = orc.adjoint_at(st[:, w], ub, 0.1, r["state"][7 * nb:13 * nb], r["state"][13 * nb:], g)
+        np.testing.assert_array_equal(a["dstate"], r["dstate"])
+        np.testing.assert_array_equal(a["dubar"], r["dubar"])

@@ -237,3 +237,16 @@ def test_robot_box_fp64_truncated_pullback_matches_oracle(ostrich):
     g = np.random.default_rng(18).normal(size=st.shape)
     g[13 * sc.n_bodies:] = 0
     _compare(sc, cfg, ostrich, st, ub, 0.1, "f64", 1e-7, 1e-6, 1e-6, 0.8, grads=g)
+
+
+def test_terrain_fp64_matches_oracle(ostrich):
+    """The FP64 build on the mesh terrain: contact search, rows, factor and the
+    truncated pull-back against the oracle, free of FP32 effects."""
+    sc = S.terrain_scene()
+    W = 24
+    st = _terrain_states(sc, W, 2)
+    ub = S.random_controls(sc.n_servos, W, seed=2, low=-3, high=3)
+    cfg = S.SolverConfig(budget=40, tol=1e-9, pullback=S.PULLBACK_TRUNCATED)
+    g = np.random.default_rng(22).normal(size=st.shape)
+    g[13 * sc.n_bodies:] = 0
+    _compare(sc, cfg, ostrich, st, ub, 0.1, "f64", 1e-7, 1e-6, 1e-6, 0.7, grads=g)

@@ -230,14 +230,15 @@ def run_ours(args, rank, world_size, local_rank):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world_size, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": "robot_over_box_8192_worlds_fp32_fwd_adj_chunk10", "worlds_per_gpu": W,
+        "config": {"workload": f"robot_over_box_{W}_worlds_fp32_fwd_adj_chunk10", "worlds_per_gpu": W,
                    "steps_per_chunk": CHUNK, "h": H, "newton_budget": cfg.budget,
                    "threads_per_world": threads,
                    "parallelism": f"replicas{world_size}",
                    "l2": f"tape of one chunk {ctx.tape_bytes() * CHUNK / 1e9:.2f} GB > 129 MB L2 (no flush needed)"},
         "gpu_launches": 2 * CHUNK * args.steps,
         "kernels": {"step_ms_avg": avg_step_ms, "adjoint_ms_avg": statistics.mean(adj_ms),
-                    "newton_iters_mean": float(n_iter.mean()), "active_rows_mean": float(n_rows.mean())},
+                    "newton_iters_mean": float(n_iter.mean()), "active_rows_mean": float(n_rows.mean()),
+                    "newton_iters_hist": np.bincount(n_iter.ravel(), minlength=cfg.budget + 1).tolist()},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": achieved / peak, "traffic": None,
                      "peak_source": f"152 SMs x 128 FP32 lanes x 2 flop x {sm_mhz:.0f} MHz (SM max clock)",

@@ -117,8 +117,12 @@ ostrich_status ostrich_create(const ostrich_scene_desc* d, const ostrich_solver_
   s.tol = cfg->tol; s.delta_rel = cfg->delta_rel; s.kappa = cfg->kappa; s.eps = cfg->eps_fb; s.margin = cfg->margin;
   if (s.m_max < 7 * s.nb) { delete c; return OSTRICH_EINVAL; }   // adjoint scratch reuse
   // FP32 factors lose the small eigenvalues (contact compliance kappa) of the Schur
-  // matrix; two sweeps of refinement against the matrix-free product recover them.
-  s.refine = dtype == OSTRICH_F32 ? 2 : 0;
+  // matrix.  The adjoint solves once, so it refines its solution against the
+  // matrix-free product (8 sweeps); the forward Newton iteration corrects an inexact
+  // step by itself (without refinement it takes the same number of iterations to the
+  // same residuals), so its solves are not refined.
+  s.refine = 0;
+  s.refine_adj = dtype == OSTRICH_F32 ? 8 : 0;
   c->n_worlds = n_worlds; c->ld = ld ? ld : n_worlds; c->dtype = dtype; c->tape_slots = tape_slots;
   size_t smem = dtype == OSTRICH_F64 ? ost::ws_bytes<double>(s) : ost::ws_bytes<float>(s);
   size_t used = dtype == OSTRICH_F64 ? ost::ws_used<double>(s) : ost::ws_used<float>(s);

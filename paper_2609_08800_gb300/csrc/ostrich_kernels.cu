@@ -1227,7 +1227,7 @@ __global__ void __launch_bounds__(128) adjoint_kernel(const DevScene scp, const 
     w.rhs[i] = -hR * jm.value();
   }
   __syncthreads();
-  schur_solve(sc, w, w.rhs, wl, w.f, w.lt, h, 4 * sc.refine);
+  schur_solve(sc, w, w.rhs, wl, w.f, w.lt, h, sc.refine_adj);
   // Eq. (19): w_u = -M^-1 (g + J^T w_lambda)
   Real* wu = w.ub;
   jt_apply_acc(sc, w, wl, w.f);     // f is free now

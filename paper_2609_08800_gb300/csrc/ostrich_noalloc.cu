@@ -86,7 +86,8 @@ bool make_scene(const ostrich_scene_desc* d, const ostrich_solver_cfg* cfg, ost:
   ost::finish_scene(s);
   s.budget = cfg->budget; s.kmin = cfg->k_min; s.ls = cfg->line_search; s.pullback = cfg->pullback;
   s.tol = cfg->tol; s.delta_rel = cfg->delta_rel; s.kappa = cfg->kappa; s.eps = cfg->eps_fb; s.margin = cfg->margin;
-  s.refine = 2;
+  s.refine = 0;
+  s.refine_adj = 8;
   if (s.m_max < 7 * s.nb) return false;
   size_t smem = ost::ws_bytes<float>(s);
   return smem <= 227 * 1024 && ost::ws_used<float>(s) <= smem;

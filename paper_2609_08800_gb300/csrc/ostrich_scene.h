@@ -32,7 +32,8 @@ struct DevScene {
   // solver settings
   int budget, kmin, ls, pullback;
   double tol, delta_rel, kappa, eps, margin;
-  int refine;     // iterative-refinement sweeps after each Schur solve
+  int refine;     // iterative-refinement sweeps after each forward (Newton-step) Schur solve
+  int refine_adj; // iterative-refinement sweeps after the adjoint's Schur solve
   // layout caps derived from the scene
   int n_groups;   // bodies that carry contact slots (leaf blocks of the Schur matrix)
   int pg;         // largest leaf block (3 x slots of one body)

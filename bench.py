@@ -162,6 +162,28 @@ class Chunk:
                 ev_adj[t][1].record()
 
 
+def measured_traffic_per_world():
+    """DRAM bytes per world-step of the step kernel from the committed ncu summary, or
+    None when the CUDA sources have changed since that capture."""
+    import hashlib
+    prof = os.path.join(ROOT, "profiles", "step_kernel_robot_box_fp32.md")
+    csrc = os.path.join(ROOT, "paper_2609_08800_gb300", "csrc")
+    try:
+        text = open(prof).read()
+    except OSError:
+        return None
+    h = hashlib.sha1()
+    for f in sorted(os.listdir(csrc)):
+        if f.endswith((".cu", ".cuh", ".h")):
+            h.update(f.encode())
+            h.update(open(os.path.join(csrc, f), "rb").read())
+    vals = dict(line.split(": ", 1) for line in text.splitlines()
+                if line.startswith(("csrc_sha1: ", "step_dram_bytes_per_world_step: ")))
+    if vals.get("csrc_sha1") != h.hexdigest() or "step_dram_bytes_per_world_step" not in vals:
+        return None
+    return float(vals["step_dram_bytes_per_world_step"])
+
+
 def run_ours(args, rank, world_size, local_rank):
     import torch
     from paper_2609_08800_gb300.ostrich import Context
@@ -224,6 +246,7 @@ def run_ours(args, rank, world_size, local_rank):
     achieved = flops_per_launch / (avg_step_ms * 1e-3) / 1e12
     sm_mhz = (clocks or {}).get("sm_max_mhz") or measured_peaks().get("sm_max_mhz", 2070.0)
     peak = SM_COUNT_GB300 * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
+    traffic_pw = measured_traffic_per_world()
     world_steps = W * CHUNK * world_size
     value = world_steps / (ms * 1e-3)
     out = {
@@ -240,7 +263,10 @@ def run_ours(args, rank, world_size, local_rank):
                     "newton_iters_mean": float(n_iter.mean()), "active_rows_mean": float(n_rows.mean()),
                     "newton_iters_hist": np.bincount(n_iter.ravel(), minlength=cfg.budget + 1).tolist()},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                     "frac": achieved / peak, "traffic": None,
+                     "frac": achieved / peak,
+                     "traffic": (None if traffic_pw is None else traffic_pw * W),
+                     "traffic_source": "ncu dram__bytes_read+write of one 2048-world step launch "
+                                       "(profiles/step_kernel_robot_box_fp32.md), per world x worlds",
                      "peak_source": f"152 SMs x 128 FP32 lanes x 2 flop x {sm_mhz:.0f} MHz (SM max clock)",
                      "kernel": "step_kernel<float>", "flops_per_launch": flops_per_launch},
     }

@@ -73,9 +73,11 @@ template <class Real> __host__ __device__ size_t ws_bytes(const DevScene& s) {
   b += 4 * sz(sizeof(int), ns);
   b += sz(sizeof(int), nb) * 2 + sz(sizeof(int), nb * ss);
   b += 2 * sz(sizeof(int), ng) + sz(sizeof(int), m);
-  int gsz = ng * pg * s.ldg > 14 * m ? ng * pg * s.ldg : 14 * m;   // G also holds the adjoint's VJP items
-  int cm = s.cmax > 0 ? s.cmax : 1, lds = s.lds > 0 ? s.lds : 1, ldg = s.ldg > 0 ? s.ldg : 1;
-  b += sz(sizeof(Real), gsz) + 2 * sz(sizeof(Real), ng * cm * ldg) + sz(sizeof(Real), ss * lds);
+  // the adjoint's VJP items (14 per row) reuse G, E, H and S, which are carved in one run
+  int cm = s.cmax > 0 ? s.cmax : 1, ldg = s.ldg > 0 ? s.ldg : 1;
+  int gsz = ng * tri_size(pg), rest = 2 * ng * cm * ldg + tri_size(ss);
+  if (gsz + rest < 14 * m) gsz = 14 * m - rest;
+  b += sz(sizeof(Real), gsz) + 2 * sz(sizeof(Real), ng * cm * ldg) + sz(sizeof(Real), tri_size(ss));
   b += sz(sizeof(Real), 4 * (pg > ss ? pg : ss)) + 2 * sz(sizeof(Real), m);
   b += sz(sizeof(Real), 64) + sz(sizeof(int), 16) + sz(sizeof(Real), 8);
   b += 256;
@@ -103,10 +105,11 @@ template <class Real> __host__ __device__ WS<Real> ws_carve(char* base, const De
   w.sact = carve<int>(p, ns); w.srow = carve<int>(p, ns); w.sid = carve<int>(p, ns); w.sftype = carve<int>(p, ns);
   w.bgrp = carve<int>(p, nb); w.bsepn = carve<int>(p, nb); w.bsep = carve<int>(p, nb * ss);
   w.g0 = carve<int>(p, ng); w.gn = carve<int>(p, ng); w.rgrp = carve<int>(p, m);
-  int gsz = ng * pg * s.ldg > 14 * m ? ng * pg * s.ldg : 14 * m;
-  int cm = s.cmax > 0 ? s.cmax : 1, lds = s.lds > 0 ? s.lds : 1, ldg = s.ldg > 0 ? s.ldg : 1;
+  int cm = s.cmax > 0 ? s.cmax : 1, ldg = s.ldg > 0 ? s.ldg : 1;
+  int gsz = ng * tri_size(pg), rest = 2 * ng * cm * ldg + tri_size(ss);
+  if (gsz + rest < 14 * m) gsz = 14 * m - rest;
   w.G = carve<Real>(p, gsz); w.E = carve<Real>(p, ng * cm * ldg); w.H = carve<Real>(p, ng * cm * ldg);
-  w.S = carve<Real>(p, ss * lds);
+  w.S = carve<Real>(p, tri_size(ss));
   w.prow = carve<Real>(p, 4 * (pg > ss ? pg : ss));
   w.tmp = carve<Real>(p, m); w.tmp2 = carve<Real>(p, m);
   w.red = carve<Real>(p, 64); w.ints = carve<int>(p, 16); w.scal = carve<Real>(p, 8);
@@ -548,7 +551,7 @@ template <class Real> __device__ __forceinline__ void minv_row(const DevScene& s
 
 template <class Real> __device__ void assemble(const DevScene& sc, WS<Real>& w, double h) {
   const int tid = threadIdx.x, nth = blockDim.x;
-  const int m = w.ints[0], mc = w.ints[1], pg = sc.pg, ss = sc.ss, ldg = sc.ldg, lds = sc.lds;
+  const int m = w.ints[0], mc = w.ints[1], gstr = tri_size(sc.pg), ss = sc.ss, ldg = sc.ldg;
   const Real hR = Real(h);
   // delta = delta_rel * mean diag(h J M^-1 J^T)
   Real part = 0;
@@ -564,7 +567,7 @@ template <class Real> __device__ void assemble(const DevScene& sc, WS<Real>& w, 
   // group blocks (full, symmetric) and their coupling rows E_g: a thread per contact row
   for (int r = tid; r < mc; r += nth) {
     const int g = w.rgrp[r], r0 = w.g0[g], i = r - r0, bg = sc.group_body[g];
-    Real* Gb = w.G + g * pg * ldg;
+    Real* Gb = w.G + g * gstr;
     const int ti = w.meta[4 * r] & 15, si = w.meta[4 * r] >> 4;
     Real Yr[12];
     minv_row(sc, w, r, Yr);
@@ -577,8 +580,7 @@ template <class Real> __device__ void assemble(const DevScene& sc, WS<Real>& w, 
         const int sj = w.meta[4 * jj] >> 4;
         v += (si == 1 && sj == 1) ? rd[0] : ((si == 2 && sj == 2) ? rd[2] : rd[1]);
       }
-      Gb[i * ldg + j] = v;
-      Gb[j * ldg + i] = v;
+      Gb[tri(i, j)] = v;
     }
     Real* Eb = w.E + g * sc.cmax * ldg;
     for (int k = 0; k < sc.cpl_n[g]; ++k) {
@@ -603,16 +605,15 @@ template <class Real> __device__ void assemble(const DevScene& sc, WS<Real>& w, 
       if (ia1 >= 0 && ia1 == jb1) v += rowdot(w.J + 12 * j, 6, Yi, 6);
       v *= hR;
       if (a == b) v += w.C[i] + delta;
-      w.S[a * lds + b] = v;
-      w.S[b * lds + a] = v;
+      w.S[tri(a, b)] = v;
     }
   }
   __syncthreads();
 }
 
 // L^-1 of an n x n symmetric positive definite block, in place, by a team of threads:
-// one warp (TEAM = 0, __syncwarp) or the whole CTA (TEAM = 1, __syncthreads).  A holds
-// the lower triangle on entry and L^-1 (lower triangle) on return, L L^T = A; colbuf
+// one warp (TEAM = 0, __syncwarp) or the whole CTA (TEAM = 1, __syncthreads).  A (packed
+// lower triangle, tri()) holds the block on entry and L^-1 on return, L L^T = A; colbuf
 // holds n values.  Right-looking, one pivot k at a time:
 //   pass 1: column k of L below the pivot goes to colbuf; row k of L^-1 is finished,
 //           X[k][c] = Xt[k][c] / L[k][k] (its partial sums Xt already sit in row k);
@@ -623,18 +624,18 @@ template <class Real> __device__ void assemble(const DevScene& sc, WS<Real>& w, 
 // Each element of L and of L^-1 receives the same operations in the same order as the
 // sequential column-by-column factor and forward substitution (k, resp. l,
 // ascending), so the result does not depend on the team size.
-template <int TEAM, class Real> __device__ void chol_inv_inplace(Real* A, int n, int ld, Real* colbuf) {
+template <int TEAM, class Real> __device__ void chol_inv_inplace(Real* A, int n, Real* colbuf) {
   const int t = TEAM ? (int)threadIdx.x : (int)(threadIdx.x & 31);
   const int T = TEAM ? (int)blockDim.x : 32;
   for (int k = 0; k < n; ++k) {
-    const Real akk = A[k * ld + k];
+    const Real akk = A[tri(k, k)];
     const Real d = ssqrt(akk > Real(0) ? akk : Real(1e-30));
     const Real inv = Real(1) / d;
     if (TEAM) __syncthreads(); else __syncwarp();       // everyone has read the pivot
     for (int e = t; e < n; e += T) {
-      if (e > k) colbuf[e] = A[e * ld + k] * inv;
-      else if (e < k) A[k * ld + e] = A[k * ld + e] / d;
-      else A[k * ld + k] = Real(1) / d;
+      if (e > k) colbuf[e] = A[tri(e, k)] * inv;
+      else if (e < k) A[tri(k, e)] = A[tri(k, e)] / d;
+      else A[tri(k, k)] = Real(1) / d;
     }
     if (TEAM) __syncthreads(); else __syncwarp();
     const int nr = n - k - 1;
@@ -642,9 +643,9 @@ template <int TEAM, class Real> __device__ void chol_inv_inplace(Real* A, int n,
       const int r = e / n, j = e - r * n, i = k + 1 + r;
       if (j > i) continue;
       const Real lik = colbuf[i];
-      if (j < k) A[i * ld + j] -= lik * A[k * ld + j];
-      else if (j == k) A[i * ld + k] = -(lik * A[k * ld + k]);
-      else A[i * ld + j] -= lik * colbuf[j];
+      if (j < k) A[tri(i, j)] -= lik * A[tri(k, j)];
+      else if (j == k) A[tri(i, k)] = -(lik * A[tri(k, k)]);
+      else A[tri(i, j)] -= lik * colbuf[j];
     }
     if (TEAM) __syncthreads(); else __syncwarp();
   }
@@ -658,21 +659,21 @@ template <int TEAM, class Real> __device__ void chol_inv_inplace(Real* A, int n,
 // the scratch E (groups; the coupling E_g is consumed first) and prow (separator).
 template <class Real> __device__ void factor(const DevScene& sc, WS<Real>& w) {
   const int tid = threadIdx.x, nth = blockDim.x, wid = tid >> 5, nw = (blockDim.x + 31) >> 5;
-  const int pg = sc.pg, ss = sc.ss, ldg = sc.ldg, lds = sc.lds, cm = sc.cmax;
+  const int pg = sc.pg, ss = sc.ss, ldg = sc.ldg, cm = sc.cmax, gstr = tri_size(pg);
   const int rb = pg > ss ? pg : ss;
   // Li_g in place: each warp its groups
-  for (int g = wid; g < sc.n_groups; g += nw) chol_inv_inplace<0>(w.G + g * pg * ldg, w.gn[g], ldg, w.prow + wid * rb);
+  for (int g = wid; g < sc.n_groups; g += nw) chol_inv_inplace<0>(w.G + g * gstr, w.gn[g], w.prow + wid * rb);
   __syncthreads();
   // F_g[k][j] = sum_{l <= j} E_g[k][l] Li_g[j][l]
   for (int g = 0; g < sc.n_groups; ++g) {
     const int n = w.gn[g], cnt = sc.cpl_n[g] * n;
-    const Real* Lb = w.G + g * pg * ldg;
+    const Real* Lb = w.G + g * gstr;
     const Real* Eb = w.E + g * cm * ldg;
     Real* Fb = w.H + g * cm * ldg;
     for (int e = tid; e < cnt; e += nth) {
       const int k = e / n, j = e - k * n;
       Real acc = 0;
-      for (int l = 0; l <= j; ++l) acc += Eb[k * ldg + l] * Lb[j * ldg + l];
+      for (int l = 0; l <= j; ++l) acc += Eb[k * ldg + l] * Lb[tri(j, l)];
       Fb[k * ldg + j] = acc;
     }
   }
@@ -690,23 +691,23 @@ template <class Real> __device__ void factor(const DevScene& sc, WS<Real>& w) {
         const Real* fb = w.H + g * cm * ldg + sc.sep_k[b][pb] * ldg;
         for (int j = 0; j < w.gn[g]; ++j) acc += fa[j] * fb[j];
       }
-    w.S[a * lds + b] -= acc;
+    w.S[tri(a, b)] -= acc;
   }
   __syncthreads();
   // Lsi in place over S, the whole CTA
-  if (ss > 0) chol_inv_inplace<1>(w.S, ss, lds, w.prow);
+  if (ss > 0) chol_inv_inplace<1>(w.S, ss, w.prow);
 }
 
 // v <- A^-1 v with the inverse-form block-arrowhead factor (row-parallel phases)
 template <class Real> __device__ void arrow_solve(const DevScene& sc, WS<Real>& w, Real* v) {
   const int tid = threadIdx.x, nth = blockDim.x;
-  const int pg = sc.pg, ss = sc.ss, ldg = sc.ldg, lds = sc.lds, cm = sc.cmax, mc = w.ints[1];
+  const int gstr = tri_size(sc.pg), ss = sc.ss, ldg = sc.ldg, cm = sc.cmax, mc = w.ints[1];
   Real* y = w.tmp;
   Real* z = w.tmp2;
   // y_g = Li_g b_g
   for (int r = tid; r < mc; r += nth) {
     const int g = w.rgrp[r], r0 = w.g0[g], i = r - r0;
-    const Real* Li = w.G + g * pg * ldg + i * ldg;
+    const Real* Li = w.G + g * gstr + tri(i, 0);
     Real acc = 0;
     for (int l = 0; l <= i; ++l) acc += Li[l] * v[r0 + l];
     y[r] = acc;
@@ -725,7 +726,7 @@ template <class Real> __device__ void arrow_solve(const DevScene& sc, WS<Real>& 
   __syncthreads();
   // y_s = Lsi b_s'
   for (int a = tid; a < ss; a += nth) {
-    const Real* La = w.S + a * lds;
+    const Real* La = w.S + tri(a, 0);
     Real acc = 0;
     for (int b = 0; b <= a; ++b) acc += La[b] * z[b];
     y[mc + a] = acc;
@@ -734,7 +735,7 @@ template <class Real> __device__ void arrow_solve(const DevScene& sc, WS<Real>& 
   // x_s = Lsi^T y_s
   for (int a = tid; a < ss; a += nth) {
     Real acc = 0;
-    for (int b = a; b < ss; ++b) acc += w.S[b * lds + a] * y[mc + b];
+    for (int b = a; b < ss; ++b) acc += w.S[tri(b, a)] * y[mc + b];
     v[mc + a] = acc;
   }
   __syncthreads();
@@ -750,9 +751,9 @@ template <class Real> __device__ void arrow_solve(const DevScene& sc, WS<Real>& 
   // x_g = Li_g^T r_g
   for (int r = tid; r < mc; r += nth) {
     const int g = w.rgrp[r], r0 = w.g0[g], i = r - r0, n = w.gn[g];
-    const Real* Lb = w.G + g * pg * ldg;
+    const Real* Lb = w.G + g * gstr;
     Real acc = 0;
-    for (int l = i; l < n; ++l) acc += Lb[l * ldg + i] * z[r0 + l];
+    for (int l = i; l < n; ++l) acc += Lb[tri(l, i)] * z[r0 + l];
     v[r] = acc;
   }
   __syncthreads();
@@ -986,9 +987,9 @@ __global__ void __launch_bounds__(128) step_kernel(const DevScene scp, const Ste
     for (int i = tid; i < sc.m_max; i += nth) tp[tl.off_lam + i] = Real(0);
     __syncthreads();
     for (int i = tid; i < m; i += nth) tp[tl.off_lam + w.meta[4 * i + 3]] = w.lk[i];
-    for (int i = tid; i < sc.n_groups * sc.pg * sc.ldg; i += nth) tp[tl.off_G + i] = w.G[i];
+    for (int i = tid; i < sc.n_groups * tri_size(sc.pg); i += nth) tp[tl.off_G + i] = w.G[i];
     for (int i = tid; i < sc.n_groups * sc.cmax * sc.ldg; i += nth) tp[tl.off_H + i] = w.H[i];
-    for (int i = tid; i < sc.ss * sc.lds; i += nth) tp[tl.off_S + i] = w.S[i];
+    for (int i = tid; i < tri_size(sc.ss); i += nth) tp[tl.off_S + i] = w.S[i];
   }
   // outputs: q+ (normalised quaternions), u+, lambda+, impulses h lambda, contact ids
   Real* so = reinterpret_cast<Real*>(a.state_out);
@@ -1171,9 +1172,9 @@ __global__ void __launch_bounds__(128) adjoint_kernel(const DevScene scp, const 
   __syncthreads();
   evaluate(sc, w, w.uk, w.lk, h);      // J (with E at u*), poses at q+
   // factor from the tape
-  for (int i = tid; i < sc.n_groups * sc.pg * sc.ldg; i += nth) w.G[i] = tp[tl.off_G + i];
+  for (int i = tid; i < sc.n_groups * tri_size(sc.pg); i += nth) w.G[i] = tp[tl.off_G + i];
   for (int i = tid; i < sc.n_groups * sc.cmax * sc.ldg; i += nth) w.H[i] = tp[tl.off_H + i];
-  for (int i = tid; i < sc.ss * sc.lds; i += nth) w.S[i] = tp[tl.off_S + i];
+  for (int i = tid; i < tri_size(sc.ss); i += nth) w.S[i] = tp[tl.off_S + i];
   // incoming cotangent: normalisation Jacobian of the output quaternions, then g
   Real* gq = w.lb;      // the best-iterate buffer is free in the adjoint; m_max >= 7 nb
   Real* gu = w.du;
@@ -1260,7 +1261,8 @@ __global__ void __launch_bounds__(128) adjoint_kernel(const DevScene scp, const 
     for (int i = mc + 5 * sc.nj + tid; i < m; i += nth) dctl[(size_t)(i - mc - 5 * sc.nj) * ld + world] = -wl[i];
   // dL/dq-: per-row and per-body dual-number derivatives, summed in a fixed order
   const bool trunc = sc.pullback == 1;
-  Real* item = w.G;     // factor no longer needed: m * 14 row items + nb * 7 body items
+  Real* item = w.G;     // the factor (G, E, H, S, one carved run) is no longer needed:
+                        // m * 14 row items; nb * 7 body items go to rhs
   for (int e = tid; e < m * 14; e += nth) {
     int i = e / 14, r = e % 14, side = r / 7, c = r % 7;
     int b = side == 0 ? w.meta[4 * i + 1] : w.meta[4 * i + 2];

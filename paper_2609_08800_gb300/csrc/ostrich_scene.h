@@ -42,7 +42,7 @@ struct DevScene {
   // static coupling between groups and separator rows (the separator rows are always
   // present): group g couples to separator rows cpl_row[g][0 .. cpl_n[g]); separator row
   // a belongs to the lists of sep_n[a] <= 2 groups, at (sep_g[a][i], sep_k[a][i])
-  int ldg, lds, cmax;                    // odd leading dimensions of group / separator blocks
+  int ldg, lds, cmax;                    // odd row lengths of the coupling blocks (ldg); cmax coupling rows
   int cpl_n[NB_CAP];
   unsigned char cpl_row[NB_CAP][SEP_CAP];
   unsigned char sep_n[SEP_CAP], sep_g[SEP_CAP][2], sep_k[SEP_CAP][2];
@@ -106,6 +106,12 @@ struct AdjArgs {
 // Tape record of one world for one step: inputs, returned iterate and the Schur factor
 // (block-arrowhead, in inverse form).
 // All counts in Real elements.
+// Packed lower-triangular storage of the symmetric Schur blocks and their inverse
+// factors: element (i, j), j <= i, of an n x n block sits at tri(i, j); a block takes
+// tri_size(n) entries and its row i is contiguous.
+__host__ __device__ inline int tri(int i, int j) { return ((i * (i + 1)) >> 1) + j; }
+__host__ __device__ inline int tri_size(int n) { return (n * (n + 1)) >> 1; }
+
 struct TapeLayout {
   int off_qm, off_um, off_ubar, off_u, off_lam, off_G, off_H, off_S, total;
 };
@@ -118,9 +124,9 @@ inline __host__ __device__ TapeLayout tape_layout(const DevScene& s) {
   t.off_ubar = o; o += s.n_servo > 0 ? s.n_servo : 1;
   t.off_u = o; o += 6 * s.nb;
   t.off_lam = o; o += s.m_max;
-  t.off_G = o; o += s.n_groups * s.pg * s.ldg;       // inverse Cholesky factors L_g^-1 of the groups
+  t.off_G = o; o += s.n_groups * tri_size(s.pg);    // inverse Cholesky factors L_g^-1 of the groups (packed)
   t.off_H = o; o += s.n_groups * s.cmax * s.ldg;     // F_g = E_g L_g^-T (coupled separator rows)
-  t.off_S = o; o += s.ss * s.lds;                    // inverse Cholesky factor of the reduced separator
+  t.off_S = o; o += tri_size(s.ss);                  // inverse Cholesky factor of the reduced separator (packed)
   o = (o + 3) & ~3;   // 16-byte multiple per world for FP32
   t.total = o;
   return t;

@@ -75,9 +75,10 @@ template <class Real> __host__ __device__ size_t ws_bytes(const DevScene& s) {
   b += 2 * sz(sizeof(int), ng) + sz(sizeof(int), m);
   // the adjoint's VJP items (14 per row) reuse G, E, H and S, which are carved in one run
   int cm = s.cmax > 0 ? s.cmax : 1, ldg = s.ldg > 0 ? s.ldg : 1;
-  int gsz = ng * tri_size(pg), rest = 2 * ng * cm * ldg + tri_size(ss);
+  int esz = ng * cm * ldg > sep_scratch(s) ? ng * cm * ldg : sep_scratch(s);   // E also holds the separator scratch
+  int gsz = ng * tri_size(pg), rest = esz + ng * cm * ldg + tri_size(ss);
   if (gsz + rest < 14 * m) gsz = 14 * m - rest;
-  b += sz(sizeof(Real), gsz) + 2 * sz(sizeof(Real), ng * cm * ldg) + sz(sizeof(Real), tri_size(ss));
+  b += sz(sizeof(Real), gsz) + sz(sizeof(Real), esz) + sz(sizeof(Real), ng * cm * ldg) + sz(sizeof(Real), tri_size(ss));
   b += sz(sizeof(Real), 4 * (pg > ss ? pg : ss)) + 2 * sz(sizeof(Real), m);
   b += sz(sizeof(Real), 64) + sz(sizeof(int), 16) + sz(sizeof(Real), 8);
   b += 256;
@@ -106,9 +107,10 @@ template <class Real> __host__ __device__ WS<Real> ws_carve(char* base, const De
   w.bgrp = carve<int>(p, nb); w.bsepn = carve<int>(p, nb); w.bsep = carve<int>(p, nb * ss);
   w.g0 = carve<int>(p, ng); w.gn = carve<int>(p, ng); w.rgrp = carve<int>(p, m);
   int cm = s.cmax > 0 ? s.cmax : 1, ldg = s.ldg > 0 ? s.ldg : 1;
-  int gsz = ng * tri_size(pg), rest = 2 * ng * cm * ldg + tri_size(ss);
+  int esz = ng * cm * ldg > sep_scratch(s) ? ng * cm * ldg : sep_scratch(s);
+  int gsz = ng * tri_size(pg), rest = esz + ng * cm * ldg + tri_size(ss);
   if (gsz + rest < 14 * m) gsz = 14 * m - rest;
-  w.G = carve<Real>(p, gsz); w.E = carve<Real>(p, ng * cm * ldg); w.H = carve<Real>(p, ng * cm * ldg);
+  w.G = carve<Real>(p, gsz); w.E = carve<Real>(p, esz); w.H = carve<Real>(p, ng * cm * ldg);
   w.S = carve<Real>(p, tri_size(ss));
   w.prow = carve<Real>(p, 4 * (pg > ss ? pg : ss));
   w.tmp = carve<Real>(p, m); w.tmp2 = carve<Real>(p, m);
@@ -631,34 +633,39 @@ template <int TEAM, class Real> __device__ void chol_inv_inplace(Real* A, int n,
     const Real akk = A[tri(k, k)];
     const Real d = ssqrt(akk > Real(0) ? akk : Real(1e-30));
     const Real inv = Real(1) / d;
-    if (TEAM) __syncthreads(); else __syncwarp();       // everyone has read the pivot
-    for (int e = t; e < n; e += T) {
+    const Real xkk = Real(1) / d;           // X[k][k], known to every thread
+    for (int e = t; e < n; e += T) {        // the pivot entry itself is left for pass 2
       if (e > k) colbuf[e] = A[tri(e, k)] * inv;
       else if (e < k) A[tri(k, e)] = A[tri(k, e)] / d;
-      else A[tri(k, k)] = Real(1) / d;
     }
     if (TEAM) __syncthreads(); else __syncwarp();
-    const int nr = n - k - 1;
-    for (int e = t; e < nr * n; e += T) {
-      const int r = e / n, j = e - r * n, i = k + 1 + r;
-      if (j > i) continue;
-      const Real lik = colbuf[i];
-      if (j < k) A[tri(i, j)] -= lik * A[tri(k, j)];
-      else if (j == k) A[tri(i, k)] = -(lik * A[tri(k, k)]);
-      else A[tri(i, j)] -= lik * colbuf[j];
+    if (t == 0) A[tri(k, k)] = xkk;
+    // lanes own columns (j = lane, lane + 32, ...), warps take every nw-th row
+    const int nw = T >> 5, lane = t & 31;
+    for (int j = lane; j < n; j += 32) {
+      // per column: the multiplier of l_ik (X[k][j], X[k][k] or l_jk) and whether the
+      // entry keeps its value (no branch inside the row loop)
+      const Real coef = j < k ? A[tri(k, j)] : (j == k ? xkk : colbuf[j]);
+      const bool keep = j != k;
+      for (int i = (k + 1 > j ? k + 1 : j) + (t >> 5); i < n; i += nw) {
+        const Real lik = colbuf[i];
+        Real* aij = A + tri(i, j);
+        const Real old = keep ? *aij : Real(0);
+        *aij = old - lik * coef;
+      }
     }
     if (TEAM) __syncthreads(); else __syncwarp();
   }
 }
 
 // Block-arrowhead factorisation kept in inverse form for row-parallel solves:
-//   Li_g = L_g^-1 with L_g L_g^T = A_g (contact groups; stored in G),
+//   Li_g = L_g^-1 with L_g L_g^T = A_g (contact groups; stored in G, packed),
 //   F_g = E_g L_g^-T (coupled separator rows; stored in H),
-//   Lsi = L_s^-1 with L_s L_s^T = S - sum_g F_g F_g^T (stored in S).
-// The group and separator blocks are factored in their own storage, then inverted into
-// the scratch E (groups; the coupling E_g is consumed first) and prow (separator).
-template <class Real> __device__ void factor(const DevScene& sc, WS<Real>& w) {
+//   S'^-1 with S' = S - sum_g F_g F_g^T, the reduced separator (stored in S, packed
+//   symmetric), from its Cholesky factor.
+template <class Real> __device__ void factor(const DevScene& sc, WS<Real>& w, double h) {
   const int tid = threadIdx.x, nth = blockDim.x, wid = tid >> 5, nw = (blockDim.x + 31) >> 5;
+  const Real hR = Real(h);
   const int pg = sc.pg, ss = sc.ss, ldg = sc.ldg, cm = sc.cmax, gstr = tri_size(pg);
   const int rb = pg > ss ? pg : ss;
   // Li_g in place: each warp its groups
@@ -694,8 +701,22 @@ template <class Real> __device__ void factor(const DevScene& sc, WS<Real>& w) {
     w.S[tri(a, b)] -= acc;
   }
   __syncthreads();
-  // Lsi in place over S, the whole CTA
-  if (ss > 0) chol_inv_inplace<1>(w.S, ss, w.prow);
+  if (ss <= 0) return;
+  {
+    // L_s^-1 in place, then S'^-1 = L_s^-T L_s^-1 from a copy (in E, free once F is formed)
+    chol_inv_inplace<1>(w.S, ss, w.prow);
+    Real* Lc = w.E;
+    for (int e = tid; e < tri_size(ss); e += nth) Lc[e] = w.S[e];
+    __syncthreads();
+    for (int e = tid; e < ss * ss; e += nth) {
+      const int a = e / ss, b = e - a * ss;
+      if (b > a) continue;
+      Real acc = 0;
+      for (int k = a; k < ss; ++k) acc += Lc[tri(k, a)] * Lc[tri(k, b)];
+      w.S[tri(a, b)] = acc;
+    }
+    __syncthreads();
+  }
 }
 
 // v <- A^-1 v with the inverse-form block-arrowhead factor (row-parallel phases)
@@ -724,18 +745,12 @@ template <class Real> __device__ void arrow_solve(const DevScene& sc, WS<Real>& 
     z[a] = acc;
   }
   __syncthreads();
-  // y_s = Lsi b_s'
+  // x_s = S'^-1 b_s' (symmetric, packed lower triangle)
   for (int a = tid; a < ss; a += nth) {
-    const Real* La = w.S + tri(a, 0);
+    const Real* Sa = w.S + tri(a, 0);
     Real acc = 0;
-    for (int b = 0; b <= a; ++b) acc += La[b] * z[b];
-    y[mc + a] = acc;
-  }
-  __syncthreads();
-  // x_s = Lsi^T y_s
-  for (int a = tid; a < ss; a += nth) {
-    Real acc = 0;
-    for (int b = a; b < ss; ++b) acc += w.S[tri(b, a)] * y[mc + b];
+    for (int b = 0; b <= a; ++b) acc += Sa[b] * z[b];
+    for (int b = a + 1; b < ss; ++b) acc += w.S[tri(b, a)] * z[b];
     v[mc + a] = acc;
   }
   __syncthreads();
@@ -923,7 +938,7 @@ __global__ void __launch_bounds__(128) step_kernel(const DevScene scp, const Ste
     if (merit < tol2) { conv = 1; break; }
     // Schur step, Eq. (12): (h J M^-1 J^T + C + delta) dl = J M^-1 r_dyn - rhat
     assemble(sc, w, h);
-    factor(sc, w);
+    factor(sc, w, h);
     for (int i = tid; i < m; i += nth) {
       const Real* Ji = w.J + 12 * i;
       int b0 = w.meta[4 * i + 1], b1 = w.meta[4 * i + 2];
@@ -979,7 +994,7 @@ __global__ void __launch_bounds__(128) step_kernel(const DevScene scp, const Ste
   status |= (uint32_t)w.ints[7];
   if (tpw) {
     assemble(sc, w, h);
-    factor(sc, w);
+    factor(sc, w, h);
     Real* tp = tpw;
     for (int i = tid; i < 7 * nb; i += nth) tp[tl.off_qm + i] = w.qm[i];
     for (int i = tid; i < 6 * nb; i += nth) { tp[tl.off_um + i] = w.um[i]; tp[tl.off_u + i] = w.uk[i]; }

@@ -48,6 +48,12 @@ struct DevScene {
   unsigned char sep_n[SEP_CAP], sep_g[SEP_CAP][2], sep_k[SEP_CAP][2];
 };
 
+// Packed lower-triangular storage of the symmetric Schur blocks and their inverse
+// factors: element (i, j), j <= i, of an n x n block sits at tri(i, j); a block takes
+// tri_size(n) entries and its row i is contiguous.
+__host__ __device__ inline int tri(int i, int j) { return ((i * (i + 1)) >> 1) + j; }
+__host__ __device__ inline int tri_size(int n) { return (n * (n + 1)) >> 1; }
+
 // Derived layout of a filled scene: groups, block sizes, the static coupling lists.
 inline void finish_scene(DevScene& s) {
   s.n_groups = 0; s.pg = 0;
@@ -84,6 +90,10 @@ inline void finish_scene(DevScene& s) {
   for (int g = 0; g < s.n_groups; ++g) if (s.cpl_n[g] > s.cmax) s.cmax = s.cpl_n[g];
 }
 
+// Scratch the separator inverse needs (in the coupling block E, free once F is formed):
+// a copy of the inverse factor.
+__host__ __device__ inline int sep_scratch(const DevScene& s) { return tri_size(s.ss); }
+
 // Arguments of one launch of the step / adjoint kernels.
 // World selection: without a list, CTA b steps world world0 + b and records into the
 // tape slot that `tape` points at.  With a list (device arrays of gridDim entries), CTA
@@ -106,12 +116,6 @@ struct AdjArgs {
 // Tape record of one world for one step: inputs, returned iterate and the Schur factor
 // (block-arrowhead, in inverse form).
 // All counts in Real elements.
-// Packed lower-triangular storage of the symmetric Schur blocks and their inverse
-// factors: element (i, j), j <= i, of an n x n block sits at tri(i, j); a block takes
-// tri_size(n) entries and its row i is contiguous.
-__host__ __device__ inline int tri(int i, int j) { return ((i * (i + 1)) >> 1) + j; }
-__host__ __device__ inline int tri_size(int n) { return (n * (n + 1)) >> 1; }
-
 struct TapeLayout {
   int off_qm, off_um, off_ubar, off_u, off_lam, off_G, off_H, off_S, total;
 };
@@ -126,7 +130,7 @@ inline __host__ __device__ TapeLayout tape_layout(const DevScene& s) {
   t.off_lam = o; o += s.m_max;
   t.off_G = o; o += s.n_groups * tri_size(s.pg);    // inverse Cholesky factors L_g^-1 of the groups (packed)
   t.off_H = o; o += s.n_groups * s.cmax * s.ldg;     // F_g = E_g L_g^-T (coupled separator rows)
-  t.off_S = o; o += tri_size(s.ss);                  // inverse Cholesky factor of the reduced separator (packed)
+  t.off_S = o; o += tri_size(s.ss);                  // inverse of the reduced separator (packed symmetric)
   o = (o + 3) & ~3;   // 16-byte multiple per world for FP32
   t.total = o;
   return t;

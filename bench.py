@@ -255,7 +255,7 @@ def run_ours(args, rank, world_size, local_rank):
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": f"robot_over_box_{W}_worlds_fp32_fwd_adj_chunk10", "worlds_per_gpu": W,
                    "steps_per_chunk": CHUNK, "h": H, "newton_budget": cfg.budget,
-                   "threads_per_world": threads,
+                   "threads_per_world": threads, "schedule": getattr(ctx, "schedule", 0),
                    "parallelism": f"replicas{world_size}",
                    "l2": f"tape of one chunk {ctx.tape_bytes() * CHUNK / 1e9:.2f} GB > 129 MB L2 (no flush needed)"},
         "gpu_launches": 2 * CHUNK * args.steps,
@@ -388,6 +388,7 @@ def run_terrain(args, torch):
     cfg = S.SolverConfig(tol=FP32_TOL, pullback=S.PULLBACK_TRUNCATED)
     ctx = Context(scene, cfg, W, dtype="f32", tape_slots=CHUNK)
     threads = tune.apply(ctx) or 64
+    schedule = getattr(ctx, "schedule", 0)
     chunk = Chunk(ctx, torch, W)
     s0 = torch.tensor(states, dtype=torch.float32, device="cuda")
     c0 = torch.tensor(ctl_all[:CHUNK], device="cuda")
@@ -413,7 +414,7 @@ def run_terrain(args, torch):
     iters = np.stack([t.cpu().numpy() for t in chunk.iters])
     ctx.close()
     return {"workload": f"mesh_terrain_{W}_worlds_fp32_fwd_adj_chunk10_truncated_pullback", "value": W * CHUNK / (ms * 1e-3),
-            "unit": UNIT, "ms_per_chunk": ms, "threads_per_world": threads,
+            "unit": UNIT, "ms_per_chunk": ms, "threads_per_world": threads, "schedule": schedule,
             "step_ms_avg": statistics.mean(e[0].elapsed_time(e[1]) for k in range(K) for e in evs[k]),
             "adjoint_ms_avg": statistics.mean(e[0].elapsed_time(e[1]) for k in range(K) for e in eva[k]),
             "newton_iters_mean": float((iters & 0xFFFF).mean()), "active_rows_mean": float((iters >> 16).mean())}

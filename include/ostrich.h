@@ -108,6 +108,14 @@ ostrich_status ostrich_layout(const ostrich_ctx* ctx, int32_t out[4]);
 /* Threads per world (32, 64 or 128) used by both kernels; the autotuner's knob. */
 ostrich_status ostrich_set_threads(ostrich_ctx* ctx, int threads);
 
+/* Launch schedule of ostrich_step (an autotuner knob; results do not depend on it):
+ * 0 one CTA per world (default); 1 persistent: as many CTAs as fit on the device take
+ * worlds from a device work counter, heaviest first by each world's Newton iterations in
+ * the previous step (a one-CTA counting sort launched before the step).  The list form
+ * always uses one CTA per entry.  ENOMEM if the context's small schedule buffers cannot
+ * be allocated. */
+ostrich_status ostrich_set_schedule(ostrich_ctx* ctx, int schedule);
+
 /* One forward step of every world (Sec. III-C): state_in -> state_out, with
  * h the time step.  impulses_out, contact_ids_out, world_status and iters_out
  * (per world: Newton iterations | active rows << 16) may be NULL.  tape_slot >= 0

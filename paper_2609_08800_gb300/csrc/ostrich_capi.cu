@@ -26,11 +26,14 @@ struct ostrich_ctx {
   std::vector<unsigned char> slot_written;
   std::vector<double> slot_h;
   double* trace = nullptr;
+  int schedule = 0;
+  int32_t* d_sched = nullptr;      // persistent schedule: [queue, cost[n_worlds], order[n_worlds]]
   char err[512] = {0};
   // device memory is released with the context, on every path out of ostrich_create too
   ~ostrich_ctx() {
     if (tape) cudaFree(tape);
     if (d_heights) cudaFree(d_heights);
+    if (d_sched) cudaFree(d_sched);
   }
 };
 
@@ -157,6 +160,20 @@ ostrich_status ostrich_set_threads(ostrich_ctx* c, int threads) {
   return OSTRICH_OK;
 }
 
+ostrich_status ostrich_set_schedule(ostrich_ctx* c, int schedule) {
+  if (!c) return OSTRICH_EINVAL;
+  if (schedule != 0 && schedule != 1) return fail(c, OSTRICH_EINVAL, "schedule must be 0 or 1");
+  if (schedule == 1 && !c->d_sched) {
+    void* p = nullptr;
+    const size_t bytes = sizeof(int32_t) * (1 + 2 * (size_t)c->n_worlds);
+    if (cudaMalloc(&p, bytes) != cudaSuccess) { cudaGetLastError(); return fail(c, OSTRICH_ENOMEM, "schedule buffers"); }
+    if (cudaMemset(p, 0, bytes) != cudaSuccess) { cudaGetLastError(); cudaFree(p); return fail(c, OSTRICH_ECUDA, "schedule buffers"); }
+    c->d_sched = static_cast<int32_t*>(p);
+  }
+  c->schedule = schedule;
+  return OSTRICH_OK;
+}
+
 static void* slot_ptr(ostrich_ctx* c, int slot) {
   return static_cast<char*>(c->tape) + (size_t)slot * c->n_worlds * c->tape_world_elems * elem_size(c->dtype);
 }
@@ -175,6 +192,9 @@ ostrich_status ostrich_step(ostrich_ctx* c, const void* state_in, const void* co
   a.tape = tape_slot >= 0 ? slot_ptr(c, tape_slot) : nullptr;
   a.ld = c->ld; a.n_worlds = c->n_worlds; a.world0 = 0; a.h = h;
   a.trace = c->trace;
+  if (c->schedule == 1 && c->d_sched) {
+    a.queue = c->d_sched; a.cost = c->d_sched + 1; a.order = c->d_sched + 1 + c->n_worlds;
+  }
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   cudaError_t e = c->dtype == OSTRICH_F64 ? ost::launch_step<double>(c->sc, a, c->threads, st)
                                           : ost::launch_step<float>(c->sc, a, c->threads, st);

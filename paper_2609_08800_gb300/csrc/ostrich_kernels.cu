@@ -891,20 +891,17 @@ __device__ __forceinline__ void scene_to_shared(const DevScene& src, DevScene& d
   __syncthreads();
 }
 
+// One world's step; `item` is the launch's work index (the CTA index of a one-CTA-per-
+// world launch, or the index a persistent CTA took from the queue).
 template <class Real>
-__global__ void __launch_bounds__(128) step_kernel(const DevScene scp, const StepArgs a) {
-  extern __shared__ __align__(16) char smem[];
-  __shared__ __align__(16) DevScene ssc;
-  scene_to_shared(scp, ssc);
-  const DevScene& sc = ssc;
-  WS<Real> w = ws_carve<Real>(smem, sc);
+__device__ __forceinline__ void step_world(const DevScene& sc, WS<Real>& w, const StepArgs& a, int item) {
   const int tid = threadIdx.x, nth = blockDim.x;
-  const int world = a.list ? a.list[blockIdx.x] : a.world0 + blockIdx.x;
+  const int world = a.list ? a.list[item] : a.world0 + item;
   if (world < 0 || world >= a.n_worlds) return;
   const TapeLayout tl = tape_layout(sc);
   Real* tpw = nullptr;    // this world's tape record (nullptr: the step records nothing)
   if (a.tape) {
-    const int slot = a.list ? (a.list_slot ? a.list_slot[blockIdx.x] : -1) : 0;
+    const int slot = a.list ? (a.list_slot ? a.list_slot[item] : -1) : 0;
     if (slot >= 0 && (!a.list || slot < a.tape_slots))
       tpw = reinterpret_cast<Real*>(a.tape) + ((size_t)slot * a.n_worlds + world) * tl.total;
   }
@@ -1031,7 +1028,55 @@ __global__ void __launch_bounds__(128) step_kernel(const DevScene scp, const Ste
     for (int sl = tid; sl < sc.n_slots; sl += nth) a.ids[(size_t)sl * ld + world] = w.sact[sl] ? w.sid[sl] : -1;
   if (tid == 0) {
     if (a.status) a.status[world] = status;
+    if (a.cost) a.cost[world] = k;
     if (a.iters) a.iters[world] = k | (m << 16);
+  }
+}
+
+template <class Real>
+__global__ void __launch_bounds__(128) step_kernel(const DevScene scp, const StepArgs a) {
+  extern __shared__ __align__(16) char smem[];
+  __shared__ __align__(16) DevScene ssc;
+  scene_to_shared(scp, ssc);
+  WS<Real> w = ws_carve<Real>(smem, ssc);
+  if (!a.queue) {
+    step_world<Real>(ssc, w, a, blockIdx.x);
+    return;
+  }
+  // persistent: take work items until the queue is exhausted (no CTA waits on another)
+  for (;;) {
+    __syncthreads();
+    if (threadIdx.x == 0) w.ints[15] = atomicAdd(a.queue, 1);
+    __syncthreads();
+    const int it = w.ints[15];
+    if (it >= a.n_items) break;
+    step_world<Real>(ssc, w, a, a.order ? a.order[it] : it);
+  }
+}
+
+// Heaviest-first order of the worlds by their previous step's Newton iterations (a
+// counting sort over 0..63, one CTA): worlds that took the most iterations start first,
+// so the last wave is short.  Worlds of equal count may come in any order; a world's
+// result does not depend on when it runs.
+__global__ void lpt_order_kernel(const int32_t* cost, int n, int32_t* order) {
+  __shared__ int bins[64], start[64];
+  for (int i = threadIdx.x; i < 64; i += blockDim.x) bins[i] = 0;
+  __syncthreads();
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    int c = cost[i];
+    c = c < 0 ? 0 : (c > 63 ? 63 : c);
+    atomicAdd(&bins[c], 1);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int acc = 0;
+    for (int c = 63; c >= 0; --c) { start[c] = acc; acc += bins[c]; }
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    int c = cost[i];
+    c = c < 0 ? 0 : (c > 63 ? 63 : c);
+    order[atomicAdd(&start[c], 1)] = i;
   }
 }
 
@@ -1327,6 +1372,25 @@ cudaError_t launch_step(const DevScene& sc, const StepArgs& a, int threads, cuda
   if (e != cudaSuccess) return e;
   int n = a.list ? a.n_list : a.n_worlds - a.world0;
   if (n <= 0) return cudaSuccess;
+  if (a.queue) {
+    // persistent: as many CTAs as fit on the device at once, fed from the queue
+    int dev = 0, sms = 0, per_sm = 0;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, step_kernel<Real>, threads, smem)) != cudaSuccess)
+      return e;
+    if (per_sm < 1) per_sm = 1;
+    int grid = sms * per_sm < n ? sms * per_sm : n;
+    if ((e = cudaMemsetAsync(a.queue, 0, sizeof(int), st)) != cudaSuccess) return e;
+    if (a.order && a.cost) {
+      lpt_order_kernel<<<1, 1024, 0, st>>>(a.cost + a.world0, n, const_cast<int32_t*>(a.order));
+      if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    StepArgs b = a;
+    b.n_items = n;
+    step_kernel<Real><<<grid, threads, smem, st>>>(sc, b);
+    return cudaGetLastError();
+  }
   step_kernel<Real><<<n, threads, smem, st>>>(sc, a);
   return cudaGetLastError();
 }

@@ -106,6 +106,10 @@ struct StepArgs {
   int ld, n_worlds, world0; double h;
   double* trace = nullptr;   // optional diagnostic: merit of each iterate, (budget + 2) per world
   const int32_t* list = nullptr; const int32_t* list_slot = nullptr; int n_list = 0, tape_slots = 0;
+  // persistent schedule (queue != nullptr): gridDim CTAs take the work items 0 .. n_items-1
+  // from the counter *queue (zero at launch) in the order order[] (or 0, 1, ...); each
+  // world's Newton iteration count goes to cost[] for the next step's order
+  int* queue = nullptr; const int32_t* order = nullptr; int32_t* cost = nullptr; int n_items = 0;
 };
 struct AdjArgs {
   const void* tape; const void* dL_dnext; void* dL_dstate; void* dL_dcontrols;

@@ -66,6 +66,7 @@ def lib():
         L.ostrich_create.restype = ctypes.c_int
         L.ostrich_layout.argtypes = [_vp, ctypes.POINTER(ctypes.c_int32)]
         L.ostrich_set_threads.argtypes = [_vp, ctypes.c_int]
+        L.ostrich_set_schedule.argtypes = [_vp, ctypes.c_int]
         L.ostrich_step.argtypes = [_vp, _vp, _vp, ctypes.c_double, _vp, _vp, _vp, _vp, _vp, ctypes.c_int, _vp]
         L.ostrich_adjoint.argtypes = [_vp, ctypes.c_int, _vp, ctypes.c_double, _vp, _vp, _vp]
         L.ostrich_step_list.argtypes = [_vp, _vp, _vp, ctypes.c_double, _vp, _vp, _vp, _vp, _vp, _vp, _vp,
@@ -83,7 +84,7 @@ def lib():
         L.ostrich_destroy.argtypes = [_vp]
         L.ostrich_step_adjoint_noalloc.argtypes = [ctypes.POINTER(SceneDesc), ctypes.POINTER(SolverCfg), ctypes.c_int,
                                                    ctypes.c_int, _vp, _vp, ctypes.c_double, _vp, _vp, _vp, _vp, _vp]
-        for name in ("ostrich_layout", "ostrich_set_threads", "ostrich_step", "ostrich_adjoint", "ostrich_tape_clear",
+        for name in ("ostrich_layout", "ostrich_set_threads", "ostrich_set_schedule", "ostrich_step", "ostrich_adjoint", "ostrich_tape_clear",
                      "ostrich_step_adjoint_noalloc", "ostrich_step_list", "ostrich_adjoint_list"):
             getattr(L, name).restype = ctypes.c_int
         _lib = L
@@ -198,6 +199,12 @@ class Context:
 
     def set_threads(self, threads):
         self._check(lib().ostrich_set_threads(self._h, int(threads)), "ostrich_set_threads")
+        self.threads = int(threads)
+
+    def set_schedule(self, schedule):
+        """0: one CTA per world; 1: persistent CTAs, heaviest worlds first."""
+        self._check(lib().ostrich_set_schedule(self._h, int(schedule)), "ostrich_set_schedule")
+        self.schedule = int(schedule)
 
     def ostrich_step(self, state_in, controls, h, state_out, impulses=None, ids=None, status=None, iters=None,
                      tape_slot=-1, stream=None):

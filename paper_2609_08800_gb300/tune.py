@@ -1,4 +1,5 @@
-"""Autotuner for the launch shape: threads per world (32, 64 or 128).
+"""Autotuner for the launch shape: threads per world (32, 64 or 128) and the schedule
+(one CTA per world, or persistent CTAs taking the heaviest worlds first).
 
 One CTA steps one world; its threads split the rows of the Schur blocks, the
 row-parallel solves and the per-body reductions.  More threads shorten each phase
@@ -44,13 +45,18 @@ def _load(path):
         return {}
 
 
-def lookup(ctx):
+def lookup_entry(ctx):
     k = key(ctx)
     for path in (cache_path(), SHIPPED):
         entry = _load(path).get(k)
         if entry:
-            return int(entry["threads"])
+            return entry
     return None
+
+
+def lookup(ctx):
+    entry = lookup_entry(ctx)
+    return int(entry["threads"]) if entry else None
 
 
 def store(k, entry, path=None):
@@ -79,26 +85,37 @@ def time_step(ctx, state, controls, h, reps=3, stream=None):
     return e0.elapsed_time(e1) / reps
 
 
-def tune(ctx, state, controls, h, candidates=CANDIDATES, reps=3, persist=True, path=None):
-    """Time each candidate on (state, controls), set the fastest on ctx, record it."""
+SCHEDULES = (0, 1)
+
+
+def tune(ctx, state, controls, h, candidates=CANDIDATES, reps=3, persist=True, path=None, schedules=SCHEDULES):
+    """Time each (threads, schedule) candidate on (state, controls), set the fastest on ctx,
+    record it.  Returns (best threads, {threads: ms} at the best schedule)."""
     times = {}
-    for t in candidates:
-        ctx.set_threads(t)
-        times[t] = time_step(ctx, state, controls, h, reps)
-    best = min(times, key=times.get)
-    ctx.set_threads(best)
+    for sch in schedules:
+        ctx.set_schedule(sch)
+        for t in candidates:
+            ctx.set_threads(t)
+            times[(t, sch)] = time_step(ctx, state, controls, h, reps)
+    best_t, best_s = min(times, key=times.get)
+    ctx.set_threads(best_t)
+    ctx.set_schedule(best_s)
     if persist:
-        store(key(ctx), {"threads": best, "ms": {str(t): round(v, 4) for t, v in times.items()},
+        store(key(ctx), {"threads": best_t, "schedule": best_s,
+                         "ms": {f"{t}/{sch}": round(v, 4) for (t, sch), v in times.items()},
                          "worlds": ctx.n_worlds}, path)
-    return best, times
+    return best_t, {t: v for (t, sch), v in times.items() if sch == best_s}
 
 
 def apply(ctx):
-    """Set the tabled thread count on ctx if the table has one; returns it (or None)."""
-    t = lookup(ctx)
-    if t is not None:
-        ctx.set_threads(t)
-    return t
+    """Set the tabled thread count and schedule on ctx if the table has them; returns the
+    thread count (or None)."""
+    entry = lookup_entry(ctx)
+    if entry is None:
+        return None
+    ctx.set_threads(int(entry["threads"]))
+    ctx.set_schedule(int(entry.get("schedule", 0)))
+    return int(entry["threads"])
 
 
 def main(argv=None):
@@ -137,7 +154,7 @@ def main(argv=None):
                 continue
             best, times = tune(ctx, torch.tensor(st, dtype=dt, device="cuda"), torch.tensor(ub, dtype=dt, device="cuda"),
                                h, reps=args.reps, path=args.out)
-            print(key(ctx), best, {t: round(v, 3) for t, v in times.items()})
+            print(key(ctx), best, ctx.schedule, {t: round(v, 3) for t, v in times.items()})
             ctx.close()
 
 

@@ -83,3 +83,35 @@ def test_autotuner_picks_persists_and_applies(M, tmp_path, monkeypatch):
     ctx.set_threads(64 if best != 64 else 32)
     assert tune.apply(ctx) == best
     ctx.close()
+
+
+def test_persistent_schedule_is_bit_identical(M):
+    """The persistent, heaviest-first schedule changes only when a world runs: three
+    consecutive steps (the later ones ordered by the earlier iteration counts) and their
+    adjoints equal the one-CTA-per-world launch bit for bit."""
+    sc = S.robot_box_scene()
+    W = 1024
+    outs = []
+    for schedule in (0, 1):
+        ctx = M.Context(sc, S.SolverConfig(tol=1e-4), W, dtype="f32", tape_slots=3)
+        ctx.set_schedule(schedule)
+        s0, ctl, gT = _inputs(sc, W, 9)
+        states = [s0]
+        iters = []
+        for t in range(3):
+            out = torch.empty_like(s0)
+            it = torch.zeros(W, dtype=torch.int32, device="cuda")
+            ctx.ostrich_step(states[t], ctl[t], H, out, iters=it, tape_slot=t)
+            states.append(out)
+            iters.append(it)
+        g = gT.clone()
+        for t in reversed(range(3)):
+            ds = torch.empty_like(g)
+            ctx.ostrich_adjoint(t, g, H, ds)
+            g = ds
+        torch.cuda.synchronize()
+        outs.append((torch.stack(states), torch.stack(iters), g))
+        ctx.close()
+    assert torch.equal(outs[0][0], outs[1][0])
+    assert torch.equal(outs[0][1], outs[1][1])
+    assert torch.equal(outs[0][2], outs[1][2])

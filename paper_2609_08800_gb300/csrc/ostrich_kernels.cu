@@ -1288,7 +1288,9 @@ __global__ void __launch_bounds__(128) adjoint_kernel(const DevScene scp, const 
     w.rhs[i] = -hR * jm.value();
   }
   __syncthreads();
-  schur_solve(sc, w, w.rhs, wl, w.f, w.lt, h, sc.refine_adj);
+  // refined until a correction no longer changes w_lambda at working precision (at most
+  // refine_adj sweeps)
+  schur_solve(sc, w, w.rhs, wl, w.f, w.lt, h, sc.refine_adj, Real(sizeof(Real) == 4 ? 1.2e-7 : 0.0));
   // Eq. (19): w_u = -M^-1 (g + J^T w_lambda)
   Real* wu = w.ub;
   jt_apply_acc(sc, w, wl, w.f);     // f is free now

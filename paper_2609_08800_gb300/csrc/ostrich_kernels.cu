@@ -685,22 +685,22 @@ template <class Real> __device__ void factor(const DevScene& sc, WS<Real>& w, do
     }
   }
   __syncthreads();
-  // S' = S - sum_g F_g F_g^T (lower triangle), one element per thread
-  for (int e = tid; e < ss * ss; e += nth) {
-    const int a = e / ss, b = e - a * ss;
-    if (b > a) continue;
-    Real acc = 0;
-    for (int pa = 0; pa < sc.sep_n[a]; ++pa)
-      for (int pb = 0; pb < sc.sep_n[b]; ++pb) {
-        const int g = sc.sep_g[a][pa];
-        if (g != sc.sep_g[b][pb]) continue;
-        const Real* fa = w.H + g * cm * ldg + sc.sep_k[a][pa] * ldg;
-        const Real* fb = w.H + g * cm * ldg + sc.sep_k[b][pb] * ldg;
-        for (int j = 0; j < w.gn[g]; ++j) acc += fa[j] * fb[j];
-      }
-    w.S[tri(a, b)] -= acc;
+  // S' = S - sum_g F_g F_g^T: group by group (a separator row may couple to two groups),
+  // one coupled row pair (k1 >= k2 of the group's coupling list) per thread
+  for (int g = 0; g < sc.n_groups; ++g) {
+    const int nc = sc.cpl_n[g], n = w.gn[g];
+    if (n == 0) continue;                    // no active contact rows: F_g is empty
+    const Real* Fb = w.H + g * cm * ldg;
+    for (int e = tid; e < nc * nc; e += nth) {
+      const int k1 = e / nc, k2 = e - k1 * nc;
+      if (k2 > k1) continue;
+      const int a = sc.cpl_row[g][k1], b = sc.cpl_row[g][k2];
+      Real acc = 0;
+      for (int j = 0; j < n; ++j) acc += Fb[k1 * ldg + j] * Fb[k2 * ldg + j];
+      w.S[a >= b ? tri(a, b) : tri(b, a)] -= acc;
+    }
+    __syncthreads();
   }
-  __syncthreads();
   if (ss <= 0) return;
   {
     // L_s^-1 in place, then S'^-1 = L_s^-T L_s^-1 from a copy (in E, free once F is formed)

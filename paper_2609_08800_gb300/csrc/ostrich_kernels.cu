@@ -627,8 +627,16 @@ template <class Real> __device__ void assemble(const DevScene& sc, WS<Real>& w, 
 // sequential column-by-column factor and forward substitution (k, resp. l,
 // ascending), so the result does not depend on the team size.
 template <int TEAM, class Real> __device__ void chol_inv_inplace(Real* A, int n, Real* colbuf) {
-  const int t = TEAM ? (int)threadIdx.x : (int)(threadIdx.x & 31);
-  const int T = TEAM ? (int)blockDim.x : 32;
+  // TEAM 0: one warp; 1: the whole CTA; 2: one half-warp (16 lanes)
+  const int t = TEAM == 1 ? (int)threadIdx.x : (TEAM == 2 ? (int)(threadIdx.x & 15) : (int)(threadIdx.x & 31));
+  const int T = TEAM == 1 ? (int)blockDim.x : (TEAM == 2 ? 16 : 32);
+  const int cw = TEAM == 2 ? 16 : 32;                         // columns per pass
+  const unsigned half = 0xffffu << (16 * ((threadIdx.x >> 4) & 1));
+  auto team_sync = [&]() {
+    if (TEAM == 1) __syncthreads();
+    else if (TEAM == 2) __syncwarp(half);
+    else __syncwarp();
+  };
   for (int k = 0; k < n; ++k) {
     const Real akk = A[tri(k, k)];
     const Real d = ssqrt(akk > Real(0) ? akk : Real(1e-30));
@@ -638,23 +646,23 @@ template <int TEAM, class Real> __device__ void chol_inv_inplace(Real* A, int n,
       if (e > k) colbuf[e] = A[tri(e, k)] * inv;
       else if (e < k) A[tri(k, e)] = A[tri(k, e)] / d;
     }
-    if (TEAM) __syncthreads(); else __syncwarp();
+    team_sync();
     if (t == 0) A[tri(k, k)] = xkk;
-    // lanes own columns (j = lane, lane + 32, ...), warps take every nw-th row
-    const int nw = T >> 5, lane = t & 31;
-    for (int j = lane; j < n; j += 32) {
+    // lanes own columns (j = lane, lane + cw, ...), groups of cw lanes take every nw-th row
+    const int nw = T / cw, lane = t % cw;
+    for (int j = lane; j < n; j += cw) {
       // per column: the multiplier of l_ik (X[k][j], X[k][k] or l_jk) and whether the
       // entry keeps its value (no branch inside the row loop)
       const Real coef = j < k ? A[tri(k, j)] : (j == k ? xkk : colbuf[j]);
       const bool keep = j != k;
-      for (int i = (k + 1 > j ? k + 1 : j) + (t >> 5); i < n; i += nw) {
+      for (int i = (k + 1 > j ? k + 1 : j) + t / cw; i < n; i += nw) {
         const Real lik = colbuf[i];
         Real* aij = A + tri(i, j);
         const Real old = keep ? *aij : Real(0);
         *aij = old - lik * coef;
       }
     }
-    if (TEAM) __syncthreads(); else __syncwarp();
+    team_sync();
   }
 }
 
@@ -668,8 +676,15 @@ template <class Real> __device__ void factor(const DevScene& sc, WS<Real>& w, do
   const Real hR = Real(h);
   const int pg = sc.pg, ss = sc.ss, ldg = sc.ldg, cm = sc.cmax, gstr = tri_size(pg);
   const int rb = pg > ss ? pg : ss;
-  // Li_g in place: each warp its groups
-  for (int g = wid; g < sc.n_groups; g += nw) chol_inv_inplace<0>(w.G + g * gstr, w.gn[g], w.prow + wid * rb);
+  // Li_g in place: up to four teams (half-warps for CTAs of up to 64 threads, else warps)
+  // each take their groups
+  if (nth <= 64) {
+    const int team = tid >> 4, nteams = nth >> 4;
+    for (int g = team; g < sc.n_groups; g += nteams)
+      chol_inv_inplace<2>(w.G + g * gstr, w.gn[g], w.prow + team * rb);
+  } else {
+    for (int g = wid; g < sc.n_groups; g += nw) chol_inv_inplace<0>(w.G + g * gstr, w.gn[g], w.prow + (wid & 3) * rb);
+  }
   __syncthreads();
   // F_g[k][j] = sum_{l <= j} E_g[k][l] Li_g[j][l]
   for (int g = 0; g < sc.n_groups; ++g) {

@@ -75,7 +75,7 @@ template <class Real> __host__ __device__ size_t ws_bytes(const DevScene& s) {
   b += 2 * sz(sizeof(int), ng) + sz(sizeof(int), m);
   // the adjoint's VJP items (14 per row) reuse G, E, H and S, which are carved in one run
   int cm = s.cmax > 0 ? s.cmax : 1, ldg = s.ldg > 0 ? s.ldg : 1;
-  int esz = ng * cm * ldg > sep_scratch(s) ? ng * cm * ldg : sep_scratch(s);   // E also holds the separator scratch
+  int esz = ng * cm * ldg;
   int gsz = ng * tri_size(pg), rest = esz + ng * cm * ldg + tri_size(ss);
   if (gsz + rest < 14 * m) gsz = 14 * m - rest;
   b += sz(sizeof(Real), gsz) + sz(sizeof(Real), esz) + sz(sizeof(Real), ng * cm * ldg) + sz(sizeof(Real), tri_size(ss));
@@ -107,7 +107,7 @@ template <class Real> __host__ __device__ WS<Real> ws_carve(char* base, const De
   w.bgrp = carve<int>(p, nb); w.bsepn = carve<int>(p, nb); w.bsep = carve<int>(p, nb * ss);
   w.g0 = carve<int>(p, ng); w.gn = carve<int>(p, ng); w.rgrp = carve<int>(p, m);
   int cm = s.cmax > 0 ? s.cmax : 1, ldg = s.ldg > 0 ? s.ldg : 1;
-  int esz = ng * cm * ldg > sep_scratch(s) ? ng * cm * ldg : sep_scratch(s);
+  int esz = ng * cm * ldg;
   int gsz = ng * tri_size(pg), rest = esz + ng * cm * ldg + tri_size(ss);
   if (gsz + rest < 14 * m) gsz = 14 * m - rest;
   w.G = carve<Real>(p, gsz); w.E = carve<Real>(p, esz); w.H = carve<Real>(p, ng * cm * ldg);
@@ -641,10 +641,10 @@ template <int TEAM, class Real> __device__ void chol_inv_inplace(Real* A, int n,
     const Real akk = A[tri(k, k)];
     const Real d = ssqrt(akk > Real(0) ? akk : Real(1e-30));
     const Real inv = Real(1) / d;
-    const Real xkk = Real(1) / d;           // X[k][k], known to every thread
+    const Real xkk = inv;                   // X[k][k], known to every thread
     for (int e = t; e < n; e += T) {        // the pivot entry itself is left for pass 2
       if (e > k) colbuf[e] = A[tri(e, k)] * inv;
-      else if (e < k) A[tri(k, e)] = A[tri(k, e)] / d;
+      else if (e < k) A[tri(k, e)] *= inv;
     }
     team_sync();
     if (t == 0) A[tri(k, k)] = xkk;
@@ -655,7 +655,19 @@ template <int TEAM, class Real> __device__ void chol_inv_inplace(Real* A, int n,
       // entry keeps its value (no branch inside the row loop)
       const Real coef = j < k ? A[tri(k, j)] : (j == k ? xkk : colbuf[j]);
       const bool keep = j != k;
-      for (int i = (k + 1 > j ? k + 1 : j) + t / cw; i < n; i += nw) {
+      int i = (k + 1 > j ? k + 1 : j) + t / cw;
+      for (; i + 3 * nw < n; i += 4 * nw) {             // four independent rows per pass
+        const int i1 = i + nw, i2 = i1 + nw, i3 = i2 + nw;
+        const Real l0 = colbuf[i], l1 = colbuf[i1], l2 = colbuf[i2], l3 = colbuf[i3];
+        Real* a0 = A + tri(i, j);
+        Real* a1 = A + tri(i1, j);
+        Real* a2 = A + tri(i2, j);
+        Real* a3 = A + tri(i3, j);
+        const Real o0 = keep ? *a0 : Real(0), o1 = keep ? *a1 : Real(0);
+        const Real o2 = keep ? *a2 : Real(0), o3 = keep ? *a3 : Real(0);
+        *a0 = o0 - l0 * coef; *a1 = o1 - l1 * coef; *a2 = o2 - l2 * coef; *a3 = o3 - l3 * coef;
+      }
+      for (; i < n; i += nw) {
         const Real lik = colbuf[i];
         Real* aij = A + tri(i, j);
         const Real old = keep ? *aij : Real(0);
@@ -669,8 +681,8 @@ template <int TEAM, class Real> __device__ void chol_inv_inplace(Real* A, int n,
 // Block-arrowhead factorisation kept in inverse form for row-parallel solves:
 //   Li_g = L_g^-1 with L_g L_g^T = A_g (contact groups; stored in G, packed),
 //   F_g = E_g L_g^-T (coupled separator rows; stored in H),
-//   S'^-1 with S' = S - sum_g F_g F_g^T, the reduced separator (stored in S, packed
-//   symmetric), from its Cholesky factor.
+//   Lsi = L_s^-1 with L_s L_s^T = S - sum_g F_g F_g^T, the reduced separator (stored in S,
+//   packed).
 template <class Real> __device__ void factor(const DevScene& sc, WS<Real>& w, double h) {
   const int tid = threadIdx.x, nth = blockDim.x, wid = tid >> 5, nw = (blockDim.x + 31) >> 5;
   const Real hR = Real(h);
@@ -716,22 +728,8 @@ template <class Real> __device__ void factor(const DevScene& sc, WS<Real>& w, do
     }
     __syncthreads();
   }
-  if (ss <= 0) return;
-  {
-    // L_s^-1 in place, then S'^-1 = L_s^-T L_s^-1 from a copy (in E, free once F is formed)
-    chol_inv_inplace<1>(w.S, ss, w.prow);
-    Real* Lc = w.E;
-    for (int e = tid; e < tri_size(ss); e += nth) Lc[e] = w.S[e];
-    __syncthreads();
-    for (int e = tid; e < ss * ss; e += nth) {
-      const int a = e / ss, b = e - a * ss;
-      if (b > a) continue;
-      Real acc = 0;
-      for (int k = a; k < ss; ++k) acc += Lc[tri(k, a)] * Lc[tri(k, b)];
-      w.S[tri(a, b)] = acc;
-    }
-    __syncthreads();
-  }
+  // Lsi = L_s^-1 in place over S, the whole CTA
+  if (ss > 0) chol_inv_inplace<1>(w.S, ss, w.prow);
 }
 
 // v <- A^-1 v with the inverse-form block-arrowhead factor (row-parallel phases)
@@ -760,12 +758,18 @@ template <class Real> __device__ void arrow_solve(const DevScene& sc, WS<Real>& 
     z[a] = acc;
   }
   __syncthreads();
-  // x_s = S'^-1 b_s' (symmetric, packed lower triangle)
+  // y_s = Lsi b_s'
   for (int a = tid; a < ss; a += nth) {
-    const Real* Sa = w.S + tri(a, 0);
+    const Real* La = w.S + tri(a, 0);
     Real acc = 0;
-    for (int b = 0; b <= a; ++b) acc += Sa[b] * z[b];
-    for (int b = a + 1; b < ss; ++b) acc += w.S[tri(b, a)] * z[b];
+    for (int b = 0; b <= a; ++b) acc += La[b] * z[b];
+    y[mc + a] = acc;
+  }
+  __syncthreads();
+  // x_s = Lsi^T y_s
+  for (int a = tid; a < ss; a += nth) {
+    Real acc = 0;
+    for (int b = a; b < ss; ++b) acc += w.S[tri(b, a)] * y[mc + b];
     v[mc + a] = acc;
   }
   __syncthreads();

@@ -90,9 +90,7 @@ inline void finish_scene(DevScene& s) {
   for (int g = 0; g < s.n_groups; ++g) if (s.cpl_n[g] > s.cmax) s.cmax = s.cpl_n[g];
 }
 
-// Scratch the separator inverse needs (in the coupling block E, free once F is formed):
-// a copy of the inverse factor.
-__host__ __device__ inline int sep_scratch(const DevScene& s) { return tri_size(s.ss); }
+
 
 // Arguments of one launch of the step / adjoint kernels.
 // World selection: without a list, CTA b steps world world0 + b and records into the
@@ -134,7 +132,7 @@ inline __host__ __device__ TapeLayout tape_layout(const DevScene& s) {
   t.off_lam = o; o += s.m_max;
   t.off_G = o; o += s.n_groups * tri_size(s.pg);    // inverse Cholesky factors L_g^-1 of the groups (packed)
   t.off_H = o; o += s.n_groups * s.cmax * s.ldg;     // F_g = E_g L_g^-T (coupled separator rows)
-  t.off_S = o; o += tri_size(s.ss);                  // inverse of the reduced separator (packed symmetric)
+  t.off_S = o; o += tri_size(s.ss);                  // inverse Cholesky factor of the reduced separator (packed)
   o = (o + 3) & ~3;   // 16-byte multiple per world for FP32
   t.total = o;
   return t;

@@ -678,6 +678,73 @@ template <int TEAM, class Real> __device__ void chol_inv_inplace(Real* A, int n,
   }
 }
 
+// The same in-place L^-1 by the whole CTA, two pivots per round: every thread forms the
+// 2 x 2 pivot block (k, k+1) itself; pass 1 gives columns k and k+1 of L (colbuf,
+// colbuf + n) and finishes rows k and k+1 of L^-1; pass 2 applies both rank-one updates
+// (k, then k+1) to the trailing block and to the rows of L^-1 below.  Each element sees
+// the same operations in the same order as one pivot per round; half the barriers.
+// colbuf holds 2 n values.
+template <class Real> __device__ void chol_inv_inplace2(Real* A, int n, Real* colbuf) {
+  const int t = threadIdx.x, T = blockDim.x;
+  Real* c0 = colbuf;
+  Real* c1 = colbuf + n;
+  int k = 0;
+  for (; k + 1 < n; k += 2) {
+    const int k1 = k + 1;
+    const Real a00 = A[tri(k, k)];
+    const Real d0 = ssqrt(a00 > Real(0) ? a00 : Real(1e-30));
+    const Real i0 = Real(1) / d0;
+    const Real l10 = A[tri(k1, k)] * i0;                   // L[k+1][k]
+    const Real a11 = A[tri(k1, k1)] - l10 * l10;
+    const Real d1 = ssqrt(a11 > Real(0) ? a11 : Real(1e-30));
+    const Real i1 = Real(1) / d1;
+    const Real x10 = (-(l10 * i0)) * i1;                   // X[k+1][k]
+    // pass 1 writes neither the pivot block (its entries are written in pass 2) nor any
+    // entry another thread reads in this pass
+    for (int e = t; e < n; e += T) {
+      if (e > k1) {
+        const Real l0 = A[tri(e, k)] * i0;
+        c0[e] = l0;
+        c1[e] = (A[tri(e, k1)] - l0 * l10) * i1;
+      } else if (e < k) {
+        const Real xk = A[tri(k, e)] * i0;
+        A[tri(k, e)] = xk;
+        A[tri(k1, e)] = (A[tri(k1, e)] - l10 * xk) * i1;
+      }
+    }
+    __syncthreads();
+    if (t == 0) { A[tri(k, k)] = i0; A[tri(k1, k)] = x10; A[tri(k1, k1)] = i1; }
+    const int nw = T >> 5, lane = t & 31;
+    for (int j = lane; j < n; j += 32) {
+      // multipliers of l_ik and l_i(k+1) for column j, and whether the entry keeps its value
+      Real m0, m1;
+      bool keep = true;
+      if (j < k) { m0 = A[tri(k, j)]; m1 = A[tri(k1, j)]; }
+      else if (j == k) { m0 = i0; m1 = x10; keep = false; }
+      else if (j == k1) { m0 = Real(0); m1 = i1; keep = false; }
+      else { m0 = c0[j]; m1 = c1[j]; }
+      for (int i = (k1 + 1 > j ? k1 + 1 : j) + (t >> 5); i < n; i += nw) {
+        Real* aij = A + tri(i, j);
+        Real v = keep ? *aij : Real(0);
+        if (j != k1) v = v - c0[i] * m0;
+        v = v - c1[i] * m1;
+        *aij = v;
+      }
+    }
+    __syncthreads();
+  }
+  if (k < n) {                                             // odd n: the last pivot alone
+    const Real akk = A[tri(k, k)];
+    const Real d = ssqrt(akk > Real(0) ? akk : Real(1e-30));
+    const Real inv = Real(1) / d;
+    __syncthreads();
+    for (int e = t; e < k; e += T) A[tri(k, e)] *= inv;
+    __syncthreads();
+    if (t == 0) A[tri(k, k)] = inv;
+    __syncthreads();
+  }
+}
+
 // Block-arrowhead factorisation kept in inverse form for row-parallel solves:
 //   Li_g = L_g^-1 with L_g L_g^T = A_g (contact groups; stored in G, packed),
 //   F_g = E_g L_g^-T (coupled separator rows; stored in H),
@@ -729,7 +796,7 @@ template <class Real> __device__ void factor(const DevScene& sc, WS<Real>& w, do
     __syncthreads();
   }
   // Lsi = L_s^-1 in place over S, the whole CTA
-  if (ss > 0) chol_inv_inplace<1>(w.S, ss, w.prow);
+  if (ss > 0) chol_inv_inplace2(w.S, ss, w.prow);
 }
 
 // v <- A^-1 v with the inverse-form block-arrowhead factor (row-parallel phases)

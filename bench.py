@@ -502,7 +502,8 @@ def dist_max(x):
     if _DIST is None:
         return x
     import torch
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dev = "cuda" if _DIST.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
     _DIST.all_reduce(t, op=_DIST.ReduceOp.MAX)
     return float(t.item())
 

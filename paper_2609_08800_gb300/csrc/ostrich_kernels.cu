@@ -591,8 +591,9 @@ template <class Real> __device__ void assemble(const DevScene& sc, WS<Real>& w, 
       Eb[k * ldg + i] = hR * rowdot(w.J + 12 * row, side, Yr, 0);
     }
   }
-  // separator block (full, symmetric): a thread per separator row
-  for (int a = tid; a < ss; a += nth) {
+  // separator block: a thread per separator row, counted from the last thread so that it
+  // runs beside the contact rows (counted from the first) rather than after them
+  for (int a = nth - 1 - tid; a >= 0 && a < ss; a += nth) {
     const int i = mc + a;
     const int ia0 = w.meta[4 * i + 1], ia1 = w.meta[4 * i + 2];
     Real Yi[12];

@@ -134,6 +134,26 @@ template <class Real> __device__ Real block_sum(WS<Real>& w, Real v) {
   return w.red[32];
 }
 
+// two deterministic block sums at once (fixed tree, as block_sum): results in a, b
+template <class Real> __device__ void block_sum2(WS<Real>& w, Real& a, Real& b) {
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = (blockDim.x + 31) >> 5;
+  for (int o = 16; o > 0; o >>= 1) {
+    a += __shfl_xor_sync(0xffffffffu, a, o);
+    b += __shfl_xor_sync(0xffffffffu, b, o);
+  }
+  __syncthreads();
+  if (lane == 0) { w.red[wid] = a; w.red[16 + wid] = b; }
+  __syncthreads();
+  if (tid == 0) {
+    Real sa = Real(0), sb = Real(0);
+    for (int i = 0; i < nw; ++i) { sa += w.red[i]; sb += w.red[16 + i]; }
+    w.red[32] = sa; w.red[48] = sb;
+  }
+  __syncthreads();
+  a = w.red[32];
+  b = w.red[48];
+}
+
 // block maximum (every thread gets it), through w.red[33..]
 template <class Real> __device__ Real block_max(WS<Real>& w, Real v) {
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = (blockDim.x + 31) >> 5;
@@ -358,6 +378,27 @@ template <class Real> __device__ __forceinline__ void clamp_cone(const DevScene&
   }
 }
 
+template <class Real> __device__ __forceinline__ Real rowdot(const Real* Ja, int sa, const Real* Yb, int sb) {
+  return Ja[sa] * Yb[sb] + Ja[sa + 1] * Yb[sb + 1] + Ja[sa + 2] * Yb[sb + 2] + Ja[sa + 3] * Yb[sb + 3] +
+         Ja[sa + 4] * Yb[sb + 4] + Ja[sa + 5] * Yb[sb + 5];
+}
+
+// y = M^-1 J_i^T for both body blocks of row i: (J_lin / m, Iw^-1 J_ang) per side (zero
+// for a side without a body); the same values Eq. (2)'s M~^-1 gives the row.
+template <class Real> __device__ __forceinline__ void minv_row(const DevScene& sc, const WS<Real>& w, int i, Real* y) {
+  const Real* Jr = w.J + 12 * i;
+  for (int side = 0; side < 2; ++side) {
+    const int b = w.meta[4 * i + 1 + side];
+    Real* ys = y + 6 * side;
+    if (b < 0) { for (int q = 0; q < 6; ++q) ys[q] = Real(0); continue; }
+    const Real* Js = Jr + 6 * side;
+    const Real mi = Real(1) / Real(sc.mass[b]);
+    ys[0] = Js[0] * mi; ys[1] = Js[1] * mi; ys[2] = Js[2] * mi;
+    const vec3<Real> ia = mat3<Real>(w.Iwi + 9 * b, v3(Js[3], Js[4], Js[5]));
+    ys[3] = ia.x; ys[4] = ia.y; ys[5] = ia.z;
+  }
+}
+
 // ---------------------------------------------------------------------------
 // one residual / Jacobian evaluation at iterate (u, lam); returns the merit
 // ---------------------------------------------------------------------------
@@ -524,48 +565,32 @@ __device__ Real evaluate(const DevScene& sc, WS<Real>& w, const Real* u, const R
     for (int k = 0; k < 6; ++k) { w.mr[6 * b + k] = mr[k]; part += mr[k] * mr[k]; }
   }
   for (int i = tid; i < m; i += nth) part += w.r2[i] * w.r2[i];
-  return block_sum(w, part);
+  // with the merit: delta = delta_rel * mean diag(h J M^-1 J^T) of these rows, for the
+  // assembly at this iterate (scal[2])
+  Real dpart = 0;
+  for (int i = tid; i < m; i += nth) {
+    const Real* Ji = w.J + 12 * i;
+    Real Yi[12];
+    minv_row(sc, w, i, Yi);
+    dpart += hR * (rowdot(Ji, 0, Yi, 0) + rowdot(Ji, 6, Yi, 6));
+  }
+  block_sum2(w, part, dpart);
+  if (tid == 0) w.scal[2] = m > 0 ? Real(sc.delta_rel) * dpart / Real(m) : Real(0);
+  __syncthreads();                         // scal[2] is read by the assembly that follows
+  return part;
 }
 
 // ---------------------------------------------------------------------------
 // Schur assembly, factorisation and solves
 // ---------------------------------------------------------------------------
-template <class Real> __device__ __forceinline__ Real rowdot(const Real* Ja, int sa, const Real* Yb, int sb) {
-  return Ja[sa] * Yb[sb] + Ja[sa + 1] * Yb[sb + 1] + Ja[sa + 2] * Yb[sb + 2] + Ja[sa + 3] * Yb[sb + 3] +
-         Ja[sa + 4] * Yb[sb + 4] + Ja[sa + 5] * Yb[sb + 5];
-}
 
-// y = M^-1 J_i^T for both body blocks of row i: (J_lin / m, Iw^-1 J_ang) per side (zero
-// for a side without a body); the same values Eq. (2)'s M~^-1 gives the row.
-template <class Real> __device__ __forceinline__ void minv_row(const DevScene& sc, const WS<Real>& w, int i, Real* y) {
-  const Real* Jr = w.J + 12 * i;
-  for (int side = 0; side < 2; ++side) {
-    const int b = w.meta[4 * i + 1 + side];
-    Real* ys = y + 6 * side;
-    if (b < 0) { for (int q = 0; q < 6; ++q) ys[q] = Real(0); continue; }
-    const Real* Js = Jr + 6 * side;
-    const Real mi = Real(1) / Real(sc.mass[b]);
-    ys[0] = Js[0] * mi; ys[1] = Js[1] * mi; ys[2] = Js[2] * mi;
-    const vec3<Real> ia = mat3<Real>(w.Iwi + 9 * b, v3(Js[3], Js[4], Js[5]));
-    ys[3] = ia.x; ys[4] = ia.y; ys[5] = ia.z;
-  }
-}
 
 template <class Real> __device__ void assemble(const DevScene& sc, WS<Real>& w, double h) {
   const int tid = threadIdx.x, nth = blockDim.x;
   const int m = w.ints[0], mc = w.ints[1], gstr = tri_size(sc.pg), ss = sc.ss, ldg = sc.ldg;
   const Real hR = Real(h);
-  // delta = delta_rel * mean diag(h J M^-1 J^T)
-  Real part = 0;
-  for (int i = tid; i < m; i += nth) {
-    const Real* Ji = w.J + 12 * i;
-    Real Yi[12];
-    minv_row(sc, w, i, Yi);
-    part += hR * (rowdot(Ji, 0, Yi, 0) + rowdot(Ji, 6, Yi, 6));
-  }
-  Real tot = block_sum(w, part);
-  const Real delta = m > 0 ? Real(sc.delta_rel) * tot / Real(m) : Real(0);
-  if (tid == 0) w.scal[2] = delta;
+  // delta = delta_rel * mean diag(h J M^-1 J^T), formed by the evaluation at this iterate
+  const Real delta = w.scal[2];
   // group blocks (full, symmetric) and their coupling rows E_g: a thread per contact row
   for (int r = tid; r < mc; r += nth) {
     const int g = w.rgrp[r], r0 = w.g0[g], i = r - r0, bg = sc.group_body[g];
@@ -1350,20 +1375,9 @@ __global__ void __launch_bounds__(128) adjoint_kernel(const DevScene scp, const 
     for (int c = 0; c < 6; ++c) w.mr[6 * b + c] = mg[c];
   }
   __syncthreads();
-  // Eq. (18): A w_lambda = -h J M^-1 g, with the forward factor (delta recomputed as
-  // in the forward assembly for the refinement's matrix-free product)
+  // Eq. (18): A w_lambda = -h J M^-1 g, with the forward factor (the refinement's
+  // matrix-free product takes delta as the evaluation at the iterate formed it, scal[2])
   Real* wl = w.dl;
-  {
-    Real part = 0;
-    for (int i = tid; i < m; i += nth) {
-      const Real* Ji = w.J + 12 * i;
-      Real Yi[12];
-      minv_row(sc, w, i, Yi);
-      part += hR * (rowdot(Ji, 0, Yi, 0) + rowdot(Ji, 6, Yi, 6));
-    }
-    Real tot = block_sum(w, part);
-    if (tid == 0) w.scal[2] = m > 0 ? Real(sc.delta_rel) * tot / Real(m) : Real(0);
-  }
   // the right-hand side is formed with exact products: its rounding would otherwise
   // reach the null space of J^T, where A's eigenvalue is only kappa
   for (int i = tid; i < m; i += nth) {

@@ -1,6 +1,6 @@
 // C ABI of libostrich (declared in include/ostrich.h): context, tape memory,
 // argument checks and kernel launches.  Every step of the path runs in the CUDA
-// kernels of ostrich_kernels.cu; this file only validates and dispatches.
+// kernels of ostrich_kernels.cuh; this file only validates and dispatches.
 #include <cuda_runtime.h>
 #include <cstdio>
 #include <cstring>

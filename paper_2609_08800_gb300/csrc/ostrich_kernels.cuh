@@ -15,6 +15,9 @@
 // so groups do not couple), then the joint/servo rows (the separator).  That block-
 // arrowhead structure is factored as Cholesky of each group block, elimination of
 // the group-separator coupling, then Cholesky of the reduced separator block.
+//
+// Included once per precision (ostrich_kernels_f32.cu, ostrich_kernels_f64.cu, which
+// define OST_REAL) so that the two compile in parallel.
 #include <cuda_runtime.h>
 #include <stdint.h>
 #include "ostrich_scene.h"
@@ -31,15 +34,16 @@ template <class Real> struct WS {
   Real *qm, *um, *ubar, *uk, *ut, *ub, *du, *f, *rdyn, *mr, *Iw, *Iwi, *R, *qp;
   // rows
   Real *J, *C, *rhat, *r2, *lk, *lt, *lb, *dl, *rhs;
-  int *meta;      // 4 per row: type | sub << 4, b0, b1 (or -1), lam index (state lambda block)
-  int *ref;       // slot or joint of the row
+  int16_t *meta;  // 4 per row: type | sub << 4, b0, b1 (or -1), lam index (state lambda block)
+  int16_t *ref;   // slot or joint of the row
   // slots
   Real *sn, *sd, *st1, *st2, *swhat, *srad, *sedge;
   int *sact, *srow, *sid, *sftype;
   // per-body row lists
   int *bgrp, *bsepn, *bsep;
   // groups
-  int *g0, *gn, *rgrp;
+  int *g0, *gn;
+  int16_t *rgrp;  // group of a contact row
   // Schur storage (block-arrowhead, inverse form): G group blocks, E coupling rows,
   // H = E G, S reduced separator; prow a pivot-row buffer per warp
   Real *G, *E, *H, *S, *prow, *tmp, *tmp2;
@@ -58,32 +62,6 @@ template <class T> __host__ __device__ __forceinline__ T* carve(char*& p, int n)
   return r;
 }
 
-template <class Real> __host__ __device__ size_t ws_bytes(const DevScene& s) {
-  // mirrors carve(): every array rounded up to 8 bytes, plus one 8-byte pad each
-  auto sz = [](size_t elem, int n) { return ((elem * (size_t)(n > 0 ? n : 1)) + 15) & ~(size_t)7; };
-  int nb = s.nb, m = s.m_max, ns = s.n_slots > 0 ? s.n_slots : 1, ng = s.n_groups > 0 ? s.n_groups : 1;
-  int ss = s.ss > 0 ? s.ss : 1, pg = s.pg > 0 ? s.pg : 1;
-  size_t b = 0;
-  b += sz(sizeof(Real), 7 * nb) + sz(sizeof(Real), 6 * nb) + sz(sizeof(Real), s.n_servo + 1);
-  b += 8 * sz(sizeof(Real), 6 * nb);                       // uk ut ub du f rdyn mr + spare
-  b += 2 * sz(sizeof(Real), 9 * nb) + sz(sizeof(Real), 9 * nb) + sz(sizeof(Real), 7 * nb);
-  b += sz(sizeof(Real), 12 * m) + 8 * sz(sizeof(Real), m);
-  b += sz(sizeof(int), 4 * m) + sz(sizeof(int), m);
-  b += 4 * sz(sizeof(Real), 3 * ns) + 2 * sz(sizeof(Real), ns) + sz(sizeof(Real), 2 * ns);
-  b += 4 * sz(sizeof(int), ns);
-  b += sz(sizeof(int), nb) * 2 + sz(sizeof(int), nb * ss);
-  b += 2 * sz(sizeof(int), ng) + sz(sizeof(int), m);
-  // the adjoint's VJP items (14 per row) reuse G, E, H and S, which are carved in one run
-  int cm = s.cmax > 0 ? s.cmax : 1, ldg = s.ldg > 0 ? s.ldg : 1;
-  int esz = ng * cm * ldg;
-  int gsz = ng * tri_size(pg), rest = esz + ng * cm * ldg + tri_size(ss);
-  if (gsz + rest < 14 * m) gsz = 14 * m - rest;
-  b += sz(sizeof(Real), gsz) + sz(sizeof(Real), esz) + sz(sizeof(Real), ng * cm * ldg) + sz(sizeof(Real), tri_size(ss));
-  b += sz(sizeof(Real), 4 * (pg > ss ? pg : ss)) + 2 * sz(sizeof(Real), m);
-  b += sz(sizeof(Real), 64) + sz(sizeof(int), 16) + sz(sizeof(Real), 8);
-  b += 256;
-  return b;
-}
 
 template <class Real> __host__ __device__ WS<Real> ws_carve(char* base, const DevScene& s) {
   WS<Real> w;
@@ -93,19 +71,19 @@ template <class Real> __host__ __device__ WS<Real> ws_carve(char* base, const De
   w.qm = carve<Real>(p, 7 * nb); w.um = carve<Real>(p, 6 * nb); w.ubar = carve<Real>(p, s.n_servo + 1);
   w.uk = carve<Real>(p, 6 * nb); w.ut = carve<Real>(p, 6 * nb); w.ub = carve<Real>(p, 6 * nb);
   w.du = carve<Real>(p, 6 * nb); w.f = carve<Real>(p, 6 * nb); w.rdyn = carve<Real>(p, 6 * nb);
-  w.mr = carve<Real>(p, 6 * nb); (void)carve<Real>(p, 6 * nb);
+  w.mr = carve<Real>(p, 6 * nb);
   w.Iw = carve<Real>(p, 9 * nb); w.Iwi = carve<Real>(p, 9 * nb); w.R = carve<Real>(p, 9 * nb);
   w.qp = carve<Real>(p, 7 * nb);
   w.J = carve<Real>(p, 12 * m);
   w.C = carve<Real>(p, m); w.rhat = carve<Real>(p, m); w.r2 = carve<Real>(p, m); w.lk = carve<Real>(p, m);
   w.lt = carve<Real>(p, m); w.lb = carve<Real>(p, m); w.dl = carve<Real>(p, m); w.rhs = carve<Real>(p, m);
-  w.meta = carve<int>(p, 4 * m); w.ref = carve<int>(p, m);
+  w.meta = carve<int16_t>(p, 4 * m); w.ref = carve<int16_t>(p, m);
   w.sn = carve<Real>(p, 3 * ns); w.st1 = carve<Real>(p, 3 * ns); w.st2 = carve<Real>(p, 3 * ns);
   w.srad = carve<Real>(p, 3 * ns); w.sd = carve<Real>(p, ns); w.swhat = carve<Real>(p, ns);
   w.sedge = carve<Real>(p, 2 * ns);
   w.sact = carve<int>(p, ns); w.srow = carve<int>(p, ns); w.sid = carve<int>(p, ns); w.sftype = carve<int>(p, ns);
   w.bgrp = carve<int>(p, nb); w.bsepn = carve<int>(p, nb); w.bsep = carve<int>(p, nb * ss);
-  w.g0 = carve<int>(p, ng); w.gn = carve<int>(p, ng); w.rgrp = carve<int>(p, m);
+  w.g0 = carve<int>(p, ng); w.gn = carve<int>(p, ng); w.rgrp = carve<int16_t>(p, m);
   int cm = s.cmax > 0 ? s.cmax : 1, ldg = s.ldg > 0 ? s.ldg : 1;
   int esz = ng * cm * ldg;
   int gsz = ng * tri_size(pg), rest = esz + ng * cm * ldg + tri_size(ss);
@@ -116,6 +94,16 @@ template <class Real> __host__ __device__ WS<Real> ws_carve(char* base, const De
   w.tmp = carve<Real>(p, m); w.tmp2 = carve<Real>(p, m);
   w.red = carve<Real>(p, 64); w.ints = carve<int>(p, 16); w.scal = carve<Real>(p, 8);
   return w;
+}
+
+// Dynamic shared memory of one world: the carve itself, run from a 16-byte aligned base
+// (the dynamic shared-memory base is 16-byte aligned and carve aligns to 8), rounded up
+// to 16 bytes.
+template <class Real> __host__ __device__ size_t ws_bytes(const DevScene& s) {
+  char* base = reinterpret_cast<char*>(uintptr_t(16));
+  WS<Real> w = ws_carve<Real>(base, s);
+  size_t used = (size_t)(reinterpret_cast<char*>(w.scal + 8) - base);
+  return (used + 15) & ~(size_t)15;
 }
 
 // deterministic block reduction (fixed tree); result broadcast through w.red[0]
@@ -665,8 +653,7 @@ template <int TEAM, class Real> __device__ void chol_inv_inplace(Real* A, int n,
   };
   for (int k = 0; k < n; ++k) {
     const Real akk = A[tri(k, k)];
-    const Real d = ssqrt(akk > Real(0) ? akk : Real(1e-30));
-    const Real inv = Real(1) / d;
+    const Real inv = pivot_rsqrt(akk > Real(0) ? akk : Real(1e-30));
     const Real xkk = inv;                   // X[k][k], known to every thread
     for (int e = t; e < n; e += T) {        // the pivot entry itself is left for pass 2
       if (e > k) colbuf[e] = A[tri(e, k)] * inv;
@@ -718,12 +705,10 @@ template <class Real> __device__ void chol_inv_inplace2(Real* A, int n, Real* co
   for (; k + 1 < n; k += 2) {
     const int k1 = k + 1;
     const Real a00 = A[tri(k, k)];
-    const Real d0 = ssqrt(a00 > Real(0) ? a00 : Real(1e-30));
-    const Real i0 = Real(1) / d0;
+    const Real i0 = pivot_rsqrt(a00 > Real(0) ? a00 : Real(1e-30));
     const Real l10 = A[tri(k1, k)] * i0;                   // L[k+1][k]
     const Real a11 = A[tri(k1, k1)] - l10 * l10;
-    const Real d1 = ssqrt(a11 > Real(0) ? a11 : Real(1e-30));
-    const Real i1 = Real(1) / d1;
+    const Real i1 = pivot_rsqrt(a11 > Real(0) ? a11 : Real(1e-30));
     const Real x10 = (-(l10 * i0)) * i1;                   // X[k+1][k]
     // pass 1 writes neither the pivot block (its entries are written in pass 2) nor any
     // entry another thread reads in this pass
@@ -749,7 +734,21 @@ template <class Real> __device__ void chol_inv_inplace2(Real* A, int n, Real* co
       else if (j == k) { m0 = i0; m1 = x10; keep = false; }
       else if (j == k1) { m0 = Real(0); m1 = i1; keep = false; }
       else { m0 = c0[j]; m1 = c1[j]; }
-      for (int i = (k1 + 1 > j ? k1 + 1 : j) + (t >> 5); i < n; i += nw) {
+      int i = (k1 + 1 > j ? k1 + 1 : j) + (t >> 5);
+      for (; i + 3 * nw < n; i += 4 * nw) {                 // four independent rows per pass
+        const int ia = i + nw, ib = ia + nw, ic = ib + nw;
+        Real* p0 = A + tri(i, j);
+        Real* p1 = A + tri(ia, j);
+        Real* p2 = A + tri(ib, j);
+        Real* p3 = A + tri(ic, j);
+        const Real a0 = c0[i], a1 = c0[ia], a2 = c0[ib], a3 = c0[ic];
+        const Real b0 = c1[i], b1 = c1[ia], b2 = c1[ib], b3 = c1[ic];
+        Real v0 = keep ? *p0 : Real(0), v1 = keep ? *p1 : Real(0);
+        Real v2 = keep ? *p2 : Real(0), v3 = keep ? *p3 : Real(0);
+        if (j != k1) { v0 = v0 - a0 * m0; v1 = v1 - a1 * m0; v2 = v2 - a2 * m0; v3 = v3 - a3 * m0; }
+        *p0 = v0 - b0 * m1; *p1 = v1 - b1 * m1; *p2 = v2 - b2 * m1; *p3 = v3 - b3 * m1;
+      }
+      for (; i < n; i += nw) {
         Real* aij = A + tri(i, j);
         Real v = keep ? *aij : Real(0);
         if (j != k1) v = v - c0[i] * m0;
@@ -761,8 +760,7 @@ template <class Real> __device__ void chol_inv_inplace2(Real* A, int n, Real* co
   }
   if (k < n) {                                             // odd n: the last pivot alone
     const Real akk = A[tri(k, k)];
-    const Real d = ssqrt(akk > Real(0) ? akk : Real(1e-30));
-    const Real inv = Real(1) / d;
+    const Real inv = pivot_rsqrt(akk > Real(0) ? akk : Real(1e-30));
     __syncthreads();
     for (int e = t; e < k; e += T) A[tri(k, e)] *= inv;
     __syncthreads();
@@ -1145,8 +1143,13 @@ __device__ __forceinline__ void step_world(const DevScene& sc, WS<Real>& w, cons
   }
 }
 
+// At most 128 threads per world, registers capped for 3 such CTAs per SM (164 in FP32,
+// no spills; 6 CTAs of 64 threads, the robot world's FP32 setting, fit as well).  A cap
+// for 7 CTAs of 64 threads (128 registers; the robot world's FP32 working set fits 7 per
+// SM) made the 8192-world step slower, 7.12 ms against 6.70 ms: the capped code spills
+// and instruction-fetch stalls grow with the extra CTA (1.5 -> 2.6 per issue).
 template <class Real>
-__global__ void __launch_bounds__(128) step_kernel(const DevScene scp, const StepArgs a) {
+__global__ void __launch_bounds__(128, 3) step_kernel(const DevScene scp, const StepArgs a) {
   extern __shared__ __align__(16) char smem[];
   __shared__ __align__(16) DevScene ssc;
   scene_to_shared(scp, ssc);
@@ -1170,7 +1173,7 @@ __global__ void __launch_bounds__(128) step_kernel(const DevScene scp, const Ste
 // counting sort over 0..63, one CTA): worlds that took the most iterations start first,
 // so the last wave is short.  Worlds of equal count may come in any order; a world's
 // result does not depend on when it runs.
-__global__ void lpt_order_kernel(const int32_t* cost, int n, int32_t* order) {
+static __global__ void lpt_order_kernel(const int32_t* cost, int n, int32_t* order) {
   __shared__ int bins[64], start[64];
   for (int i = threadIdx.x; i < 64; i += blockDim.x) bins[i] = 0;
   __syncthreads();
@@ -1320,7 +1323,7 @@ __device__ Real body_vjp(const DevScene& sc, const WS<Real>& w, int b, int dc, c
 }
 
 template <class Real>
-__global__ void __launch_bounds__(128) adjoint_kernel(const DevScene scp, const AdjArgs a) {
+__global__ void __launch_bounds__(128, 3) adjoint_kernel(const DevScene scp, const AdjArgs a) {
   extern __shared__ __align__(16) char smem[];
   __shared__ __align__(16) DevScene ssc;
   scene_to_shared(scp, ssc);
@@ -1462,6 +1465,9 @@ template <class K> cudaError_t ensure_smem(K kernel, size_t smem, int* done_dev,
   if (e != cudaSuccess) return e;
   if (dev < 64 && done_size[dev] >= smem && done_dev[dev]) return cudaSuccess;
   e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  // all of the unified L1 as shared memory: the working sets live there, global traffic is small
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout, (int)cudaSharedmemCarveoutMaxShared);
   if (e == cudaSuccess && dev < 64) { done_dev[dev] = 1; if (smem > done_size[dev]) done_size[dev] = smem; }
   return e;
 }
@@ -1470,8 +1476,9 @@ template <class Real>
 cudaError_t launch_step(const DevScene& sc, const StepArgs& a, int threads, cudaStream_t st) {
   static int done_dev[64] = {0};
   static size_t done_size[64] = {0};
+  auto kernel = step_kernel<Real>;
   size_t smem = ws_bytes<Real>(sc);
-  cudaError_t e = ensure_smem(step_kernel<Real>, smem, done_dev, done_size);
+  cudaError_t e = ensure_smem(kernel, smem, done_dev, done_size);
   if (e != cudaSuccess) return e;
   int n = a.list ? a.n_list : a.n_worlds - a.world0;
   if (n <= 0) return cudaSuccess;
@@ -1480,7 +1487,7 @@ cudaError_t launch_step(const DevScene& sc, const StepArgs& a, int threads, cuda
     int dev = 0, sms = 0, per_sm = 0;
     if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
     if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
-    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, step_kernel<Real>, threads, smem)) != cudaSuccess)
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, smem)) != cudaSuccess)
       return e;
     if (per_sm < 1) per_sm = 1;
     int grid = sms * per_sm < n ? sms * per_sm : n;
@@ -1491,10 +1498,10 @@ cudaError_t launch_step(const DevScene& sc, const StepArgs& a, int threads, cuda
     }
     StepArgs b = a;
     b.n_items = n;
-    step_kernel<Real><<<grid, threads, smem, st>>>(sc, b);
+    kernel<<<grid, threads, smem, st>>>(sc, b);
     return cudaGetLastError();
   }
-  step_kernel<Real><<<n, threads, smem, st>>>(sc, a);
+  kernel<<<n, threads, smem, st>>>(sc, a);
   return cudaGetLastError();
 }
 
@@ -1502,21 +1509,16 @@ template <class Real>
 cudaError_t launch_adjoint(const DevScene& sc, const AdjArgs& a, int threads, cudaStream_t st) {
   static int done_dev[64] = {0};
   static size_t done_size[64] = {0};
+  auto kernel = adjoint_kernel<Real>;
   size_t smem = ws_bytes<Real>(sc);
-  cudaError_t e = ensure_smem(adjoint_kernel<Real>, smem, done_dev, done_size);
+  cudaError_t e = ensure_smem(kernel, smem, done_dev, done_size);
   if (e != cudaSuccess) return e;
   int n = a.list ? a.n_list : a.n_worlds - a.world0;
   if (n <= 0) return cudaSuccess;
-  adjoint_kernel<Real><<<n, threads, smem, st>>>(sc, a);
+  kernel<<<n, threads, smem, st>>>(sc, a);
   return cudaGetLastError();
 }
 
-template cudaError_t launch_step<float>(const DevScene&, const StepArgs&, int, cudaStream_t);
-template cudaError_t launch_step<double>(const DevScene&, const StepArgs&, int, cudaStream_t);
-template cudaError_t launch_adjoint<float>(const DevScene&, const AdjArgs&, int, cudaStream_t);
-template cudaError_t launch_adjoint<double>(const DevScene&, const AdjArgs&, int, cudaStream_t);
-template size_t ws_bytes<float>(const DevScene&);
-template size_t ws_bytes<double>(const DevScene&);
 
 // Bytes the carve of one world actually consumes from a 16-byte aligned base; the
 // context refuses a scene for which this exceeds ws_bytes (checked on the host).
@@ -1526,7 +1528,10 @@ template <class Real> size_t ws_used(const DevScene& s) {
   WS<Real> w = ws_carve<Real>(base, s);
   return (size_t)(reinterpret_cast<char*>(w.scal + 8) - base);
 }
-template size_t ws_used<float>(const DevScene&);
-template size_t ws_used<double>(const DevScene&);
+
+template cudaError_t launch_step<OST_REAL>(const DevScene&, const StepArgs&, int, cudaStream_t);
+template cudaError_t launch_adjoint<OST_REAL>(const DevScene&, const AdjArgs&, int, cudaStream_t);
+template size_t ws_bytes<OST_REAL>(const DevScene&);
+template size_t ws_used<OST_REAL>(const DevScene&);
 
 }  // namespace ost

@@ -36,6 +36,11 @@ template <class T> __device__ __forceinline__ dual<T> ssqrt(dual<T> a) {
   T s = ssqrt(a.v);
   return dual<T>(s, a.d / (T(2) * s));
 }
+// 1 / sqrt(x) of a Cholesky pivot: the hardware reciprocal square root in FP32 (within
+// 2 ulp, one instruction instead of a rounded square root and a rounded division), the
+// correctly rounded square root and quotient in FP64
+__device__ __forceinline__ float pivot_rsqrt(float x) { return rsqrtf(x); }
+__device__ __forceinline__ double pivot_rsqrt(double x) { return 1.0 / sqrt(x); }
 __device__ __forceinline__ float sval(float x) { return x; }
 __device__ __forceinline__ double sval(double x) { return x; }
 template <class T> __device__ __forceinline__ T sval(dual<T> x) { return x.v; }

@@ -250,3 +250,44 @@ def test_terrain_fp64_matches_oracle(ostrich):
     g = np.random.default_rng(22).normal(size=st.shape)
     g[13 * sc.n_bodies:] = 0
     _compare(sc, cfg, ostrich, st, ub, 0.1, "f64", 1e-7, 1e-6, 1e-6, 0.7, grads=g)
+
+
+def _hinged_boxes():
+    """Two boxes on the plane joined by a servoed revolute joint: both bodies carry
+    contact slots, so every joint row couples to two contact groups (the general
+    separator update, group by group)."""
+    m, a, b, c = 10.0, 0.4, 0.4, 0.2
+    bodies = [S.Body(mass=m, inertia=S._box_inertia(m, a, b, c), shape=S.SHAPE_BOX,
+                     half_extents=(a / 2, b / 2, c / 2)) for _ in range(2)]
+    joints = [S.Joint(parent=0, child=1, anchor_parent=(0.21, 0.0, 0.0), anchor_child=(-0.21, 0.0, 0.0), kp=50.0)]
+    return S.Scene("hinged_boxes", bodies, joints, S.Env(S.ENV_PLANE), 0.8)
+
+
+def _hinged_states(sc, W, seed):
+    rng = np.random.default_rng(seed)
+    nb = sc.n_bodies
+    st = np.zeros((sc.n_state, W))
+    for w in range(W):
+        z, vx = 0.1 + rng.uniform(-0.01, 0.03), rng.uniform(-0.3, 0.3)
+        for b, x in enumerate((-0.21, 0.21)):
+            st[7 * b:7 * b + 7, w] = (x, 0.0, z, 1.0, 0.0, 0.0, 0.0)
+            st[7 * nb + 6 * b, w] = vx
+            st[7 * nb + 6 * b + 2, w] = rng.uniform(-0.2, 0.1)
+    return st
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+def test_hinged_boxes_matches_oracle(ostrich, dtype):
+    sc = _hinged_boxes()
+    W = 40
+    st = _hinged_states(sc, W, 4)
+    ub = S.random_controls(sc.n_servos, W, seed=4, low=-2, high=2)
+    g = np.random.default_rng(24).normal(size=st.shape)
+    g[13 * sc.n_bodies:] = 0
+    if dtype == "f64":
+        cfg = S.SolverConfig(budget=60, tol=1e-9)
+        _compare(sc, cfg, ostrich, st, ub, 0.1, "f64", 1e-7, 1e-6, 1e-6, 0.6, grads=g)
+    else:
+        cfg = S.SolverConfig(budget=40)
+        _compare(sc, cfg, ostrich, st, ub, 0.1, "f32", 1e-4, 1e-3, 1e-3, 0.6, grads=g,
+                 oracle_cfg=S.SolverConfig(budget=60, tol=1e-8), floor=3e-4, tol_grad_exact=3e-3)

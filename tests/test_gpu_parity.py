@@ -291,3 +291,34 @@ def test_hinged_boxes_matches_oracle(ostrich, dtype):
         cfg = S.SolverConfig(budget=40)
         _compare(sc, cfg, ostrich, st, ub, 0.1, "f32", 1e-4, 1e-3, 1e-3, 0.6, grads=g,
                  oracle_cfg=S.SolverConfig(budget=60, tol=1e-8), floor=3e-4, tol_grad_exact=3e-3)
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+def test_resting_robot_closed_form(ostrich, dtype):
+    """The CUDA path against the closed form of the robot standing on the plane (equal
+    rim loads, compliant sinking u_z = -kappa lambda_n, joint loads), without the oracle."""
+    from tests.test_oracle_pins import resting_robot_closed_form, resting_robot_state
+    sc = S.robot_plane_scene()
+    h, kappa = 0.1, 1e-4
+    W = 5
+    st = np.repeat(resting_robot_state(sc), W, axis=1)
+    tol = 1e-9 if dtype == "f64" else 2e-4
+    cfg = S.SolverConfig(budget=40, tol=1e-10 if dtype == "f64" else 1e-5, kappa=kappa)
+    r = _run_gpu(ostrich, sc, cfg, st, np.zeros((sc.n_servos, W)), h, dtype)
+    ln, uz, lz = resting_robot_closed_form(sc, h, kappa)
+    nb, nj = sc.n_bodies, len(sc.joints)
+    for w in range(W):
+        out = r["state"][:, w].double().numpy()
+        u = out[7 * nb:13 * nb].reshape(nb, 6)
+        # FP32: velocities to the Newton tolerance's order (2e-5 m/s)
+        assert np.abs(u[:, 2] - uz).max() <= (tol * abs(uz) if dtype == "f64" else 2e-5)
+        assert np.abs(np.delete(u, 2, axis=1)).max() <= (1e-12 if dtype == "f64" else 2e-5)
+        act = r["ids"][:, w].numpy() >= 0
+        assert act.sum() == 8
+        cl = out[sc.contact_lam_index:].reshape(-1, 3)
+        assert np.abs(cl[act, 0] - ln).max() <= tol * ln
+        assert np.abs(cl[:, 1:]).max() <= tol * ln
+        jl = out[sc.lam_index:sc.lam_index + 5 * nj].reshape(nj, 5)
+        assert np.abs(jl[:, 2] - np.array(lz)).max() <= tol * ln
+        assert np.abs(jl[:, [0, 1, 3, 4]]).max() <= tol * ln
+        assert np.abs(out[sc.lam_index + 5 * nj:sc.contact_lam_index]).max() <= tol * ln

@@ -253,6 +253,53 @@ def test_robot_step_invariants(w):
     assert np.abs(cl[inactive]).max() == 0.0
 
 
+def resting_robot_closed_form(sc, h, kappa, g=9.81):
+    """The robot standing still on the plane, zero servo targets (Sec. III-B rows with the
+    normal compliance kappa): the geometry is symmetric about the chassis centre, so its
+    eight rim contacts carry equal normal forces lambda_n; the compliant normal row reads
+    u_z + kappa lambda_n = 0 (the rims start exactly on the plane), and the vertical
+    momentum balance M u_z = -M g h + 8 h lambda_n gives
+        lambda_n = M g / (8 + M kappa / h),  u_z = -kappa lambda_n  (every body);
+    each wheel's joint carries lambda_z = 2 lambda_n - m_w (g + u_z / h) on its vertical
+    position row; every other velocity, friction and servo multiplier is zero."""
+    M = sum(b.mass for b in sc.bodies)
+    ln = M * g / (8.0 + M * kappa / h)
+    uz = -kappa * ln
+    lz = [2.0 * ln - sc.bodies[j.child].mass * (g + uz / h) for j in sc.joints]
+    return ln, uz, lz
+
+
+def resting_robot_state(sc):
+    s = np.zeros((sc.n_state, 1))
+    S._place_robot(s, sc, 0, 0.0, 0.0, S.ROBOT_CHASSIS_Z, 0.0)
+    return s
+
+
+def test_robot_resting_on_plane_closed_form():
+    sc = S.robot_plane_scene()
+    h, kappa = 0.1, 1e-4
+    orc = O.Oracle(sc, S.SolverConfig(budget=60, tol=1e-12, kappa=kappa))
+    r = orc.step(resting_robot_state(sc)[:, 0], np.zeros(sc.n_servos), h)
+    assert r["status"] == 0
+    ln, uz, lz = resting_robot_closed_form(sc, h, kappa)
+    nb, nj = sc.n_bodies, len(sc.joints)
+    out = r["state"]
+    u = out[7 * nb:13 * nb].reshape(nb, 6)
+    assert np.abs(u[:, 2] - uz).max() <= 1e-9 * abs(uz)
+    assert np.abs(np.delete(u, 2, axis=1)).max() <= 1e-12
+    act = r["ids"] >= 0
+    assert act.sum() == 8
+    cl = out[sc.contact_lam_index:].reshape(-1, 3)
+    assert np.abs(cl[act, 0] - ln).max() <= 1e-9 * ln
+    assert np.abs(cl[:, 1:]).max() <= 1e-9 * ln
+    jl = out[sc.lam_index:sc.lam_index + 5 * nj].reshape(nj, 5)
+    assert np.abs(jl[:, 2] - np.array(lz)).max() <= 1e-9 * ln
+    assert np.abs(jl[:, [0, 1, 3, 4]]).max() <= 1e-9 * ln
+    assert np.abs(out[sc.lam_index + 5 * nj:sc.contact_lam_index]).max() <= 1e-9 * ln
+    # impulses are h lambda in the same layout
+    assert r["impulses"][sc.contact_lam_index - sc.lam_index:].reshape(-1, 3)[act, 0] == pytest.approx(h * ln, rel=1e-9)
+
+
 # --------------------------------------------------------------------------
 # Jacobian: analytic rows equal the definition d c(q+(u))/du / h
 # --------------------------------------------------------------------------

@@ -273,6 +273,7 @@ def run_ours(args, rank, world_size, local_rank):
     if clocks:
         out["clocks"] = clocks
     if rank == 0 and not args.skip_extras:
+        out["param_grads"] = run_param_grads(ctx, chunk, torch)
         out["e2e"] = run_e2e(args, ctx, chunk, states, controls, g, torch)
         out["plain_form"] = run_plain(args, scene, cfg, states, controls, g, torch)
         out["cpu_baseline"] = run_cpu_baseline(args)
@@ -282,6 +283,34 @@ def run_ours(args, rank, world_size, local_rank):
             out["serving"] = run_serving(args, torch)
     ctx.close()
     return out
+
+
+def run_param_grads(ctx, chunk, torch, reps=20):
+    """The adjoint launch of one recorded step with and without the physical-parameter
+    gradients (servo gains, body masses; Eq. (17) with xi = theta), CUDA events."""
+    W = ctx.ld
+    dev = "cuda"
+    ds = torch.empty(ctx.n_state, W, dtype=torch.float32, device=dev)
+    du = torch.empty(ctx.n_servo, W, dtype=torch.float32, device=dev)
+    dkp = torch.empty(ctx.n_servo, W, dtype=torch.float32, device=dev)
+    dm = torch.empty(ctx.nb, W, dtype=torch.float32, device=dev)
+
+    def timed(fn):
+        for _ in range(3):
+            fn()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record()
+        for _ in range(reps):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    plain = timed(lambda: ctx.ostrich_adjoint(0, chunk.g[1], H, ds, du))
+    params = timed(lambda: ctx.ostrich_adjoint_params(0, chunk.g[1], H, ds, du, dkp, dm))
+    return {"worlds": W, "adjoint_ms": plain, "adjoint_params_ms": params,
+            "outputs": f"dL/dk_p ({ctx.n_servo} servo gains), dL/dm ({ctx.nb} body masses) per world"}
 
 
 def run_e2e(args, ctx, chunk, states, controls, g, torch):

@@ -1122,7 +1122,7 @@ S psi(const Solver& Sv, const std::vector<double>& gq, const std::vector<double>
   return acc;
 }
 
-struct AdjOut { std::vector<double> dq, du, dubar; };
+struct AdjOut { std::vector<double> dq, du, dubar, dkp, dmass; };
 
 void adjoint(const Solver& Sv, const double* dL_dsp, int mode, AdjOut& out) {
   const OScene& sc = *Sv.W.s;
@@ -1217,6 +1217,30 @@ void adjoint(const Solver& Sv, const double* dL_dsp, int mode, AdjOut& out) {
     else if (c < 7 * nb + nu) out.du[c - 7 * nb] = p.d;
     else out.dubar[c - 7 * nb - nu] = p.d;
   }
+  // Eq. (17) with xi = theta, the physical parameters: the explicit partial derivative
+  // of the stacked residual at the returned iterate, contracted with the adjoint.
+  //   servo gain k_p of a joint: only its servo row, Eq. (8), holds it, through
+  //     lambda_c / k_p:  d/dk_p = -lambda_c / k_p^2;
+  //   mass m_b of a body: only the linear rows of Eq. (10) for that body hold it
+  //     (m (v - v-) - h m g):  d/dm_b = (v - v-) - h g e_z.
+  // (The FB scaling what = J M^-1 J^T of the normal rows also holds m_b, but in the
+  // paper's adjoint it is a step-start constant like W, and the FB root does not move
+  // under it.)
+  const std::vector<double>& wr = mode == ADJ_EXACT ? wfull : wl;
+  out.dkp.assign(sc.n_servo, 0.0);
+  out.dmass.assign(nb, 0.0);
+  for (size_t i = 0; i < m; ++i) {
+    const Row& r = Sv.W.rows[i];
+    if (r.type != ROW_SERVO) continue;
+    const double kp = sc.j[r.joint].kp;
+    out.dkp[sc.servo_of_joint[r.joint]] = wr[i] * (-Sv.lam[r.lam] / (kp * kp));
+  }
+  for (int b = 0; b < nb; ++b) {
+    double acc = 0.0;
+    for (int k = 0; k < 3; ++k) acc += wu[6 * b + k] * (Sv.u[6 * b + k] - Sv.um[6 * b + k]);
+    acc += wu[6 * b + 2] * (-h * sc.g);
+    out.dmass[b] = acc;
+  }
 }
 
 }  // namespace
@@ -1255,10 +1279,11 @@ int oracle_step(const double* scene, const float* heights, const double* cfgv, c
 
 // Forward step plus adjoint (mode 0: paper, frozen W, forward Schur matrix;
 // mode 1: exact IFT).  dL_dstate_next has the state layout; lambda entries ignored.
+// dL_dkp (n_servo) and dL_dmass (nb), the servo-gain and body-mass gradients, may be null.
 int oracle_step_adjoint(const double* scene, const float* heights, const double* cfgv, const double* state_in,
                         const double* ubar, double h, const double* dL_dnext, int mode, double* state_out,
                         double* impulses, int32_t* ids, uint32_t* status, double* dL_dstate, double* dL_dubar,
-                        double* info) {
+                        double* info, double* dL_dkp, double* dL_dmass) {
   OScene s; OCfg cfg;
   if (!parse_scene(scene, heights, s)) return 1;
   parse_cfg(cfgv, cfg);
@@ -1274,6 +1299,8 @@ int oracle_step_adjoint(const double* scene, const float* heights, const double*
   for (int i = 0; i < 6 * s.nb; ++i) dL_dstate[7 * s.nb + i] = A.du[i];
   for (int i = 0; i < s.m_max; ++i) dL_dstate[13 * s.nb + i] = 0.0;
   for (int i = 0; i < s.n_servo; ++i) dL_dubar[i] = A.dubar[i];
+  if (dL_dkp) for (int i = 0; i < s.n_servo; ++i) dL_dkp[i] = A.dkp[i];
+  if (dL_dmass) for (int b = 0; b < s.nb; ++b) dL_dmass[b] = A.dmass[b];
   return 0;
 }
 
@@ -1284,7 +1311,8 @@ int oracle_step_adjoint(const double* scene, const float* heights, const double*
 // lambda layout (m_max entries).
 int oracle_adjoint_at(const double* scene, const float* heights, const double* cfgv, const double* state_in,
                       const double* ubar, double h, const double* u_ret, const double* lam_ret,
-                      const double* dL_dnext, int mode, double* dL_dstate, double* dL_dubar) {
+                      const double* dL_dnext, int mode, double* dL_dstate, double* dL_dubar, double* dL_dkp,
+                      double* dL_dmass) {
   OScene s; OCfg cfg;
   if (!parse_scene(scene, heights, s)) return 1;
   parse_cfg(cfgv, cfg);
@@ -1298,6 +1326,8 @@ int oracle_adjoint_at(const double* scene, const float* heights, const double* c
   for (int i = 0; i < 6 * s.nb; ++i) dL_dstate[7 * s.nb + i] = A.du[i];
   for (int i = 0; i < s.m_max; ++i) dL_dstate[13 * s.nb + i] = 0.0;
   for (int i = 0; i < s.n_servo; ++i) dL_dubar[i] = A.dubar[i];
+  if (dL_dkp) for (int i = 0; i < s.n_servo; ++i) dL_dkp[i] = A.dkp[i];
+  if (dL_dmass) for (int b = 0; b < s.nb; ++b) dL_dmass[b] = A.dmass[b];
   return 0;
 }
 

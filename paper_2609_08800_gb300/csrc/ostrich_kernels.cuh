@@ -1406,6 +1406,26 @@ __global__ void __launch_bounds__(128, 3) adjoint_kernel(const DevScene scp, con
     for (int c = 0; c < 6; ++c) wu[6 * b + c] = -o[c];
   }
   __syncthreads();
+  // Eq. (17) with xi = theta, the physical parameters: explicit partials of the rows
+  // that hold them, contracted with the adjoint.  Servo gain k_p: the servo row of
+  // Eq. (8) holds lambda_c / k_p, so d/dk_p = -lambda_c / k_p^2.  Body mass m_b: the
+  // linear rows of Eq. (10), m_b (v - v-) - h m_b g, so d/dm_b = (v - v-) - h g e_z.
+  if (a.dL_dkp) {
+    Real* dkp = reinterpret_cast<Real*>(a.dL_dkp);
+    for (int i = mc + 5 * sc.nj + tid; i < m; i += nth) {
+      const Real kp = Real(sc.kp[w.ref[i]]);
+      dkp[(size_t)(i - mc - 5 * sc.nj) * ld + world] = wl[i] * (-w.lk[i] / (kp * kp));
+    }
+  }
+  if (a.dL_dmass) {
+    Real* dm = reinterpret_cast<Real*>(a.dL_dmass);
+    for (int b = tid; b < nb; b += nth) {
+      Real acc = 0;
+      for (int k = 0; k < 3; ++k) acc += wu[6 * b + k] * (w.uk[6 * b + k] - w.um[6 * b + k]);
+      acc += wu[6 * b + 2] * (-hR * Real(sc.g));
+      dm[(size_t)b * ld + world] = acc;
+    }
+  }
   // dL/du- = -M w_u - h (df/du-)^T w_u ;  dL/dubar = -w_lambda of the servo rows
   Real* dout = reinterpret_cast<Real*>(a.dL_dstate);
   for (int b = tid; b < nb; b += nth) {

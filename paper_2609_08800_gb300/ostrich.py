@@ -69,6 +69,7 @@ def lib():
         L.ostrich_set_schedule.argtypes = [_vp, ctypes.c_int]
         L.ostrich_step.argtypes = [_vp, _vp, _vp, ctypes.c_double, _vp, _vp, _vp, _vp, _vp, ctypes.c_int, _vp]
         L.ostrich_adjoint.argtypes = [_vp, ctypes.c_int, _vp, ctypes.c_double, _vp, _vp, _vp]
+        L.ostrich_adjoint_params.argtypes = [_vp, ctypes.c_int, _vp, ctypes.c_double, _vp, _vp, _vp, _vp, _vp]
         L.ostrich_step_list.argtypes = [_vp, _vp, _vp, ctypes.c_double, _vp, _vp, _vp, _vp, _vp, _vp, _vp,
                                         ctypes.c_int, _vp]
         L.ostrich_adjoint_list.argtypes = [_vp, _vp, ctypes.c_double, _vp, _vp, _vp, _vp, ctypes.c_int, _vp]
@@ -189,6 +190,7 @@ class Context:
         lib().ostrich_layout(self._h, out)
         self.n_state, self.m_max, self.n_slots, self.n_servo = map(int, out)
         self.tape_slots = int(tape_slots)
+        self.nb = scene.n_bodies
         if threads is not None:
             self.set_threads(threads)
 
@@ -215,6 +217,12 @@ class Context:
     def ostrich_adjoint(self, tape_slot, dL_dnext, h, dL_dstate, dL_dcontrols=None, stream=None):
         self._check(lib().ostrich_adjoint(self._h, int(tape_slot), _ptr(dL_dnext), float(h), _ptr(dL_dstate),
                                           _ptr(dL_dcontrols), _stream(stream)), "ostrich_adjoint")
+
+    def ostrich_adjoint_params(self, tape_slot, dL_dnext, h, dL_dstate, dL_dcontrols=None, dL_dkp=None,
+                               dL_dmass=None, stream=None):
+        self._check(lib().ostrich_adjoint_params(self._h, int(tape_slot), _ptr(dL_dnext), float(h), _ptr(dL_dstate),
+                                                 _ptr(dL_dcontrols), _ptr(dL_dkp), _ptr(dL_dmass), _stream(stream)),
+                    "ostrich_adjoint_params")
 
     def ostrich_step_list(self, state_in, controls, h, state_out, worlds, tape_slots=None, impulses=None, ids=None,
                           status=None, iters=None, stream=None):
@@ -263,6 +271,18 @@ class Context:
         du = torch.empty(max(self.n_servo, 1), self.ld, dtype=self.dtype, device=dev)
         self.ostrich_adjoint(tape_slot, dL_dnext, h, ds, du, stream)
         return ds, du[:self.n_servo]
+
+    def adjoint_params(self, tape_slot, dL_dnext, h, stream=None):
+        """The adjoint plus the physical-parameter gradients: (dL/dstate, dL/dcontrols,
+        dL/dk_p [n_servo, ld], dL/dm [nb, ld])."""
+        import torch
+        dev = dL_dnext.device
+        ds = torch.empty(self.n_state, self.ld, dtype=self.dtype, device=dev)
+        du = torch.empty(max(self.n_servo, 1), self.ld, dtype=self.dtype, device=dev)
+        dkp = torch.empty(max(self.n_servo, 1), self.ld, dtype=self.dtype, device=dev)
+        dm = torch.empty(self.nb, self.ld, dtype=self.dtype, device=dev)
+        self.ostrich_adjoint_params(tape_slot, dL_dnext, h, ds, du, dkp, dm, stream)
+        return ds, du[:self.n_servo], dkp[:self.n_servo], dm
 
     def close(self):
         if getattr(self, "_h", None):

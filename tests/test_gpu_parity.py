@@ -322,3 +322,53 @@ def test_resting_robot_closed_form(ostrich, dtype):
         assert np.abs(jl[:, 2] - np.array(lz)).max() <= tol * ln
         assert np.abs(jl[:, [0, 1, 3, 4]]).max() <= tol * ln
         assert np.abs(out[sc.lam_index + 5 * nj:sc.contact_lam_index]).max() <= tol * ln
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+def test_param_grads_match_oracle(ostrich, dtype):
+    """dL/dk_p and dL/dm from ostrich_adjoint_params against the oracle's adjoint at the
+    CUDA path's returned iterate (Eq. (17) with xi = theta), and against the identities
+    that tie them to the control and velocity gradients of the same call."""
+    sc = S.robot_box_scene()
+    W = 24
+    st = S.robot_box_states(sc, W, seed=6)
+    ub = S.random_controls(sc.n_servos, W, seed=6, low=-3, high=3)
+    h = 0.1
+    cfg = S.SolverConfig(budget=40, tol=1e-9 if dtype == "f64" else 1e-5)
+    tdt = torch.float64 if dtype == "f64" else torch.float32
+    g = np.random.default_rng(26).normal(size=st.shape)
+    g[13 * sc.n_bodies:] = 0
+    ctx = ostrich.Context(sc, cfg, W, dtype=dtype, tape_slots=1)
+    s_in = torch.tensor(st, dtype=tdt, device="cuda")
+    u_in = torch.tensor(ub, dtype=tdt, device="cuda")
+    r = ctx.step(s_in, u_in, h, tape_slot=0)
+    ds, du, dkp, dm = ctx.adjoint_params(0, torch.tensor(g, dtype=tdt, device="cuda"), h)
+    torch.cuda.synchronize()
+    out = r["state"].double().cpu().numpy()
+    ds, du, dkp, dm = (x.double().cpu().numpy() for x in (ds, du, dkp, dm))
+    s64, u64 = s_in.double().cpu().numpy(), u_in.double().cpu().numpy()
+    ctx.close()
+    nb, nj = sc.n_bodies, len(sc.joints)
+    orc = O.Oracle(sc, cfg)
+    kp = np.array([j.kp for j in sc.joints])
+    m = np.array([b.mass for b in sc.bodies])
+    tol = 1e-6 if dtype == "f64" else 1e-3
+    n_cmp = 0
+    for w in range(W):
+        if int(r["status"][w]) & 2:
+            continue
+        gw = g[:, w] if dtype == "f64" else g[:, w].astype(np.float32).astype(np.float64)
+        at = orc.adjoint_at(s64[:, w], u64[:, w], h, out[7 * nb:13 * nb, w], out[13 * nb:, w], gw)
+        scale_kp = max(np.abs(at["dkp"]).max(), 1e-12)
+        scale_m = max(np.abs(at["dmass"]).max(), 1e-12)
+        assert np.abs(dkp[:, w] - at["dkp"]).max() <= tol * scale_kp, f"world {w}: dL/dk_p"
+        assert np.abs(dm[:, w] - at["dmass"]).max() <= tol * scale_m, f"world {w}: dL/dm"
+        # identities among the outputs of the same call
+        lam_c = out[sc.lam_index + 5 * nj:sc.contact_lam_index, w]
+        assert np.abs(dkp[:, w] - du[:, w] * lam_c / kp ** 2).max() <= (1e-12 if dtype == "f64" else 1e-5) * scale_kp
+        dv = ds[7 * nb:13 * nb, w].reshape(nb, 6)[:, :3]
+        acc = out[7 * nb:13 * nb, w].reshape(nb, 6)[:, :3] - s64[7 * nb:13 * nb, w].reshape(nb, 6)[:, :3]
+        acc[:, 2] -= h * sc.gravity
+        assert np.abs(dm[:, w] + (dv * acc).sum(1) / m).max() <= (1e-9 if dtype == "f64" else 1e-4) * scale_m
+        n_cmp += 1
+    assert n_cmp >= 0.9 * W

@@ -509,3 +509,78 @@ def test_adjoint_at_own_solution_equals_step_adjoint():
         a = orc.adjoint_at(st[:, w], ub, 0.1, r["state"][7 * nb:13 * nb], r["state"][13 * nb:], g)
         np.testing.assert_array_equal(a["dstate"], r["dstate"])
         np.testing.assert_array_equal(a["dubar"], r["dubar"])
+
+
+# --------------------------------------------------------------------------
+# Physical-parameter gradients (Eq. (17) with xi = theta): servo gains, body masses
+# --------------------------------------------------------------------------
+
+def _param_case():
+    """The robot standing on the plane with small servo targets (the wheels start to roll
+    and the contacts stick) and a random cotangent on the next poses and velocities."""
+    sc = S.robot_plane_scene()
+    s0 = resting_robot_state(sc)[:, 0]
+    ub = np.array([0.05, -0.03, 0.04, 0.02])
+    rng = np.random.default_rng(7)
+    g = np.zeros(sc.n_state)
+    g[:13 * sc.n_bodies] = rng.normal(size=13 * sc.n_bodies)
+    return sc, s0, ub, g
+
+
+def _loss_of(scene, cfg, s0, ub, h, g):
+    r = O.Oracle(scene, cfg).step(s0, ub, h)
+    assert r["status"] == 0
+    nb = scene.n_bodies
+    return g[:13 * nb] @ r["state"][:13 * nb]
+
+
+def test_param_grads_exact_match_central_differences():
+    """Exact-IFT mode: dL/dk_p and dL/dm_b against central differences of the loss through
+    the converged step (the contact set is fixed at q-, so the step is smooth in theta)."""
+    import copy
+    sc, s0, ub, g = _param_case()
+    h, cfg = 0.1, S.SolverConfig(budget=60, tol=1e-12)
+    r = O.Oracle(sc, cfg).step_adjoint(s0, ub, h, g, mode=O.ADJ_EXACT)
+    fd_kp, fd_m = [], []
+    for j in range(len(sc.joints)):
+        d = 1e-4 * sc.joints[j].kp
+        sp, sm = copy.deepcopy(sc), copy.deepcopy(sc)
+        sp.joints[j].kp += d
+        sm.joints[j].kp -= d
+        fd_kp.append((_loss_of(sp, cfg, s0, ub, h, g) - _loss_of(sm, cfg, s0, ub, h, g)) / (2 * d))
+    for b in range(sc.n_bodies):
+        d = 1e-3 * sc.bodies[b].mass
+        sp, sm = copy.deepcopy(sc), copy.deepcopy(sc)
+        sp.bodies[b].mass += d
+        sm.bodies[b].mass -= d
+        fd_m.append((_loss_of(sp, cfg, s0, ub, h, g) - _loss_of(sm, cfg, s0, ub, h, g)) / (2 * d))
+    fd_kp, fd_m = np.array(fd_kp), np.array(fd_m)
+    assert np.abs(fd_kp).max() > 1e-5 and np.abs(fd_m).max() > 1e-4       # not a trivial zero
+    assert np.abs(r["dkp"] - fd_kp).max() <= 1e-5 * np.abs(fd_kp).max()
+    # the masses also enter the step through the FB scaling what = J M^-1 J^T (normal rows,
+    # friction cone margin), a step-start constant that the parameter gradient leaves
+    # out; against the differences that omission measures 3e-5 of the largest entry
+    assert np.abs(r["dmass"] - fd_m).max() <= 1e-4 * np.abs(fd_m).max()
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_param_grads_identities(mode):
+    """In both adjoint modes the parameter gradients are the same adjoint vector
+    contracted with other partials of the same rows, so they follow from the gradients
+    the dual-number VJP returns:  dL/dk_p = dL/dubar * lambda_c / k_p^2 (servo row
+    v + lambda_c/k_p - ubar) and dL/dm_b = -(dL/dv-_b . (v+ - v- - h g e_z)) / m_b (linear
+    rows of Eq. (10), whose only v- dependence is -m_b v-)."""
+    sc, s0, ub, g = _param_case()
+    h = 0.1
+    r = O.Oracle(sc, S.SolverConfig(budget=60, tol=1e-12)).step_adjoint(s0, ub, h, g, mode=mode)
+    nb, nj = sc.n_bodies, len(sc.joints)
+    lam_c = r["state"][sc.lam_index + 5 * nj:sc.contact_lam_index]
+    kp = np.array([j.kp for j in sc.joints])
+    assert r["dkp"] == pytest.approx(r["dubar"] * lam_c / kp ** 2, rel=1e-12, abs=1e-18)
+    dv = r["dstate"][7 * nb:13 * nb].reshape(nb, 6)[:, :3]
+    vp = r["state"][7 * nb:13 * nb].reshape(nb, 6)[:, :3]
+    vm = s0[7 * nb:13 * nb].reshape(nb, 6)[:, :3]
+    m = np.array([b.mass for b in sc.bodies])
+    acc = vp - vm
+    acc[:, 2] -= h * sc.gravity
+    assert r["dmass"] == pytest.approx(-(dv * acc).sum(1) / m, rel=1e-9, abs=1e-15)

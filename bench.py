@@ -287,13 +287,14 @@ def run_ours(args, rank, world_size, local_rank):
 
 def run_param_grads(ctx, chunk, torch, reps=20):
     """The adjoint launch of one recorded step with and without the physical-parameter
-    gradients (servo gains, body masses; Eq. (17) with xi = theta), CUDA events."""
+    gradients (servo gains, body masses, inertias; Eq. (17) with xi = theta), CUDA events."""
     W = ctx.ld
     dev = "cuda"
     ds = torch.empty(ctx.n_state, W, dtype=torch.float32, device=dev)
     du = torch.empty(ctx.n_servo, W, dtype=torch.float32, device=dev)
     dkp = torch.empty(ctx.n_servo, W, dtype=torch.float32, device=dev)
     dm = torch.empty(ctx.nb, W, dtype=torch.float32, device=dev)
+    di = torch.empty(3 * ctx.nb, W, dtype=torch.float32, device=dev)
 
     def timed(fn):
         for _ in range(3):
@@ -308,9 +309,10 @@ def run_param_grads(ctx, chunk, torch, reps=20):
         return e0.elapsed_time(e1) / reps
 
     plain = timed(lambda: ctx.ostrich_adjoint(0, chunk.g[1], H, ds, du))
-    params = timed(lambda: ctx.ostrich_adjoint_params(0, chunk.g[1], H, ds, du, dkp, dm))
+    params = timed(lambda: ctx.ostrich_adjoint_params(0, chunk.g[1], H, ds, du, dkp, dm, di))
     return {"worlds": W, "adjoint_ms": plain, "adjoint_params_ms": params,
-            "outputs": f"dL/dk_p ({ctx.n_servo} servo gains), dL/dm ({ctx.nb} body masses) per world"}
+            "outputs": f"dL/dk_p ({ctx.n_servo} servo gains), dL/dm ({ctx.nb} body masses), "
+                       f"dL/dI ({3 * ctx.nb} principal moments) per world"}
 
 
 def run_e2e(args, ctx, chunk, states, controls, g, torch):

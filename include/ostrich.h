@@ -133,16 +133,18 @@ ostrich_status ostrich_adjoint(ostrich_ctx* ctx, int tape_slot, const void* dL_d
                                void* dL_dstate, void* dL_dcontrols, void* stream);
 
 /* ostrich_adjoint plus the gradients of the physical parameters (Eq. (17) with xi =
- * theta): dL/dk_p of each servo gain (n_servo x ld, servo order as the controls) and
- * dL/dm of each body mass (nb x ld), element type as the context's, either may be NULL.
- * They contract the step's adjoint with the explicit partials of the rows holding the
- * parameter: the servo row of Eq. (8) (-lambda_c / k_p^2) and the linear rows of
- * Eq. (10) ((v+ - v-) - h g e_z).  The FB scaling what = J M^-1 J^T, which also holds
- * the masses, is a step-start constant here, as the frozen W is.  Arguments and errors
+ * theta): dL/dk_p of each servo gain (n_servo x ld, servo order as the controls), dL/dm
+ * of each body mass (nb x ld) and dL/dI of each body-frame principal moment (3 nb x ld,
+ * body-major), element type as the context's, any may be NULL.  They contract the
+ * step's adjoint with the explicit partials of the rows holding the parameter: the servo
+ * row of Eq. (8) (-lambda_c / k_p^2) and the linear and angular rows of Eq. (10)
+ * ((v+ - v-) - h g e_z; r_k (r_k . (w+ - w-)) + h (r_k . w-) (w- x r_k), r_k the k-th
+ * column of R(q-)).  The FB scaling what = J M^-1 J^T, which also holds the mass
+ * properties, is a step-start constant here, as the frozen W is.  Arguments and errors
  * otherwise as ostrich_adjoint. */
 ostrich_status ostrich_adjoint_params(ostrich_ctx* ctx, int tape_slot, const void* dL_dstate_next, double h,
                                       void* dL_dstate, void* dL_dcontrols, void* dL_dkp, void* dL_dmass,
-                                      void* stream);
+                                      void* dL_dinertia, void* stream);
 
 /* Step of a selected subset of worlds (Sec. III-C, per world as ostrich_step): CTA b
  * steps world worlds[b] and, when tape_slots is not NULL and tape_slots[b] >= 0,

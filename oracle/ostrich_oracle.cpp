@@ -1122,7 +1122,7 @@ S psi(const Solver& Sv, const std::vector<double>& gq, const std::vector<double>
   return acc;
 }
 
-struct AdjOut { std::vector<double> dq, du, dubar, dkp, dmass; };
+struct AdjOut { std::vector<double> dq, du, dubar, dkp, dmass, dinertia; };
 
 void adjoint(const Solver& Sv, const double* dL_dsp, int mode, AdjOut& out) {
   const OScene& sc = *Sv.W.s;
@@ -1222,13 +1222,17 @@ void adjoint(const Solver& Sv, const double* dL_dsp, int mode, AdjOut& out) {
   //   servo gain k_p of a joint: only its servo row, Eq. (8), holds it, through
   //     lambda_c / k_p:  d/dk_p = -lambda_c / k_p^2;
   //   mass m_b of a body: only the linear rows of Eq. (10) for that body hold it
-  //     (m (v - v-) - h m g):  d/dm_b = (v - v-) - h g e_z.
+  //     (m (v - v-) - h m g):  d/dm_b = (v - v-) - h g e_z;
+  //   principal moment I_k of a body: its angular rows, I_w (w - w-) + h w- x (I_w w-)
+  //     with I_w = R diag(I) R^T at q-, so with r_k the k-th column of R,
+  //     d/dI_k = r_k (r_k . (w - w-)) + h (r_k . w-) (w- x r_k).
   // (The FB scaling what = J M^-1 J^T of the normal rows also holds m_b, but in the
   // paper's adjoint it is a step-start constant like W, and the FB root does not move
   // under it.)
   const std::vector<double>& wr = mode == ADJ_EXACT ? wfull : wl;
   out.dkp.assign(sc.n_servo, 0.0);
   out.dmass.assign(nb, 0.0);
+  out.dinertia.assign(3 * nb, 0.0);
   for (size_t i = 0; i < m; ++i) {
     const Row& r = Sv.W.rows[i];
     if (r.type != ROW_SERVO) continue;
@@ -1240,6 +1244,15 @@ void adjoint(const Solver& Sv, const double* dL_dsp, int mode, AdjOut& out) {
     for (int k = 0; k < 3; ++k) acc += wu[6 * b + k] * (Sv.u[6 * b + k] - Sv.um[6 * b + k]);
     acc += wu[6 * b + 2] * (-h * sc.g);
     out.dmass[b] = acc;
+    Pose<double> Pm = pose_of(Sv.qm.data() + 7 * b);
+    V3<double> wm = mk(Sv.um[6 * b + 3], Sv.um[6 * b + 4], Sv.um[6 * b + 5]);
+    V3<double> dw = mk(Sv.u[6 * b + 3] - wm.x, Sv.u[6 * b + 4] - wm.y, Sv.u[6 * b + 5] - wm.z);
+    V3<double> ww = mk(wu[6 * b + 3], wu[6 * b + 4], wu[6 * b + 5]);
+    for (int k = 0; k < 3; ++k) {
+      V3<double> rk = mk(Pm.R.a[0][k], Pm.R.a[1][k], Pm.R.a[2][k]);
+      V3<double> d = rk * dot(rk, dw) + cross(wm, rk) * (h * dot(rk, wm));
+      out.dinertia[3 * b + k] = dot(ww, d);
+    }
   }
 }
 
@@ -1279,11 +1292,12 @@ int oracle_step(const double* scene, const float* heights, const double* cfgv, c
 
 // Forward step plus adjoint (mode 0: paper, frozen W, forward Schur matrix;
 // mode 1: exact IFT).  dL_dstate_next has the state layout; lambda entries ignored.
-// dL_dkp (n_servo) and dL_dmass (nb), the servo-gain and body-mass gradients, may be null.
+// dL_dkp (n_servo), dL_dmass (nb) and dL_dinertia (3 nb, body-frame principal moments), the
+// servo-gain, body-mass and inertia gradients, may be null.
 int oracle_step_adjoint(const double* scene, const float* heights, const double* cfgv, const double* state_in,
                         const double* ubar, double h, const double* dL_dnext, int mode, double* state_out,
                         double* impulses, int32_t* ids, uint32_t* status, double* dL_dstate, double* dL_dubar,
-                        double* info, double* dL_dkp, double* dL_dmass) {
+                        double* info, double* dL_dkp, double* dL_dmass, double* dL_dinertia) {
   OScene s; OCfg cfg;
   if (!parse_scene(scene, heights, s)) return 1;
   parse_cfg(cfgv, cfg);
@@ -1301,6 +1315,7 @@ int oracle_step_adjoint(const double* scene, const float* heights, const double*
   for (int i = 0; i < s.n_servo; ++i) dL_dubar[i] = A.dubar[i];
   if (dL_dkp) for (int i = 0; i < s.n_servo; ++i) dL_dkp[i] = A.dkp[i];
   if (dL_dmass) for (int b = 0; b < s.nb; ++b) dL_dmass[b] = A.dmass[b];
+  if (dL_dinertia) for (int i = 0; i < 3 * s.nb; ++i) dL_dinertia[i] = A.dinertia[i];
   return 0;
 }
 
@@ -1312,7 +1327,7 @@ int oracle_step_adjoint(const double* scene, const float* heights, const double*
 int oracle_adjoint_at(const double* scene, const float* heights, const double* cfgv, const double* state_in,
                       const double* ubar, double h, const double* u_ret, const double* lam_ret,
                       const double* dL_dnext, int mode, double* dL_dstate, double* dL_dubar, double* dL_dkp,
-                      double* dL_dmass) {
+                      double* dL_dmass, double* dL_dinertia) {
   OScene s; OCfg cfg;
   if (!parse_scene(scene, heights, s)) return 1;
   parse_cfg(cfgv, cfg);
@@ -1328,6 +1343,7 @@ int oracle_adjoint_at(const double* scene, const float* heights, const double* c
   for (int i = 0; i < s.n_servo; ++i) dL_dubar[i] = A.dubar[i];
   if (dL_dkp) for (int i = 0; i < s.n_servo; ++i) dL_dkp[i] = A.dkp[i];
   if (dL_dmass) for (int b = 0; b < s.nb; ++b) dL_dmass[b] = A.dmass[b];
+  if (dL_dinertia) for (int i = 0; i < 3 * s.nb; ++i) dL_dinertia[i] = A.dinertia[i];
   return 0;
 }
 

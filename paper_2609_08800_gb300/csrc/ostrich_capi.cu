@@ -251,11 +251,12 @@ ostrich_status ostrich_adjoint_list(ostrich_ctx* c, const void* dL_dnext, double
 
 ostrich_status ostrich_adjoint(ostrich_ctx* c, int tape_slot, const void* dL_dnext, double h, void* dL_dstate,
                                void* dL_dcontrols, void* stream) {
-  return ostrich_adjoint_params(c, tape_slot, dL_dnext, h, dL_dstate, dL_dcontrols, nullptr, nullptr, stream);
+  return ostrich_adjoint_params(c, tape_slot, dL_dnext, h, dL_dstate, dL_dcontrols, nullptr, nullptr, nullptr, stream);
 }
 
 ostrich_status ostrich_adjoint_params(ostrich_ctx* c, int tape_slot, const void* dL_dnext, double h, void* dL_dstate,
-                                      void* dL_dcontrols, void* dL_dkp, void* dL_dmass, void* stream) {
+                                      void* dL_dcontrols, void* dL_dkp, void* dL_dmass, void* dL_dinertia,
+                                      void* stream) {
   if (!c) return OSTRICH_EINVAL;
   if (tape_slot < 0 || tape_slot >= c->tape_slots) return fail(c, OSTRICH_EINVAL, "tape_slot out of range");
   if (!c->slot_written[tape_slot]) return fail(c, OSTRICH_ETAPE, "tape slot holds no recorded step");
@@ -264,7 +265,7 @@ ostrich_status ostrich_adjoint_params(ostrich_ctx* c, int tape_slot, const void*
   ost::AdjArgs a;
   a.tape = slot_ptr(c, tape_slot); a.dL_dnext = dL_dnext; a.dL_dstate = dL_dstate; a.dL_dcontrols = dL_dcontrols;
   a.ld = c->ld; a.n_worlds = c->n_worlds; a.world0 = 0; a.h = h;
-  a.dL_dkp = c->sc.n_servo > 0 ? dL_dkp : nullptr; a.dL_dmass = dL_dmass;
+  a.dL_dkp = c->sc.n_servo > 0 ? dL_dkp : nullptr; a.dL_dmass = dL_dmass; a.dL_dinertia = dL_dinertia;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   cudaError_t e = c->dtype == OSTRICH_F64 ? ost::launch_adjoint<double>(c->sc, a, c->threads, st)
                                           : ost::launch_adjoint<float>(c->sc, a, c->threads, st);

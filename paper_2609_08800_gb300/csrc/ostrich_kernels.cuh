@@ -1410,6 +1410,9 @@ __global__ void __launch_bounds__(128, 3) adjoint_kernel(const DevScene scp, con
   // that hold them, contracted with the adjoint.  Servo gain k_p: the servo row of
   // Eq. (8) holds lambda_c / k_p, so d/dk_p = -lambda_c / k_p^2.  Body mass m_b: the
   // linear rows of Eq. (10), m_b (v - v-) - h m_b g, so d/dm_b = (v - v-) - h g e_z.
+  // Principal moment I_k: the angular rows, I_w (w - w-) + h w- x (I_w w-) with
+  // I_w = R diag(I) R^T at q-, so d/dI_k = r_k (r_k . (w - w-)) + h (r_k . w-) (w- x r_k),
+  // r_k the k-th column of R(q-).
   if (a.dL_dkp) {
     Real* dkp = reinterpret_cast<Real*>(a.dL_dkp);
     for (int i = mc + 5 * sc.nj + tid; i < m; i += nth) {
@@ -1424,6 +1427,23 @@ __global__ void __launch_bounds__(128, 3) adjoint_kernel(const DevScene scp, con
       for (int k = 0; k < 3; ++k) acc += wu[6 * b + k] * (w.uk[6 * b + k] - w.um[6 * b + k]);
       acc += wu[6 * b + 2] * (-hR * Real(sc.g));
       dm[(size_t)b * ld + world] = acc;
+    }
+  }
+  if (a.dL_dinertia) {
+    Real* di = reinterpret_cast<Real*>(a.dL_dinertia);
+    for (int b = tid; b < nb; b += nth) {
+      Real R[9];
+      qmat(w.qm + 7 * b + 3, R);                 // R(q-); w.R holds R(q+) after the evaluation
+      const vec3<Real> wm = v3(w.um[6 * b + 3], w.um[6 * b + 4], w.um[6 * b + 5]);
+      const vec3<Real> dw = v3(w.uk[6 * b + 3] - wm.x, w.uk[6 * b + 4] - wm.y, w.uk[6 * b + 5] - wm.z);
+      const vec3<Real> ww = v3(wu[6 * b + 3], wu[6 * b + 4], wu[6 * b + 5]);
+      for (int k = 0; k < 3; ++k) {
+        const vec3<Real> rk = v3(R[k], R[3 + k], R[6 + k]);
+        const vec3<Real> c = cross3(wm, rk);
+        const Real s1 = dot3(rk, dw), s2 = hR * dot3(rk, wm);
+        di[(size_t)(3 * b + k) * ld + world] =
+            ww.x * (rk.x * s1 + c.x * s2) + ww.y * (rk.y * s1 + c.y * s2) + ww.z * (rk.z * s1 + c.z * s2);
+      }
     }
   }
   // dL/du- = -M w_u - h (df/du-)^T w_u ;  dL/dubar = -w_lambda of the servo rows

@@ -113,9 +113,9 @@ struct AdjArgs {
   const void* tape; const void* dL_dnext; void* dL_dstate; void* dL_dcontrols;
   int ld, n_worlds, world0; double h;
   const int32_t* list = nullptr; const int32_t* list_slot = nullptr; int n_list = 0, tape_slots = 0;
-  // optional physical-parameter gradients: dL/dk_p per servo (n_servo x ld) and dL/dm per
-  // body (nb x ld), or null
-  void* dL_dkp = nullptr; void* dL_dmass = nullptr;
+  // optional physical-parameter gradients: dL/dk_p per servo (n_servo x ld), dL/dm per
+  // body (nb x ld), dL/dI per body-frame principal moment (3 nb x ld), or null
+  void* dL_dkp = nullptr; void* dL_dmass = nullptr; void* dL_dinertia = nullptr;
 };
 
 // Tape record of one world for one step: inputs, returned iterate and the Schur factor

@@ -69,7 +69,7 @@ def lib():
         L.ostrich_set_schedule.argtypes = [_vp, ctypes.c_int]
         L.ostrich_step.argtypes = [_vp, _vp, _vp, ctypes.c_double, _vp, _vp, _vp, _vp, _vp, ctypes.c_int, _vp]
         L.ostrich_adjoint.argtypes = [_vp, ctypes.c_int, _vp, ctypes.c_double, _vp, _vp, _vp]
-        L.ostrich_adjoint_params.argtypes = [_vp, ctypes.c_int, _vp, ctypes.c_double, _vp, _vp, _vp, _vp, _vp]
+        L.ostrich_adjoint_params.argtypes = [_vp, ctypes.c_int, _vp, ctypes.c_double, _vp, _vp, _vp, _vp, _vp, _vp]
         L.ostrich_step_list.argtypes = [_vp, _vp, _vp, ctypes.c_double, _vp, _vp, _vp, _vp, _vp, _vp, _vp,
                                         ctypes.c_int, _vp]
         L.ostrich_adjoint_list.argtypes = [_vp, _vp, ctypes.c_double, _vp, _vp, _vp, _vp, ctypes.c_int, _vp]
@@ -219,9 +219,10 @@ class Context:
                                           _ptr(dL_dcontrols), _stream(stream)), "ostrich_adjoint")
 
     def ostrich_adjoint_params(self, tape_slot, dL_dnext, h, dL_dstate, dL_dcontrols=None, dL_dkp=None,
-                               dL_dmass=None, stream=None):
+                               dL_dmass=None, dL_dinertia=None, stream=None):
         self._check(lib().ostrich_adjoint_params(self._h, int(tape_slot), _ptr(dL_dnext), float(h), _ptr(dL_dstate),
-                                                 _ptr(dL_dcontrols), _ptr(dL_dkp), _ptr(dL_dmass), _stream(stream)),
+                                                 _ptr(dL_dcontrols), _ptr(dL_dkp), _ptr(dL_dmass), _ptr(dL_dinertia),
+                                                 _stream(stream)),
                     "ostrich_adjoint_params")
 
     def ostrich_step_list(self, state_in, controls, h, state_out, worlds, tape_slots=None, impulses=None, ids=None,
@@ -274,15 +275,16 @@ class Context:
 
     def adjoint_params(self, tape_slot, dL_dnext, h, stream=None):
         """The adjoint plus the physical-parameter gradients: (dL/dstate, dL/dcontrols,
-        dL/dk_p [n_servo, ld], dL/dm [nb, ld])."""
+        dL/dk_p [n_servo, ld], dL/dm [nb, ld], dL/dI [nb, 3, ld] of the principal moments)."""
         import torch
         dev = dL_dnext.device
         ds = torch.empty(self.n_state, self.ld, dtype=self.dtype, device=dev)
         du = torch.empty(max(self.n_servo, 1), self.ld, dtype=self.dtype, device=dev)
         dkp = torch.empty(max(self.n_servo, 1), self.ld, dtype=self.dtype, device=dev)
         dm = torch.empty(self.nb, self.ld, dtype=self.dtype, device=dev)
-        self.ostrich_adjoint_params(tape_slot, dL_dnext, h, ds, du, dkp, dm, stream)
-        return ds, du[:self.n_servo], dkp[:self.n_servo], dm
+        di = torch.empty(self.nb, 3, self.ld, dtype=self.dtype, device=dev)
+        self.ostrich_adjoint_params(tape_slot, dL_dnext, h, ds, du, dkp, dm, di, stream)
+        return ds, du[:self.n_servo], dkp[:self.n_servo], dm, di
 
     def close(self):
         if getattr(self, "_h", None):

@@ -326,7 +326,7 @@ def test_resting_robot_closed_form(ostrich, dtype):
 
 @pytest.mark.parametrize("dtype", ["f64", "f32"])
 def test_param_grads_match_oracle(ostrich, dtype):
-    """dL/dk_p and dL/dm from ostrich_adjoint_params against the oracle's adjoint at the
+    """dL/dk_p, dL/dm and dL/dI from ostrich_adjoint_params against the oracle's adjoint at the
     CUDA path's returned iterate (Eq. (17) with xi = theta), and against the identities
     that tie them to the control and velocity gradients of the same call."""
     sc = S.robot_box_scene()
@@ -342,10 +342,10 @@ def test_param_grads_match_oracle(ostrich, dtype):
     s_in = torch.tensor(st, dtype=tdt, device="cuda")
     u_in = torch.tensor(ub, dtype=tdt, device="cuda")
     r = ctx.step(s_in, u_in, h, tape_slot=0)
-    ds, du, dkp, dm = ctx.adjoint_params(0, torch.tensor(g, dtype=tdt, device="cuda"), h)
+    ds, du, dkp, dm, di = ctx.adjoint_params(0, torch.tensor(g, dtype=tdt, device="cuda"), h)
     torch.cuda.synchronize()
     out = r["state"].double().cpu().numpy()
-    ds, du, dkp, dm = (x.double().cpu().numpy() for x in (ds, du, dkp, dm))
+    ds, du, dkp, dm, di = (x.double().cpu().numpy() for x in (ds, du, dkp, dm, di))
     s64, u64 = s_in.double().cpu().numpy(), u_in.double().cpu().numpy()
     ctx.close()
     nb, nj = sc.n_bodies, len(sc.joints)
@@ -363,6 +363,8 @@ def test_param_grads_match_oracle(ostrich, dtype):
         scale_m = max(np.abs(at["dmass"]).max(), 1e-12)
         assert np.abs(dkp[:, w] - at["dkp"]).max() <= tol * scale_kp, f"world {w}: dL/dk_p"
         assert np.abs(dm[:, w] - at["dmass"]).max() <= tol * scale_m, f"world {w}: dL/dm"
+        scale_i = max(np.abs(at["dinertia"]).max(), 1e-12)
+        assert np.abs(di[:, :, w] - at["dinertia"]).max() <= tol * scale_i, f"world {w}: dL/dI"
         # identities among the outputs of the same call
         lam_c = out[sc.lam_index + 5 * nj:sc.contact_lam_index, w]
         assert np.abs(dkp[:, w] - du[:, w] * lam_c / kp ** 2).max() <= (1e-12 if dtype == "f64" else 1e-5) * scale_kp

@@ -584,3 +584,32 @@ def test_param_grads_identities(mode):
     acc = vp - vm
     acc[:, 2] -= h * sc.gravity
     assert r["dmass"] == pytest.approx(-(dv * acc).sum(1) / m, rel=1e-9, abs=1e-15)
+
+
+def test_inertia_grads_exact_match_central_differences():
+    """Exact-IFT mode: dL/dI_k (body-frame principal moments) against central differences
+    through the converged step, with every body spinning (~1 rad/s) so the gyroscopic
+    part h w- x (I_w w-) of Eq. (10) carries weight.  The moments also enter the FB
+    scaling what of the rim contacts (lever arm off the normal), a step-start constant the
+    gradient leaves out: 8e-6 of the largest entry here."""
+    import copy
+    sc, s0, ub, g = _param_case()
+    nb = sc.n_bodies
+    s0 = s0.copy()
+    rng = np.random.default_rng(11)
+    for b in range(nb):
+        s0[7 * nb + 6 * b + 3:7 * nb + 6 * b + 6] = rng.normal(scale=1.0, size=3)
+    h, cfg = 0.1, S.SolverConfig(budget=60, tol=1e-12)
+    r = O.Oracle(sc, cfg).step_adjoint(s0, ub, h, g, mode=O.ADJ_EXACT)
+    assert r["status"] == 0
+    fd = np.zeros((nb, 3))
+    for b in range(nb):
+        for k in range(3):
+            inertia = list(sc.bodies[b].inertia)
+            d = 1e-3 * inertia[k]
+            sp, sm = copy.deepcopy(sc), copy.deepcopy(sc)
+            sp.bodies[b].inertia = tuple(v + (d if i == k else 0.0) for i, v in enumerate(inertia))
+            sm.bodies[b].inertia = tuple(v - (d if i == k else 0.0) for i, v in enumerate(inertia))
+            fd[b, k] = (_loss_of(sp, cfg, s0, ub, h, g) - _loss_of(sm, cfg, s0, ub, h, g)) / (2 * d)
+    assert np.abs(fd).max() > 1e-2
+    assert np.abs(r["dinertia"] - fd).max() <= 5e-5 * np.abs(fd).max()

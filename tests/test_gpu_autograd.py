@@ -1,5 +1,6 @@
-"""Rollout autograd with the CUDA engine: checkpointed gradients are bit-identical to
-the plain ones, and the FP64 build's rollout gradient matches the oracle engine's."""
+"""Rollout autograd with the CUDA engine: checkpointed gradients (states, controls and
+the scene parameters) are bit-identical to the plain ones, and the FP64 build's rollout
+gradients match the oracle engine's."""
 import numpy as np
 import pytest
 
@@ -34,15 +35,17 @@ def test_checkpointing_is_bit_identical_fp32():
         eng = CudaEngine(sc, cfg, W, h, slots)
         s0 = st.clone().requires_grad_(True)
         u = ctl.clone().requires_grad_(True)
-        traj = rollout(s0, u, eng, segment=seg)
+        theta = eng.theta().requires_grad_(True)
+        traj = rollout(s0, u, eng, segment=seg, theta=theta)
         _loss(traj, sc.n_bodies).backward()
         torch.cuda.synchronize()
-        out.append((traj.detach().clone(), s0.grad.clone(), u.grad.clone()))
+        out.append((traj.detach().clone(), s0.grad.clone(), u.grad.clone(), theta.grad.clone()))
         eng.close()
     for o in out[1:]:
         assert torch.equal(o[0], out[0][0])
         assert torch.equal(o[1], out[0][1]) and torch.equal(o[2], out[0][2])
-    assert torch.isfinite(out[0][1]).all()
+        assert torch.equal(o[3], out[0][3])
+    assert torch.isfinite(out[0][1]).all() and torch.isfinite(out[0][3]).all()
 
 
 def test_fp64_rollout_gradient_matches_oracle_engine():
@@ -58,13 +61,19 @@ def test_fp64_rollout_gradient_matches_oracle_engine():
     eng = CudaEngine(sc, cfg, W, h, T, dtype="f64")
     s0 = torch.tensor(st, dtype=torch.float64, device="cuda", requires_grad=True)
     u = torch.tensor(ctl, dtype=torch.float64, device="cuda", requires_grad=True)
-    _loss(rollout(s0, u, eng), sc.n_bodies).backward()
-    g_s, g_u = s0.grad.cpu(), u.grad.cpu()
+    theta = eng.theta().requires_grad_(True)
+    _loss(rollout(s0, u, eng, theta=theta), sc.n_bodies).backward()
+    g_s, g_u, g_th = s0.grad.cpu(), u.grad.cpu(), theta.grad.clone()
     eng.close()
     oe = OracleEngine(sc, cfg, h, O.ADJ_PAPER)
     s0c = torch.tensor(st, dtype=torch.float64, requires_grad=True)
     uc = torch.tensor(ctl, dtype=torch.float64, requires_grad=True)
-    _loss(rollout(s0c, uc, oe), sc.n_bodies).backward()
+    thc = oe.theta().requires_grad_(True)
+    _loss(rollout(s0c, uc, oe, theta=thc), sc.n_bodies).backward()
     scale = max(s0c.grad.abs().max().item(), uc.grad.abs().max().item())
     assert (g_s - s0c.grad).abs().max().item() <= 1e-6 * scale
     assert (g_u - uc.grad).abs().max().item() <= 1e-6 * scale
+    ns, nb = sc.n_servos, sc.n_bodies
+    for sl in (slice(0, ns), slice(ns, ns + nb), slice(ns + nb, None)):
+        sc_th = thc.grad[sl].abs().max().item()
+        assert (g_th[sl] - thc.grad[sl]).abs().max().item() <= 1e-6 * sc_th

@@ -24,6 +24,7 @@ pytestmark = pytest.mark.gpu
 
 from oracle import oracle as O  # noqa: E402
 from paper_2609_08800_gb300 import scenes as S  # noqa: E402
+from tests.test_oracle_pins import hinged_boxes_scene, resting_closed_form  # noqa: E402
 
 
 @pytest.fixture(scope="module")
@@ -252,17 +253,6 @@ def test_terrain_fp64_matches_oracle(ostrich):
     _compare(sc, cfg, ostrich, st, ub, 0.1, "f64", 1e-7, 1e-6, 1e-6, 0.7, grads=g)
 
 
-def _hinged_boxes():
-    """Two boxes on the plane joined by a servoed revolute joint: both bodies carry
-    contact slots, so every joint row couples to two contact groups (the general
-    separator update, group by group)."""
-    m, a, b, c = 10.0, 0.4, 0.4, 0.2
-    bodies = [S.Body(mass=m, inertia=S._box_inertia(m, a, b, c), shape=S.SHAPE_BOX,
-                     half_extents=(a / 2, b / 2, c / 2)) for _ in range(2)]
-    joints = [S.Joint(parent=0, child=1, anchor_parent=(0.21, 0.0, 0.0), anchor_child=(-0.21, 0.0, 0.0), kp=50.0)]
-    return S.Scene("hinged_boxes", bodies, joints, S.Env(S.ENV_PLANE), 0.8)
-
-
 def _hinged_states(sc, W, seed):
     rng = np.random.default_rng(seed)
     nb = sc.n_bodies
@@ -278,7 +268,7 @@ def _hinged_states(sc, W, seed):
 
 @pytest.mark.parametrize("dtype", ["f64", "f32"])
 def test_hinged_boxes_matches_oracle(ostrich, dtype):
-    sc = _hinged_boxes()
+    sc = hinged_boxes_scene()
     W = 40
     st = _hinged_states(sc, W, 4)
     ub = S.random_controls(sc.n_servos, W, seed=4, low=-2, high=2)
@@ -374,3 +364,30 @@ def test_param_grads_match_oracle(ostrich, dtype):
         assert np.abs(dm[:, w] + (dv * acc).sum(1) / m).max() <= (1e-9 if dtype == "f64" else 1e-4) * scale_m
         n_cmp += 1
     assert n_cmp >= 0.9 * W
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+def test_resting_hinged_boxes_closed_form(ostrich, dtype):
+    """The CUDA path (general separator update: each joint row couples to two contact
+    groups) against the closed form of the two hinged boxes standing on the plane."""
+    from tests.test_oracle_pins import hinged_resting_state
+    sc = hinged_boxes_scene()
+    h, kappa = 0.1, 1e-4
+    W = 4
+    st = np.repeat(hinged_resting_state(sc)[:, None], W, axis=1)
+    tol = 1e-9 if dtype == "f64" else 2e-4
+    cfg = S.SolverConfig(budget=40, tol=1e-10 if dtype == "f64" else 1e-5, kappa=kappa)
+    r = _run_gpu(ostrich, sc, cfg, st, np.zeros((sc.n_servos, W)), h, dtype)
+    ln, uz = resting_closed_form(sc.bodies[0].mass, 4, h, kappa)
+    nb = sc.n_bodies
+    for w in range(W):
+        out = r["state"][:, w].double().numpy()
+        u = out[7 * nb:13 * nb].reshape(nb, 6)
+        assert np.abs(u[:, 2] - uz).max() <= (tol * abs(uz) if dtype == "f64" else 2e-5)
+        assert np.abs(np.delete(u, 2, axis=1)).max() <= (1e-12 if dtype == "f64" else 2e-5)
+        act = r["ids"][:, w].numpy() >= 0
+        assert act.sum() == 8
+        cl = out[sc.contact_lam_index:].reshape(-1, 3)
+        assert np.abs(cl[act, 0] - ln).max() <= tol * ln
+        assert np.abs(cl[:, 1:]).max() <= tol * ln
+        assert np.abs(out[sc.lam_index:sc.contact_lam_index]).max() <= tol * ln

@@ -275,6 +275,53 @@ def resting_robot_state(sc):
     return s
 
 
+def resting_closed_form(m, n_contacts, h, kappa, g=9.81):
+    """A body of mass m standing on the plane on n_contacts symmetric contacts that start
+    exactly on it (Sec. III-B with the normal compliance kappa): each carries
+    lambda_n = m g / (n + m kappa / h) and the body sinks at u_z = -kappa lambda_n."""
+    ln = m * g / (n_contacts + m * kappa / h)
+    return ln, -kappa * ln
+
+
+def hinged_boxes_scene():
+    """Two boxes on the plane joined by a servoed revolute joint: both bodies carry
+    contact slots, so every joint row couples to two contact groups."""
+    m, a, b, c = 10.0, 0.4, 0.4, 0.2
+    bodies = [S.Body(mass=m, inertia=S._box_inertia(m, a, b, c), shape=S.SHAPE_BOX,
+                     half_extents=(a / 2, b / 2, c / 2)) for _ in range(2)]
+    joints = [S.Joint(parent=0, child=1, anchor_parent=(0.21, 0.0, 0.0), anchor_child=(-0.21, 0.0, 0.0), kp=50.0)]
+    return S.Scene("hinged_boxes", bodies, joints, S.Env(S.ENV_PLANE), 0.8)
+
+
+def hinged_resting_state(sc):
+    s = np.zeros(sc.n_state)
+    for b, x in enumerate((-0.21, 0.21)):
+        s[7 * b:7 * b + 7] = (x, 0.0, 0.1, 1.0, 0.0, 0.0, 0.0)
+    return s
+
+
+def test_hinged_boxes_resting_closed_form():
+    """Two hinged boxes standing on the plane, zero servo target: each box rests on its
+    own four corners (mirror symmetry: the joint carries nothing), so every corner holds
+    m g / (4 + m kappa / h) and both boxes sink at -kappa lambda_n."""
+    sc = hinged_boxes_scene()
+    h, kappa = 0.1, 1e-4
+    r = O.Oracle(sc, S.SolverConfig(budget=60, tol=1e-12, kappa=kappa)).step(hinged_resting_state(sc), np.zeros(1), h)
+    assert r["status"] == 0
+    ln, uz = resting_closed_form(sc.bodies[0].mass, 4, h, kappa)
+    nb = sc.n_bodies
+    out = r["state"]
+    u = out[7 * nb:13 * nb].reshape(nb, 6)
+    assert np.abs(u[:, 2] - uz).max() <= 1e-9 * abs(uz)
+    assert np.abs(np.delete(u, 2, axis=1)).max() <= 1e-12
+    act = r["ids"] >= 0
+    assert act.sum() == 8
+    cl = out[sc.contact_lam_index:].reshape(-1, 3)
+    assert np.abs(cl[act, 0] - ln).max() <= 1e-9 * ln
+    assert np.abs(cl[:, 1:]).max() <= 1e-9 * ln
+    assert np.abs(out[sc.lam_index:sc.contact_lam_index]).max() <= 1e-9 * ln
+
+
 def test_robot_resting_on_plane_closed_form():
     sc = S.robot_plane_scene()
     h, kappa = 0.1, 1e-4

@@ -24,6 +24,7 @@ import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 import numpy as np
@@ -209,8 +210,7 @@ def run_ours(args, rank, world_size, local_rank):
     # live per-launch timing of the two kernels over the timed region
     evs = [[[torch.cuda.Event(enable_timing=True) for _ in range(2)] for _ in range(CHUNK)] for _ in range(args.steps)]
     eva = [[[torch.cuda.Event(enable_timing=True) for _ in range(2)] for _ in range(CHUNK)] for _ in range(args.steps)]
-    clk_path = os.path.join(ROOT, "gpurun_out" if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else ".",
-                            f".clocks_rank{rank}.csv")
+    clk_path = os.path.join(tempfile.gettempdir(), f"ostrich_clocks_rank{rank}_{os.getpid()}.csv")
     clk = sample_clocks_start(clk_path)
     start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()

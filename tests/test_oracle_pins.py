@@ -660,3 +660,32 @@ def test_inertia_grads_exact_match_central_differences():
             fd[b, k] = (_loss_of(sp, cfg, s0, ub, h, g) - _loss_of(sm, cfg, s0, ub, h, g)) / (2 * d)
     assert np.abs(fd).max() > 1e-2
     assert np.abs(r["dinertia"] - fd).max() <= 5e-5 * np.abs(fd).max()
+
+
+def test_sliding_box_trajectory_matches_discrete_closed_form_at_every_h():
+    """Timestep sweep (Sec. III-B, friction at the step's own h): a box launched at
+    v0 = 2 m/s along the plane decelerates by exactly mu g h per step until it sticks,
+    v_{n+1} = max(0, v_n - mu g h), x_{n+1} = x_n + h v_{n+1} (backward Euler), at every h;
+    the stopping distance tends to the continuous v0^2 / (2 mu g) as h -> 0, within v0 h."""
+    sc = S.box_drop_scene()
+    orc = O.Oracle(sc, S.SolverConfig(budget=60, k_min=4, tol=1e-10, kappa=0.0))
+    v0, mu, g = 2.0, 0.8, 9.81
+    for h in (0.0125, 0.025, 0.05, 0.1, 0.2):
+        s = S.box_drop_state(sc, 0.0, gap=0.0)[:, 0]
+        for _ in range(3):
+            s = orc.step(s, np.zeros(1), h)["state"]          # settle at rest on the plane
+        x0 = s[0]
+        s[7] = v0
+        v, x = v0, x0
+        for _ in range(int(round(0.4 / h))):
+            r = orc.step(s, np.zeros(1), h)
+            assert r["status"] & 2 == 0
+            s = r["state"]
+            v = max(0.0, v - mu * g * h)
+            x = x + h * v
+            # at h = 0.0125 the frozen-W iteration stalls at residuals of 1e-9 to 1e-6 m/s in
+            # the slow-sliding steps (any budget); the returned iterates stay within 1.5e-8
+            assert s[7] == pytest.approx(v, abs=5e-8)
+            assert s[0] == pytest.approx(x, abs=5e-8)
+        assert v == 0.0                                       # stopped within 0.4 s
+        assert abs((x - x0) - v0 ** 2 / (2 * mu * g)) <= v0 * h

@@ -17,9 +17,11 @@
 //               included) are forward-mode dual-number derivatives of one residual
 //               evaluation at the converged state.
 // Readings of passages the paper leaves open are listed beside the code that uses
-// them.  Parity unpinned: the robot/terrain steady states have no closed form; they
-// are pinned only through invariants (joint closure, servo law, complementarity,
-// cone admissibility) and finite differences.
+// them.  Parity unpinned for the robot's and the terrain's general motion: no closed
+// form; they are pinned through invariants (joint closure, servo law,
+// complementarity, cone admissibility) and finite differences.  Closed forms pin the
+// box drop and slide, the robot standing on the plane and two hinged boxes standing
+// on the plane.
 //
 // Build: g++ -O2 -std=c++17 -ffp-contract=off -shared -fPIC  (no FMA contraction, so
 // the FP32 contact predicate rounds exactly like the CUDA one on x86 and on Arm).

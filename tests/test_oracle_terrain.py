@@ -212,3 +212,25 @@ def test_terrain_rows_match_definition():
         assert (rows["meta"][:, 0] == 2).sum() >= 1
         mask = rows["meta"][:, 0] != 1
         np.testing.assert_allclose(rows["J"][mask], rows["Jdual"][mask], rtol=1e-9, atol=1e-9)
+
+
+def test_robot_resting_on_flat_heightmap_closed_form():
+    """The terrain contact path against the closed form of the robot standing still: on
+    a flat heightmap each rim finds one face under its lowest point, and the eight rim
+    contacts share the weight as on the plane, M g / (8 + M kappa / h) each, with every
+    body sinking at -kappa lambda_n."""
+    from tests.test_oracle_pins import resting_robot_closed_form, resting_robot_state
+    sc = _flat_scene()
+    h, kappa = 0.1, 1e-4
+    r = O.Oracle(sc, S.SolverConfig(budget=60, tol=1e-12, kappa=kappa)).step(
+        resting_robot_state(sc)[:, 0], np.zeros(sc.n_servos), h)
+    assert r["status"] == 0
+    ln, uz, _ = resting_robot_closed_form(sc, h, kappa)
+    nb = sc.n_bodies
+    act = r["ids"] >= 0
+    assert act.sum() == 8
+    cl = r["state"][sc.contact_lam_index:].reshape(-1, 3)
+    assert np.abs(cl[act, 0] - ln).max() <= 1e-9 * ln
+    assert np.abs(cl[:, 1:]).max() <= 1e-9 * ln
+    u = r["state"][7 * nb:13 * nb].reshape(nb, 6)
+    assert np.abs(u[:, 2] - uz).max() <= 1e-9 * abs(uz)

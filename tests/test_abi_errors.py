@@ -1,0 +1,63 @@
+"""Boundary error behaviour that needs no GPU: the C ABI validates a scene description
+and a solver configuration before it touches the device, and returns EINVAL (never
+aborts) on what it cannot represent; calls on a null context return EINVAL."""
+import copy
+import ctypes
+
+import pytest
+
+from paper_2609_08800_gb300 import build as B
+from paper_2609_08800_gb300 import ostrich as M
+from paper_2609_08800_gb300 import scenes as S
+
+OSTRICH_EINVAL = 1
+
+
+@pytest.fixture(scope="module")
+def lib():
+    B.build()
+    return M.lib()
+
+
+def _create(lib, scene, cfg=None, n_worlds=4, ld=0, dtype=0, tape_slots=1):
+    d, c = M.scene_desc(scene), M.solver_cfg(cfg or S.SolverConfig())
+    h = ctypes.c_void_p()
+    rc = lib.ostrich_create(ctypes.byref(d), ctypes.byref(c), n_worlds, ld, dtype, tape_slots, ctypes.byref(h))
+    return rc, h
+
+
+def _robot():
+    return S.robot_plane_scene()
+
+
+@pytest.mark.parametrize("case", ["zero_mass", "bad_inertia", "joint_self", "joint_out_of_range"])
+def test_create_rejects_invalid_scenes(lib, case):
+    sc = copy.deepcopy(_robot())
+    if case == "zero_mass":
+        sc.bodies[1].mass = 0.0
+    elif case == "bad_inertia":
+        sc.bodies[0].inertia = (1.0, -1.0, 1.0)
+    elif case == "joint_self":
+        sc.joints[0].child = sc.joints[0].parent
+    else:
+        sc.joints[2].child = 7
+    rc, h = _create(lib, sc)
+    assert rc == OSTRICH_EINVAL and not h.value
+
+
+@pytest.mark.parametrize("kw", [dict(n_worlds=0), dict(ld=2, n_worlds=4), dict(dtype=7), dict(tape_slots=-1)])
+def test_create_rejects_invalid_sizes(lib, kw):
+    rc, h = _create(lib, _robot(), **kw)
+    assert rc == OSTRICH_EINVAL and not h.value
+
+
+def test_create_rejects_negative_budget(lib):
+    rc, h = _create(lib, _robot(), cfg=S.SolverConfig(budget=-1))
+    assert rc == OSTRICH_EINVAL and not h.value
+
+
+def test_calls_on_a_null_context_return_einval(lib):
+    assert lib.ostrich_adjoint(None, 0, None, 0.1, None, None, None) == OSTRICH_EINVAL
+    assert lib.ostrich_adjoint_params(None, 0, None, 0.1, None, None, None, None, None, None) == OSTRICH_EINVAL
+    assert lib.ostrich_step(None, None, None, 0.1, None, None, None, None, None, -1, None) == OSTRICH_EINVAL
+    assert lib.ostrich_tape_clear(None) == OSTRICH_EINVAL

@@ -485,15 +485,10 @@ def run_serving(args, torch):
     return out
 
 
-def run_cpu_baseline(args, impl_line=False):
-    """FP64 oracle on the host: forward + adjoint of a bounded sample of the workload."""
-    from oracle import oracle as O
-    W = args.cpu_worlds
-    scene, states, controls, g = make_inputs(max(W, 1), seed=0)
-    orc = O.Oracle(scene, S.SolverConfig(tol=FP32_TOL))
-    t0 = time.perf_counter()
+def _oracle_chunk_worlds(states, controls, g, orc):
+    """Forward CHUNK steps then CHUNK adjoints of each world on the oracle; world-steps run."""
     n = 0
-    for w in range(W):
+    for w in range(states.shape[1]):
         s = states[:, w].astype(np.float32).astype(np.float64)
         traj = [s]
         for t in range(CHUNK):
@@ -502,10 +497,50 @@ def run_cpu_baseline(args, impl_line=False):
         for t in reversed(range(CHUNK)):
             gg = orc.step_adjoint(traj[t], controls[t, :, w].astype(np.float64), H, gg)["dstate"]
         n += CHUNK
-    dt = time.perf_counter() - t0
-    return {"value": n / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+    return n
+
+
+_WORKER_ORACLE = None
+
+
+def _worker_init():
+    global _WORKER_ORACLE
+    from oracle import oracle as O
+    _WORKER_ORACLE = O.Oracle(S.robot_box_scene(), S.SolverConfig(tol=FP32_TOL))
+
+
+def _worker_run(job):
+    states, controls, g = job
+    return _oracle_chunk_worlds(states, controls, g, _WORKER_ORACLE)
+
+
+def run_cpu_baseline(args, impl_line=False, procs=1):
+    """FP64 oracle on the host: forward + adjoint of a bounded sample of the workload,
+    in this process (procs = 1) or split over `procs` spawned processes (one oracle each,
+    args.cpu_worlds worlds per process; pool start-up outside the timing)."""
+    from oracle import oracle as O
+    W = args.cpu_worlds * procs
+    scene, states, controls, g = make_inputs(max(W, 1), seed=0)
+    if procs <= 1:
+        orc = O.Oracle(scene, S.SolverConfig(tol=FP32_TOL))
+        t0 = time.perf_counter()
+        n = _oracle_chunk_worlds(states[:, :W], controls[:, :, :W], g[:, :W], orc)
+        dt = time.perf_counter() - t0
+        how = "single thread"
+    else:
+        import multiprocessing as mp
+        per = args.cpu_worlds
+        jobs = [(states[:, k * per:(k + 1) * per], controls[:, :, k * per:(k + 1) * per], g[:, k * per:(k + 1) * per])
+                for k in range(procs)]
+        with mp.get_context("spawn").Pool(procs, initializer=_worker_init) as pool:
+            pool.map(_worker_run, [(j[0][:, :1], j[1][:, :, :1], j[2][:, :1]) for j in jobs])    # warm: load, first call
+            t0 = time.perf_counter()
+            n = sum(pool.map(_worker_run, jobs))
+            dt = time.perf_counter() - t0
+        how = f"{procs} processes, one oracle each"
+    return {"value": n / dt, "unit": UNIT, "cores": procs, "kind": "oracle",
             "sample": f"{W} worlds x {CHUNK}-step chunk, forward + adjoint (the adjoint call re-solves the step), "
-                      f"single thread, {dt:.1f} s"}
+                      f"{how}, {dt:.1f} s"}
 
 
 # ---------------------------------------------------------------------------
@@ -552,6 +587,8 @@ def main():
     ap.add_argument("--threads", type=int, default=None, help="threads per world (default: autotuner table)")
     ap.add_argument("--plain-worlds", type=int, default=512)
     ap.add_argument("--cpu-worlds", type=int, default=24)
+    ap.add_argument("--cpu-procs", type=int, default=0,
+                    help="processes for the reference arm's oracle (0: all host cores)")
     ap.add_argument("--skip-extras", action="store_true",
                     help="time the batched kernels only (no e2e, plain-form or CPU legs); profiling runs")
     args = ap.parse_args()
@@ -560,16 +597,17 @@ def main():
         if rank != 0:
             return
         times = []
+        procs = max(1, args.cpu_procs or (os.cpu_count() or 1))
         for _ in range(args.warmup):
-            run_cpu_baseline(args)
+            run_cpu_baseline(args, procs=procs)
         for _ in range(args.steps):
-            times.append(run_cpu_baseline(args))
+            times.append(run_cpu_baseline(args, procs=procs))
         v = statistics.median(t["value"] for t in times)
         line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
-                "warmup": args.warmup, "ms_per_step": 1e3 * args.cpu_worlds * CHUNK / v, "higher_is_better": True,
-                "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "warmup": args.warmup, "ms_per_step": 1e3 * args.cpu_worlds * procs * CHUNK / v,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
                 "config": {"workload": "robot_over_box_8192_worlds_fp32_fwd_adj_chunk10",
-                           "sample_worlds": args.cpu_worlds},
+                           "sample_worlds": args.cpu_worlds * procs},
                 "cpu_baseline": dict(times[-1], value=v),
                 "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
         print(json.dumps(line))

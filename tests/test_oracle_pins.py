@@ -689,3 +689,166 @@ def test_sliding_box_trajectory_matches_discrete_closed_form_at_every_h():
             assert s[0] == pytest.approx(x, abs=5e-8)
         assert v == 0.0                                       # stopped within 0.4 s
         assert abs((x - x0) - v0 ** 2 / (2 * mu * g)) <= v0 * h
+
+
+# --------------------------------------------------------------------------
+# paper-mode (frozen W) adjoint on a sliding contact; truncated pull-back
+# --------------------------------------------------------------------------
+
+def _corner_what(b, k):
+    """J_n M^-1 J_n^T of bottom corner k of a flat box on z = 0, from its geometry."""
+    hx, hy, hz = b.half_extents
+    rho = np.array([hx if k & 1 else -hx, hy if k & 2 else -hy, hz if k & 4 else -hz])
+    rn = np.cross(rho, [0.0, 0.0, 1.0])
+    return 1.0 / b.mass + rn @ (rn / np.array(b.inertia))
+
+
+def _paper_sliding_ratio(sc, h, v_plus, lam_n, act, kappa=0.0):
+    """Closed form of dv+/dv- for a flat box sliding on a plane under the paper's frozen W
+    (Sec. III-B, III-D): each sliding corner i linearises to dv + (W_i + rho_i + kappa) dlam_f = 0,
+    with W_i = v+/(mu lam_n,i) (the sliding branch) and rho_i = h what_i (the radial term of
+    W's |lambda_f| dependence, which the paper keeps); the normal rows hold pitch and roll,
+    so m dv+ = m dv- + h sum dlam_f gives 1 / (1 + (h/m) sum_i 1/(W_i + rho_i + kappa))."""
+    b = sc.bodies[0]
+    tot = 0.0
+    for k in range(8):
+        if act[k]:
+            tot += 1.0 / (v_plus / (sc.mu * lam_n[k]) + h * _corner_what(b, k) + kappa)
+    return 1.0 / (1.0 + h / b.mass * tot)
+
+
+@pytest.mark.parametrize("v", [0.9, 1.5, 3.0])
+def test_paper_adjoint_on_sliding_box_closed_form(v):
+    """A flat box resting on the plane, pushed to slide (v+ = v- - mu g h > 0): the paper's
+    adjoint gives dv+/dv- = 1/(1 + (h/m) sum_i 1/(W_i + h what_i)) (frozen-W linearisation),
+    the exact IFT gives 1 (the slide loses mu g h whatever v- is)."""
+    sc = S.box_drop_scene()
+    h = 0.1
+    orc = O.Oracle(sc, _box_cfg())
+    s = S.box_drop_state(sc, 0.0, gap=0.0)[:, 0]
+    for _ in range(4):
+        s = orc.step(s, np.zeros(1), h)["state"]
+    s[7] = v
+    g = np.zeros(sc.n_state)
+    g[7] = 1.0
+    rp = orc.step_adjoint(s, np.zeros(1), h, g, mode=O.ADJ_PAPER)
+    re = orc.step_adjoint(s, np.zeros(1), h, g, mode=O.ADJ_EXACT)
+    v_plus = rp["state"][7]
+    assert v_plus == pytest.approx(v - 0.8 * 9.81 * h, abs=1e-9)
+    lam = rp["state"][sc.lam_index:].reshape(-1, 3)
+    act = rp["ids"] >= 0
+    assert act.sum() == 4
+    ratio = _paper_sliding_ratio(sc, h, v_plus, lam[:, 0], act)
+    assert rp["dstate"][7] == pytest.approx(ratio, rel=1e-5)
+    assert ratio < 0.9                                    # a real bias, not a rounding effect
+    assert re["dstate"][7] == pytest.approx(1.0, abs=1e-9)
+
+
+def test_paper_adjoint_config1_bias():
+    """Config 1 (box drop, v0 from seed 0, T = 20): the exact gradient dx_T/dv0 is h; the
+    paper's frozen-W adjoint gives h times the landing step's sliding ratio (the box stops
+    in step 2, where sticking makes both modes agree), a bias of about -31 %."""
+    sc, st = S.box_drop_inputs(0)
+    h, T = 0.1, 20
+    orc = O.Oracle(sc, S.SolverConfig(budget=50, k_min=4, tol=1e-10, kappa=0.0))
+    states = [st[:, 0]]
+    for _ in range(T):
+        states.append(orc.step(states[-1], np.zeros(1), h)["state"])
+    grads = {}
+    for mode in (O.ADJ_PAPER, O.ADJ_EXACT):
+        g = np.zeros(sc.n_state)
+        g[0] = 1.0
+        for t in reversed(range(T)):
+            g = orc.step_adjoint(states[t], np.zeros(1), h, g, mode=mode)["dstate"]
+        grads[mode] = g[7]
+    r1 = orc.step(states[0], np.zeros(1), h)
+    lam = r1["state"][sc.lam_index:].reshape(-1, 3)
+    ratio = _paper_sliding_ratio(sc, h, r1["state"][7], lam[:, 0], r1["ids"] >= 0)
+    print(f"config-1 dx_T/dv0: exact {grads[O.ADJ_EXACT]:.6f}, paper {grads[O.ADJ_PAPER]:.6f} "
+          f"(bias {grads[O.ADJ_PAPER] / h - 1:+.4f})")
+    assert grads[O.ADJ_EXACT] == pytest.approx(h, abs=1e-9)
+    assert grads[O.ADJ_PAPER] == pytest.approx(h * ratio, rel=1e-5)
+    assert -0.35 < grads[O.ADJ_PAPER] / h - 1 < -0.25
+
+
+def _box_at_compliant_rest(sc, h, kappa, g0=9.81):
+    """A flat box at rest on the plane at the depth its compliance gives (each of the four
+    bottom corners carries m g / 4 and sits kappa h m g / 4 below the plane), warm-started
+    with those impulses: the step returns u+ = 0 and the same impulses."""
+    b = sc.bodies[0]
+    s = np.zeros(sc.n_state)
+    s[2] = b.half_extents[2] - h * kappa * b.mass * g0 / 4.0
+    s[3] = 1.0
+    lam = np.zeros((sc.n_slots, 3))
+    lam[:4, 0] = b.mass * g0 / 4.0                   # slots 0-3: the bottom corners (k & 4 == 0)
+    s[sc.lam_index:] = lam.ravel()
+    return s
+
+
+def _damping(sc, h, delta_rel=1e-6):
+    """delta = delta_rel mean diag(h J M^-1 J^T) over the 12 rows of the four bottom corners
+    of the flat box (normal z, tangents x and y), from the geometry."""
+    b = sc.bodies[0]
+    hx, hy, hz = b.half_extents
+    I = np.array(b.inertia)
+    d = []
+    for k in range(4):
+        rho = np.array([hx if k & 1 else -hx, hy if k & 2 else -hy, -hz])
+        for e in np.eye(3)[[2, 0, 1]]:
+            a = np.cross(rho, e)
+            d.append(h * (1.0 / b.mass + a @ (a / I)))
+    return delta_rel * float(np.mean(d))
+
+
+@pytest.mark.parametrize("kappa", [0.0, 1e-4])
+@pytest.mark.parametrize("pullback", [S.PULLBACK_FULL, S.PULLBACK_TRUNCATED])
+def test_resting_box_height_gradient_closed_form(kappa, pullback):
+    """Sec. IV-D truncated pull-back (and the full one): a box at rest on the plane, loss
+    z+.  Raising the box by dz makes the step lower it again through the normal rows; with
+    the compliance C = kappa + delta the paper's linearised rows give
+    dz+/dz- = C m / (4 h + C m) and dz+/dvz- = h C m / (4 h + C m) (0 for a rigid contact).
+    Dropping the contact point's first-order rigid motion from the truncated rows would
+    give dz+/dz- = 1 instead."""
+    sc = S.box_drop_scene()
+    h = 0.1
+    cfg = S.SolverConfig(budget=60, k_min=4, tol=1e-12, kappa=kappa, pullback=pullback)
+    orc = O.Oracle(sc, cfg)
+    s = _box_at_compliant_rest(sc, h, kappa)
+    g = np.zeros(sc.n_state)
+    g[2] = 1.0
+    r = orc.step_adjoint(s, np.zeros(1), h, g)
+    assert abs(r["state"][9]) < 1e-12 and r["state"][2] == pytest.approx(s[2], abs=1e-12)
+    C = kappa + _damping(sc, h)
+    m = sc.bodies[0].mass
+    assert r["dstate"][2] == pytest.approx(C * m / (4 * h + C * m), rel=1e-6)
+    assert r["dstate"][9] == pytest.approx(h * C * m / (4 * h + C * m), rel=1e-6)
+    assert r["dstate"][0] == pytest.approx(0.0, abs=1e-12) and r["dstate"][1] == pytest.approx(0.0, abs=1e-12)
+
+
+@pytest.mark.parametrize("kappa", [0.0, 1e-4])
+def test_truncated_minus_full_is_the_lever_arm_term(kappa):
+    """What truncation drops, by hand: for a box at rest on the plane (u+ = 0, lambda_f = 0,
+    each bottom corner carrying Lambda/4 = m g/4), the full pull-back differentiates the
+    force term -h lambda_n (R rho_i x n) . w_omega of each normal row through R(q-); the
+    truncated one holds the lever arm.  Summed over the corners (sum rho_i = -4 hz e_z) the
+    difference is d/dq [h Lambda hz ((R e_z)_y w_x - (R e_z)_x w_y)] at R = I, i.e.
+    -2 h Lambda hz (w_x, w_y) in the (qx, qy) entries and zero elsewhere, with
+    w_omega = -I^-1 dL/domega- (the shared adjoint at omega- = 0)."""
+    sc = S.box_drop_scene()
+    h = 0.1
+    s = _box_at_compliant_rest(sc, h, kappa)
+    g = np.random.default_rng(3).normal(size=sc.n_state)
+    g[13:] = 0.0
+    out = {}
+    for pb in (S.PULLBACK_FULL, S.PULLBACK_TRUNCATED):
+        orc = O.Oracle(sc, S.SolverConfig(budget=60, k_min=4, tol=1e-12, kappa=kappa, pullback=pb))
+        out[pb] = orc.step_adjoint(s, np.zeros(1), h, g)["dstate"]
+    d = out[S.PULLBACK_FULL][:13] - out[S.PULLBACK_TRUNCATED][:13]
+    b = sc.bodies[0]
+    w = -out[S.PULLBACK_FULL][10:13] / np.array(b.inertia)
+    lam_tot, hz = b.mass * 9.81, b.half_extents[2]
+    expect = np.zeros(13)
+    expect[4] = -2.0 * h * lam_tot * hz * w[0]
+    expect[5] = -2.0 * h * lam_tot * hz * w[1]
+    assert np.abs(expect[4:6]).min() > 1e-7                 # the case exercises the term
+    np.testing.assert_allclose(d, expect, rtol=1e-6, atol=1e-9 * np.abs(expect).max())

@@ -188,24 +188,30 @@ const char* ostrich_last_error(const ostrich_ctx* ctx);
 void ostrich_destroy(ostrich_ctx* ctx);
 
 /* Allocation-free step + adjoint (FP32), for callers that cannot call cudaMalloc: a
- * real-time control loop that must not allocate once running, work issued inside a
- * stream capture, or a plugin whose host framework owns all device memory.  The paper
- * has no counterpart; it adds no computation to ostrich_step / ostrich_adjoint.
+ * real-time control loop that must not allocate once running (an allocation can block
+ * or fail at an arbitrary moment), or a plugin whose host framework owns all device
+ * memory and hands out only the buffers it manages.  The paper has no counterpart; it
+ * adds no computation to ostrich_step / ostrich_adjoint.
  *
  * One forward step of n_worlds worlds (as ostrich_step, without impulses, ids or
- * status) followed at once by the adjoint of that step (as ostrich_adjoint), with the
- * tape in a fixed library array of OSTRICH_NOALLOC_SCRATCH_BYTES instead of a context.
- * Arrays are caller-owned device pointers in the layout above (ld >= n_worlds; 0 means
- * n_worlds).  No context is needed and nothing is allocated, freed or kept.
+ * status; one CTA of 64 threads per world) followed at once by the adjoint of that step
+ * (as ostrich_adjoint), with the tape in a fixed library array of
+ * OSTRICH_NOALLOC_SCRATCH_BYTES instead of a context.  Arrays are caller-owned device
+ * pointers in the layout above (ld >= n_worlds; 0 means n_worlds).  No context is
+ * needed and nothing is allocated, freed or kept.
  *
- * EINVAL if n_worlds times the scene's per-world tape record exceeds the array (for the
- * four-wheel robot over a box, 15.3 KB per world: at most 1097 worlds), or on the same
- * argument errors as ostrich_create / ostrich_step; ECUDA if a launch fails.
+ * EINVAL if n_worlds times the scene's per-world tape record exceeds the array (the
+ * record is ostrich_tape_bytes / n_worlds of an FP32 context for the same scene: 9280 B
+ * for the four-wheel robot over a box, so at most 1807 worlds per call), for heightmap
+ * scenes (env OSTRICH_ENV_HEIGHTMAP: the heights would need a device copy), or on the
+ * same argument errors as ostrich_create / ostrich_step; ECUDA if a launch fails.
  * The first call on a device resolves the array's device address on that device (with
- * it current); make that first call before any stream capture.  Every call on a device
- * shares the one array and leaves its contents behind; nothing in it needs clearing,
- * as the step writes every entry the adjoint reads.  Calls that overlap on the GPU
- * (different streams, or host threads) race on the array: order them on one stream. */
+ * it current) and caches it; make that first call before any stream capture, and do not
+ * use the entry point across a cudaDeviceReset (the cached address would be stale).
+ * Every call on a device shares the one array and leaves its contents behind; nothing
+ * in it needs clearing, as the step writes every entry the adjoint reads.  Calls that
+ * overlap on the GPU (different streams, or host threads) race on the array: order
+ * them on one stream. */
 #define OSTRICH_NOALLOC_SCRATCH_BYTES (16u << 20)
 ostrich_status ostrich_step_adjoint_noalloc(const ostrich_scene_desc* scene, const ostrich_solver_cfg* cfg,
                                             int n_worlds, int ld, const float* state_in, const float* controls,

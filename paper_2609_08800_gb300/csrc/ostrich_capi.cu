@@ -9,12 +9,11 @@
 
 #include "ostrich.h"
 #include "ostrich_scene.h"
+#include "ostrich_scene_build.h"
 
 namespace ost {
 template <class Real> cudaError_t launch_step(const DevScene&, const StepArgs&, int, cudaStream_t);
 template <class Real> cudaError_t launch_adjoint(const DevScene&, const AdjArgs&, int, cudaStream_t);
-template <class Real> size_t ws_bytes(const DevScene&);
-template <class Real> size_t ws_used(const DevScene&);
 }  // namespace ost
 
 struct ostrich_ctx {
@@ -56,25 +55,14 @@ ostrich_status ostrich_create(const ostrich_scene_desc* d, const ostrich_solver_
   if (!out) return OSTRICH_EINVAL;
   *out = nullptr;
   if (!d || !cfg) return OSTRICH_EINVAL;
+  if (n_worlds < 1 || (ld != 0 && ld < n_worlds) || tape_slots < 0) return OSTRICH_EINVAL;
   ostrich_ctx* c = new (std::nothrow) ostrich_ctx();
   if (!c) return OSTRICH_ENOMEM;
-  if (n_worlds < 1 || (ld != 0 && ld < n_worlds) || (dtype != OSTRICH_F32 && dtype != OSTRICH_F64) || tape_slots < 0 ||
-      d->n_bodies < 1 || d->n_bodies > ost::NB_CAP || d->n_joints < 0 || d->n_joints > ost::NJ_CAP ||
-      d->env < 0 || d->env > 2 || cfg->budget < 0 || cfg->k_min < 0) {
-    delete c;
-    return OSTRICH_EINVAL;
-  }
   ost::DevScene& s = c->sc;
-  std::memset(&s, 0, sizeof(s));
-  s.nb = d->n_bodies; s.nj = d->n_joints; s.env = d->env;
-  s.mu = d->mu; s.g = d->gravity;
-  for (int i = 0; i < 5; ++i) s.box[i] = d->box[i];
-  s.hn = d->hm_n; s.hsp = d->hm_spacing; s.hox = d->hm_origin[0]; s.hoy = d->hm_origin[1];
-  s.nf = s.env == ost::ENV_PLANE ? 1 : (s.env == ost::ENV_BOX ? 4 : 8);
-  if (s.env != ost::ENV_PLANE && s.env != ost::ENV_BOX && s.env != ost::ENV_HEIGHTMAP) { delete c; return OSTRICH_EINVAL; }
+  ostrich_status rc = ost::build_scene(d, cfg, dtype, s);
+  if (rc != OSTRICH_OK) { delete c; return rc; }
   if (s.env == ost::ENV_HEIGHTMAP) {
-    // at least one 2 x 2 block of cells; face ids must fit the 20-bit field of a contact id
-    if (!d->heights || s.hn < 3 || s.hn > 724 || !(s.hsp > 0)) { delete c; return OSTRICH_EINVAL; }
+    // the heights stay on the device for the context's life
     size_t bytes = (size_t)s.hn * s.hn * sizeof(float);
     void* hp = nullptr;
     if (cudaMalloc(&hp, bytes) != cudaSuccess) { cudaGetLastError(); delete c; return OSTRICH_ENOMEM; }
@@ -86,50 +74,7 @@ ostrich_status ostrich_create(const ostrich_scene_desc* d, const ostrich_solver_
     }
     s.heights = c->d_heights;
   }
-  int slots = 0;
-  for (int b = 0; b < s.nb; ++b) {
-    const ostrich_body_desc& bd = d->bodies[b];
-    if (!(bd.mass > 0) || !(bd.inertia[0] > 0) || !(bd.inertia[1] > 0) || !(bd.inertia[2] > 0)) { delete c; return OSTRICH_EINVAL; }
-    s.mass[b] = bd.mass;
-    for (int k = 0; k < 3; ++k) { s.inertia[b][k] = bd.inertia[k]; s.half[b][k] = bd.half_extents[k]; }
-    s.radius[b] = bd.radius; s.hw[b] = bd.half_width; s.shape[b] = bd.shape;
-    int cnt = bd.shape == ost::SHAPE_BOX ? 8 : (bd.shape == ost::SHAPE_WHEEL ? 2 * s.nf : 0);
-    s.slot_base[b] = slots; s.slot_count[b] = cnt;
-    for (int k = 0; k < cnt && slots + k < ost::SLOT_CAP; ++k) s.slot_body[slots + k] = (unsigned char)b;
-    slots += cnt;
-  }
-  if (slots > ost::SLOT_CAP) { delete c; return OSTRICH_EINVAL; }
-  s.n_slots = slots;
-  s.n_servo = 0;
-  for (int j = 0; j < s.nj; ++j) {
-    const ostrich_joint_desc& jd = d->joints[j];
-    if (jd.parent < 0 || jd.parent >= s.nb || jd.child < 0 || jd.child >= s.nb || jd.parent == jd.child) { delete c; return OSTRICH_EINVAL; }
-    s.jp[j] = jd.parent; s.jc[j] = jd.child;
-    for (int k = 0; k < 3; ++k) {
-      s.ap[j][k] = jd.anchor_parent[k]; s.ac[j][k] = jd.anchor_child[k];
-      s.axp[j][k] = jd.axis_parent[k]; s.axc[j][k] = jd.axis_child[k];
-      s.p1[j][k] = jd.perp1_parent[k]; s.p2[j][k] = jd.perp2_parent[k];
-    }
-    s.kp[j] = jd.kp;
-    s.servo_of[j] = jd.kp > 0 ? s.n_servo++ : -1;
-  }
-  s.m_max = 5 * s.nj + s.n_servo + 3 * s.n_slots;
-  s.n_state = 13 * s.nb + s.m_max;
-  ost::finish_scene(s);
-  s.budget = cfg->budget; s.kmin = cfg->k_min; s.ls = cfg->line_search; s.pullback = cfg->pullback;
-  s.tol = cfg->tol; s.delta_rel = cfg->delta_rel; s.kappa = cfg->kappa; s.eps = cfg->eps_fb; s.margin = cfg->margin;
-  if (s.m_max < 7 * s.nb) { delete c; return OSTRICH_EINVAL; }   // adjoint scratch reuse
-  // FP32 factors lose the small eigenvalues (contact compliance kappa) of the Schur
-  // matrix.  The adjoint solves once, so it refines its solution against the
-  // matrix-free product (8 sweeps); the forward Newton iteration corrects an inexact
-  // step by itself (without refinement it takes the same number of iterations to the
-  // same residuals), so its solves are not refined.
-  s.refine = 0;
-  s.refine_adj = dtype == OSTRICH_F32 ? 8 : 0;
   c->n_worlds = n_worlds; c->ld = ld ? ld : n_worlds; c->dtype = dtype; c->tape_slots = tape_slots;
-  size_t smem = dtype == OSTRICH_F64 ? ost::ws_bytes<double>(s) : ost::ws_bytes<float>(s);
-  size_t used = dtype == OSTRICH_F64 ? ost::ws_used<double>(s) : ost::ws_used<float>(s);
-  if (smem > 227 * 1024 || used > smem) { delete c; return OSTRICH_EINVAL; }
   ost::TapeLayout tl = ost::tape_layout(s);
   c->tape_world_elems = (size_t)tl.total;
   if (tape_slots > 0) {

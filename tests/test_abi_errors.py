@@ -61,3 +61,21 @@ def test_calls_on_a_null_context_return_einval(lib):
     assert lib.ostrich_adjoint_params(None, 0, None, 0.1, None, None, None, None, None, None) == OSTRICH_EINVAL
     assert lib.ostrich_step(None, None, None, 0.1, None, None, None, None, None, -1, None) == OSTRICH_EINVAL
     assert lib.ostrich_tape_clear(None) == OSTRICH_EINVAL
+
+
+def _noalloc(lib, scene, n_worlds):
+    """Call the allocation-free entry with placeholder (never dereferenced) pointers: the
+    checks that refuse the call come before any device work."""
+    d, c = M.scene_desc(scene), M.solver_cfg(S.SolverConfig())
+    p = ctypes.c_void_p(4096)
+    return lib.ostrich_step_adjoint_noalloc(ctypes.byref(d), ctypes.byref(c), n_worlds, 0, p, p, 0.1,
+                                            ctypes.c_void_p(8192), p, ctypes.c_void_p(12288), None, None)
+
+
+def test_noalloc_refuses_heightmap_scenes(lib):
+    assert _noalloc(lib, S.terrain_scene(n=16), 4) == OSTRICH_EINVAL
+
+
+def test_noalloc_refuses_worlds_beyond_its_array(lib):
+    # 9280 B of tape per robot-over-box world: 1807 fit the 16 MiB array, 1808 do not
+    assert _noalloc(lib, S.robot_box_scene(), 1808) == OSTRICH_EINVAL

@@ -44,14 +44,19 @@ SM_COUNT_GB300 = 152
 FP32_LANES_PER_SM = 128
 
 
-def world_flops(iters, rows, groups, sep, refine=2, trials_per_iter=1):
+# Refinement sweeps per Schur solve of the forward step kernel: none (the Newton
+# iteration corrects an inexact step itself; only the adjoint's single solve is refined).
+FORWARD_REFINE_SWEEPS = 0
+
+
+def world_flops(iters, rows, groups, sep, refine=FORWARD_REFINE_SWEEPS, trials_per_iter=1):
     """Algorithmic FP32 flops of one world-step of the forward kernel (structured count).
 
     iters: Newton iterations run; rows: active rows m; groups: contact rows per body
     group p_g; sep: separator rows s.  Per evaluation 250 m (residual, Jacobian,
     dynamics); per assembly: group blocks 6 p(p+1), coupling 72 p, separator 12 s(s+1);
     per factorisation: sum p^3/3 + 6 p^2 + 36 p, plus s^3/3; per solve 2 (sum p^2 + s^2)
-    + 24 sum p, plus 48 m per refinement product."""
+    + 24 sum p, plus 48 m per refinement product (the forward kernel runs none)."""
     m = rows
     ev = 250.0 * m
     asm = sum(6.0 * p * (p + 1) + 72.0 * p for p in groups) + 12.0 * sep * (sep + 1)
@@ -59,6 +64,18 @@ def world_flops(iters, rows, groups, sep, refine=2, trials_per_iter=1):
     sol = 2.0 * (sum(p * p for p in groups) + sep * sep) + 24.0 * sum(groups)
     per_iter = asm + fac + (1 + refine) * sol + refine * 48.0 * m + trials_per_iter * ev
     return iters * per_iter + 2 * ev + asm + fac     # warm-start eval, final eval, taped factor
+
+
+def world_bytes(scene, rows, tape_record_bytes, elem=4, persistent=True):
+    """Algorithmic HBM bytes of one world-step of the forward kernel: the inputs it reads
+    (q-, u-, the warm-start multipliers of its active rows, the servo targets), the
+    outputs it writes (the whole next state, impulses, contact ids, status and
+    iteration words), its tape record, and the schedule's per-world words."""
+    nb = scene.n_bodies
+    reads = (13 * nb + rows + scene.n_servos) * elem
+    writes = (scene.n_state + scene.m_max) * elem + 4 * (scene.n_slots + 2)
+    sched = 12 if persistent else 0
+    return reads + writes + tape_record_bytes + sched
 
 
 def sample_clocks_start(path):
@@ -163,28 +180,6 @@ class Chunk:
                 ev_adj[t][1].record()
 
 
-def measured_traffic_per_world():
-    """DRAM bytes per world-step of the step kernel from the committed ncu summary, or
-    None when the CUDA sources have changed since that capture."""
-    import hashlib
-    prof = os.path.join(ROOT, "profiles", "step_kernel_robot_box_fp32.md")
-    csrc = os.path.join(ROOT, "paper_2609_08800_gb300", "csrc")
-    try:
-        text = open(prof).read()
-    except OSError:
-        return None
-    h = hashlib.sha1()
-    for f in sorted(os.listdir(csrc)):
-        if f.endswith((".cu", ".cuh", ".h")):
-            h.update(f.encode())
-            h.update(open(os.path.join(csrc, f), "rb").read())
-    vals = dict(line.split(": ", 1) for line in text.splitlines()
-                if line.startswith(("csrc_sha1: ", "step_dram_bytes_per_world_step: ")))
-    if vals.get("csrc_sha1") != h.hexdigest() or "step_dram_bytes_per_world_step" not in vals:
-        return None
-    return float(vals["step_dram_bytes_per_world_step"])
-
-
 def run_ours(args, rank, world_size, local_rank):
     import torch
     from paper_2609_08800_gb300.ostrich import Context
@@ -221,6 +216,8 @@ def run_ours(args, rank, world_size, local_rank):
     torch.cuda.synchronize()
     clocks = sample_clocks_stop(clk, clk_path, local_rank)
     ms = start.elapsed_time(stop) / args.steps
+    from paper_2609_08800_gb300.ostrich import probe_ffma
+    peak_ffma, probe_ms = probe_ffma()
     ms = dist_max(ms)
     step_ms = [e[0].elapsed_time(e[1]) for k in range(args.steps) for e in evs[k]]
     adj_ms = [e[0].elapsed_time(e[1]) for k in range(args.steps) for e in eva[k]]
@@ -231,6 +228,9 @@ def run_ours(args, rank, world_size, local_rank):
     n_rows = iters >> 16
     sep = 5 * len(scene.joints) + scene.n_servos
     flops = 0.0
+    tape_rec = ctx.tape_bytes() / ctx.n_worlds
+    sched_on = getattr(ctx, "schedule", 0) == 1
+    traffic = float(sum(world_bytes(scene, int(r), tape_rec, persistent=sched_on) for r in n_rows.ravel())) / CHUNK
     for t in range(CHUNK):
         for w in range(W):
             groups = []
@@ -244,9 +244,8 @@ def run_ours(args, rank, world_size, local_rank):
     flops_per_launch = flops / CHUNK
     avg_step_ms = statistics.mean(step_ms)
     achieved = flops_per_launch / (avg_step_ms * 1e-3) / 1e12
-    sm_mhz = (clocks or {}).get("sm_max_mhz") or measured_peaks().get("sm_max_mhz", 2070.0)
-    peak = SM_COUNT_GB300 * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
-    traffic_pw = measured_traffic_per_world()
+    sm_mhz = (clocks or {}).get("sm_mhz") or measured_peaks().get("sm_max_mhz", 2070.0)
+    peak_derived = SM_COUNT_GB300 * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
     world_steps = W * CHUNK * world_size
     value = world_steps / (ms * 1e-3)
     out = {
@@ -262,12 +261,20 @@ def run_ours(args, rank, world_size, local_rank):
         "kernels": {"step_ms_avg": avg_step_ms, "adjoint_ms_avg": statistics.mean(adj_ms),
                     "newton_iters_mean": float(n_iter.mean()), "active_rows_mean": float(n_rows.mean()),
                     "newton_iters_hist": np.bincount(n_iter.ravel(), minlength=cfg.budget + 1).tolist()},
-        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                     "frac": achieved / peak,
-                     "traffic": (None if traffic_pw is None else traffic_pw * W),
-                     "traffic_source": "ncu dram__bytes_read+write of one 2048-world step launch "
-                                       "(profiles/step_kernel_robot_box_fp32.md), per world x worlds",
-                     "peak_source": f"152 SMs x 128 FP32 lanes x 2 flop x {sm_mhz:.0f} MHz (SM max clock)",
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_ffma, "unit": "TFLOP/s",
+                     "frac": achieved / peak_ffma,
+                     "traffic": traffic,
+                     "traffic_source": "algorithmic bytes of one step launch: per world q-, u-, warm-start "
+                                       "multipliers of the active rows and servo targets read; next state, "
+                                       "impulses, ids, status and iteration words, the tape record and the "
+                                       "schedule words written (the DRAM bytes ncu measures for the same "
+                                       "launch are in profiles/)",
+                     "hbm_gbs_achieved": traffic / (avg_step_ms * 1e-3) / 1e9,
+                     "peak_source": f"measured: FFMA-only probe kernel (ostrich_probe_ffma), {probe_ms:.1f} ms "
+                                    f"per launch, run beside the timed region",
+                     "peak_derived": peak_derived,
+                     "peak_derived_source": f"152 SMs x 128 FP32 lanes x 2 flop x {sm_mhz:.0f} MHz "
+                                            "(median SM clock sampled in the timed region)",
                      "kernel": "step_kernel<float>", "flops_per_launch": flops_per_launch},
     }
     if clocks:

@@ -11,7 +11,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libostrich.so")
-SOURCES = ["ostrich_kernels_f32.cu", "ostrich_kernels_f64.cu", "ostrich_capi.cu", "ostrich_noalloc.cu"]
+SOURCES = ["ostrich_kernels_f32.cu", "ostrich_kernels_f64.cu", "ostrich_capi.cu", "ostrich_noalloc.cu", "ostrich_probe.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-I" + os.path.join(ROOT, "include"), "-I" + CSRC]
 

@@ -85,6 +85,9 @@ def lib():
         L.ostrich_destroy.argtypes = [_vp]
         L.ostrich_step_adjoint_noalloc.argtypes = [ctypes.POINTER(SceneDesc), ctypes.POINTER(SolverCfg), ctypes.c_int,
                                                    ctypes.c_int, _vp, _vp, ctypes.c_double, _vp, _vp, _vp, _vp, _vp]
+        L.ostrich_probe_ffma.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, _vp, ctypes.POINTER(ctypes.c_size_t),
+                                         ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double), _vp]
+        L.ostrich_probe_ffma.restype = ctypes.c_int
         for name in ("ostrich_layout", "ostrich_set_threads", "ostrich_set_schedule", "ostrich_step", "ostrich_adjoint", "ostrich_tape_clear",
                      "ostrich_step_adjoint_noalloc", "ostrich_step_list", "ostrich_adjoint_list"):
             getattr(L, name).restype = ctypes.c_int
@@ -167,6 +170,23 @@ def ostrich_step_adjoint_noalloc(scene, cfg, n_worlds, state_in, controls, h, st
                                             _ptr(dL_dstate), _ptr(dL_dcontrols), _stream(stream))
     if rc != OSTRICH_OK:
         raise RuntimeError(f"ostrich_step_adjoint_noalloc failed with status {rc}")
+
+
+def probe_ffma(blocks_per_sm=2, iters=40000, reps=10, stream=None):
+    """Measured FP32 FFMA throughput of the current GPU (include/ostrich_probe.h):
+    returns (TFLOP/s, mean kernel ms).  A measurement helper, not part of the method."""
+    import torch
+    n = ctypes.c_size_t()
+    rc = lib().ostrich_probe_ffma(blocks_per_sm, iters, reps, None, ctypes.byref(n), None, None, None)
+    if rc != 0:
+        raise RuntimeError(f"ostrich_probe_ffma failed with CUDA error {rc}")
+    out = torch.empty(n.value, dtype=torch.float32, device="cuda")
+    tf, ms = ctypes.c_double(), ctypes.c_double()
+    rc = lib().ostrich_probe_ffma(blocks_per_sm, iters, reps, _ptr(out), ctypes.byref(n), ctypes.byref(tf),
+                                  ctypes.byref(ms), _stream(stream))
+    if rc != 0:
+        raise RuntimeError(f"ostrich_probe_ffma failed with CUDA error {rc}")
+    return tf.value, ms.value
 
 
 class Context:

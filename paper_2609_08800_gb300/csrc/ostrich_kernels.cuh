@@ -432,8 +432,18 @@ __device__ Real evaluate(const DevScene& sc, WS<Real>& w, const Real* u, const R
       Real cn = dot3(n, x) - w.sd[sl];
       Real ln = lam[i], l1 = lam[i + 1], l2 = lam[i + 2];
       Real a = cn / hR + kap * ln, bb = hw * ln;
+      // At an active contact b = h what lambda_n is large (~10 m/s) and a ~ 0, so the
+      // textbook forms a + b - s, 1 - a/s and 1 - b/s cancel; in FP32 that leaves ~1e-6
+      // m/s of noise in the row, which the small eigenvalue (~kappa) of the impulse split
+      // between redundant contacts amplifies to ~1e-3 N and the Newton iteration stalls.
+      // The same quantities in forms free of cancellation (exact rearrangements):
+      // a + b - s = (2ab - eps^2)/(a + b + s) for a + b > 0;  1 - a/s = (b^2 + eps^2)/(s (s + a))
+      // for a > 0;  1 - b/s likewise.
       Real s = ssqrt(a * a + bb * bb + eps * eps);
-      Real phi = a + bb - s, fa = Real(1) - a / s, fb = Real(1) - bb / s;
+      const Real apb = a + bb;
+      Real phi = apb > Real(0) ? (Real(2) * a * bb - eps * eps) / (apb + s) : apb - s;
+      Real fa = a > Real(0) ? (bb * bb + eps * eps) / (s * (s + a)) : Real(1) - a / s;
+      Real fb = bb > Real(0) ? (a * a + eps * eps) / (s * (s + bb)) : Real(1) - bb / s;
       Real scl = fa > Real(1e-12) ? fa : Real(1e-12);
       w.r2[i] = phi; w.rhat[i] = phi / scl; w.C[i] = kap + hw * fb / scl;
       // friction rows, Eq. (7): J_f u + (W + kappa) lambda_f with W from the FB reading
@@ -442,8 +452,9 @@ __device__ Real evaluate(const DevScene& sc, WS<Real>& w, const Real* u, const R
       Real lnp = ln > Real(0) ? ln : Real(0);
       Real g = hw * (Real(sc.mu) * lnp - lfn);
       Real sg = ssqrt(vt * vt + g * g + eps * eps);
-      Real phif = vt + g - sg;
-      Real num = vt - phif; if (num < Real(0)) num = Real(0);
+      // W's numerator max(0, vt - phi_eps(vt, g)) is sg - g >= 0; for g > 0 (sticking) it is
+      // the small difference of two large numbers, taken as (vt^2 + eps^2)/(sg + g)
+      Real num = g > Real(0) ? (vt * vt + eps * eps) / (sg + g) : sg - g;
       Real den = Real(sc.mu) * lnp; if (den < Real(1e-12)) den = Real(1e-12);
       Real W = num / den;
       Real rf1 = vel[1] + (W + kap) * l1, rf2 = vel[2] + (W + kap) * l2;
@@ -454,7 +465,7 @@ __device__ Real evaluate(const DevScene& sc, WS<Real>& w, const Real* u, const R
       // radial part of the friction block: rho e e^T, e = lambda_f/|lambda_f|
       Real rho = Real(0);
       if (num > Real(0)) {
-        Real fbg = Real(1) - g / sg;
+        Real fbg = num / sg;                  // 1 - g/sg
         rho = fbg * hw * lfn / den;
       }
       Real e1 = l1 / lfn, e2 = l2 / lfn;

@@ -1,18 +1,24 @@
 """Benchmark: forward + adjoint world-steps/s of the Ostrich per-step solve on GB300.
 
-Workload (one bench step): the wheeled robot over a box obstacle, 8192 worlds,
-FP32, a 10-step horizon chunk (the checkpoint segment length): 10 forward steps
-that record the tape, then 10 adjoint steps back through it, every step one launch
-of the step kernel / adjoint kernel over all worlds.  Inputs (states, per-step
-servo targets from seeded control splines, the loss cotangent) are resident in HBM
-when the timed region starts; every bench step restarts from the same inputs.
+Headline workload (one bench step = one optimisation iteration): the wheeled robot
+over a box obstacle, 8192 worlds per GPU, FP32, 8-knot wheel-velocity splines per
+world, a 100-step horizon (10 s at h = 0.1) rolled out through the autograd.Function
+with checkpoints every 10 steps, the loss gradient swept back by the IFT adjoint (the
+backward recomputes each 10-step segment into the tape first), and an Adam update of
+the knots (lr 0.3).  `value` counts W x T forward+adjoint world-steps per iteration
+over all ranks (replicas: each GPU runs its own worlds); the recompute is counted as
+cost, not as world-steps.  Inputs are resident in HBM when the timed region starts.
 
-Prints one JSON line.  `value` counts forward+adjoint world-steps per second over
-all ranks (replicas: each GPU runs its own 8192 worlds).  Extra keys:
-  e2e            the same metric through the public API with pinned host buffers,
-                 host->device inputs and device->host results inside the timed region
+Prints one JSON line.  Extra keys:
+  e2e            the same metric through the public API: every iteration copies its
+                 initial states up from pinned host memory and reads the losses and the
+                 updated knots back, inside the timed region
+  chunk          one 10-step chunk (10 forward steps recording the tape, 10 adjoints)
+                 repeated from the same states: per-kernel times, Newton histogram
+  roofline       ALU roofline of the step kernel (algorithmic flops / event time) in the
+                 chunk leg, against a measured FFMA peak
   plain_form     the same kernels launched once per world per step (W = 1)
-  roofline       ALU roofline of the step kernel (algorithmic flops / event time)
+  serving        the Poisson request stream: continuous batching, FIFO queue, plain form
   cpu_baseline   the FP64 oracle on the host cores, on a bounded sample
 `--impl reference` times the FP64 oracle instead (the reference arm).
 """
@@ -39,6 +45,8 @@ METRIC = "fwd+adjoint world-steps/s @8192 worlds"
 UNIT = "world-steps/s"
 H = 0.1
 CHUNK = 10
+OPT_T = 100      # horizon of the optimisation workload (10 s at h = 0.1)
+CHUNK_WARMUP, CHUNK_TIMED = 3, 5   # chunk leg: warm-up and timed chunks
 FP32_TOL = 1e-4      # m/s: the FP32 residual floor of this scene (FP32-rounded exact states sit near 1e-5)
 SM_COUNT_GB300 = 152
 FP32_LANES_PER_SM = 128
@@ -198,29 +206,30 @@ def run_ours(args, rank, world_size, local_rank):
     ctl = torch.tensor(controls, dtype=torch.float32, device=dev)
     gT = torch.tensor(g, dtype=torch.float32, device=dev)
     chunk = Chunk(ctx, torch, W)
-    for _ in range(args.warmup):
+    for _ in range(CHUNK_WARMUP):
         chunk.run(s0, ctl, gT, record_ids=True)
     torch.cuda.synchronize()
     dist_barrier()
     # live per-launch timing of the two kernels over the timed region
-    evs = [[[torch.cuda.Event(enable_timing=True) for _ in range(2)] for _ in range(CHUNK)] for _ in range(args.steps)]
-    eva = [[[torch.cuda.Event(enable_timing=True) for _ in range(2)] for _ in range(CHUNK)] for _ in range(args.steps)]
+    n_chunks = CHUNK_TIMED
+    evs = [[[torch.cuda.Event(enable_timing=True) for _ in range(2)] for _ in range(CHUNK)] for _ in range(n_chunks)]
+    eva = [[[torch.cuda.Event(enable_timing=True) for _ in range(2)] for _ in range(CHUNK)] for _ in range(n_chunks)]
     clk_path = os.path.join(tempfile.gettempdir(), f"ostrich_clocks_rank{rank}_{os.getpid()}.csv")
     clk = sample_clocks_start(clk_path)
     start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
     start.record()
-    for k in range(args.steps):
+    for k in range(n_chunks):
         chunk.run(s0, ctl, gT, evs[k], eva[k])
     stop.record()
     torch.cuda.synchronize()
     clocks = sample_clocks_stop(clk, clk_path, local_rank)
-    ms = start.elapsed_time(stop) / args.steps
+    ms = start.elapsed_time(stop) / n_chunks
     from paper_2609_08800_gb300.ostrich import probe_ffma
     peak_ffma, probe_ms = probe_ffma()
     ms = dist_max(ms)
-    step_ms = [e[0].elapsed_time(e[1]) for k in range(args.steps) for e in evs[k]]
-    adj_ms = [e[0].elapsed_time(e[1]) for k in range(args.steps) for e in eva[k]]
+    step_ms = [e[0].elapsed_time(e[1]) for k in range(n_chunks) for e in evs[k]]
+    adj_ms = [e[0].elapsed_time(e[1]) for k in range(n_chunks) for e in eva[k]]
     # algorithmic flops of the step launches (from the warm-up run: same inputs, same work)
     iters = np.stack([t.cpu().numpy() for t in chunk.iters])           # [CHUNK, W]
     ids = np.stack([t.cpu().numpy() for t in chunk.ids_all])           # [CHUNK, slots, W]
@@ -246,18 +255,27 @@ def run_ours(args, rank, world_size, local_rank):
     achieved = flops_per_launch / (avg_step_ms * 1e-3) / 1e12
     sm_mhz = (clocks or {}).get("sm_mhz") or measured_peaks().get("sm_max_mhz", 2070.0)
     peak_derived = SM_COUNT_GB300 * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
-    world_steps = W * CHUNK * world_size
-    value = world_steps / (ms * 1e-3)
+    chunk_value = W * CHUNK * world_size / (ms * 1e-3)
+    opt = run_optimisation(args, torch, rank, world_size)
     out = {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world_size, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "metric": METRIC, "value": opt["value"], "unit": UNIT, "n_gpus": world_size, "steps": opt["iterations"],
+        "warmup": args.warmup, "ms_per_step": opt["ms_per_iteration"], "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": f"robot_over_box_{W}_worlds_fp32_fwd_adj_chunk10", "worlds_per_gpu": W,
-                   "steps_per_chunk": CHUNK, "h": H, "newton_budget": cfg.budget,
-                   "threads_per_world": threads, "schedule": getattr(ctx, "schedule", 0),
+        "config": {"workload": f"robot_over_box_{W}_worlds_fp32_adam_T{OPT_T}_ckpt{CHUNK}",
+                   "worlds_per_gpu": W, "horizon_steps": OPT_T, "h": H, "checkpoint_every": CHUNK,
+                   "step": "one Adam iteration (lr 0.3) on 8-knot wheel splines: T forward steps, the backward's "
+                           "T recomputed steps and T adjoint steps; world-steps = W x T per iteration",
+                   "newton_budget": cfg.budget, "tol": FP32_TOL, "threads_per_world": opt["threads_per_world"],
                    "parallelism": f"replicas{world_size}",
-                   "l2": f"tape of one chunk {ctx.tape_bytes() * CHUNK / 1e9:.2f} GB > 129 MB L2 (no flush needed)"},
-        "gpu_launches": 2 * CHUNK * args.steps,
+                   "l2": "trajectory 0.61 GB and tape of one segment 0.76 GB per iteration > 129 MB L2 (no flush needed)"},
+        "gpu_launches": opt["gpu_launches_per_iteration"] * opt["iterations"],
+        "e2e": opt["e2e"],
+        "optimisation": {k: opt[k] for k in ("loss_first_warmup", "loss_first_timed", "loss_last_timed",
+                                             "last_iteration_ms", "iterations")},
+        "chunk": {"workload": f"robot_over_box_{W}_worlds_fp32_fwd_adj_chunk10 (every chunk restarts from the same "
+                              "states: steps 1-10 of the horizon, tape recorded in the forward, no recompute)",
+                  "value": chunk_value, "unit": UNIT, "ms_per_chunk": ms, "timed_chunks": n_chunks,
+                  "warmup_chunks": CHUNK_WARMUP, "schedule": getattr(ctx, "schedule", 0)},
         "kernels": {"step_ms_avg": avg_step_ms, "adjoint_ms_avg": statistics.mean(adj_ms),
                     "newton_iters_mean": float(n_iter.mean()), "active_rows_mean": float(n_rows.mean()),
                     "newton_iters_hist": np.bincount(n_iter.ravel(), minlength=cfg.budget + 1).tolist()},
@@ -270,6 +288,7 @@ def run_ours(args, rank, world_size, local_rank):
                                        "schedule words written (the DRAM bytes ncu measures for the same "
                                        "launch are in profiles/)",
                      "hbm_gbs_achieved": traffic / (avg_step_ms * 1e-3) / 1e9,
+                     "timed_region": "the chunk leg (step launches timed one by one with CUDA events)",
                      "peak_source": f"measured: FFMA-only probe kernel (ostrich_probe_ffma), {probe_ms:.1f} ms "
                                     f"per launch, run beside the timed region",
                      "peak_derived": peak_derived,
@@ -277,11 +296,13 @@ def run_ours(args, rank, world_size, local_rank):
                                             "(median SM clock sampled in the timed region)",
                      "kernel": "step_kernel<float>", "flops_per_launch": flops_per_launch},
     }
+    if opt["clocks"]:
+        out["clocks"] = opt["clocks"]
     if clocks:
-        out["clocks"] = clocks
+        out["chunk"]["clocks"] = clocks
     if rank == 0 and not args.skip_extras:
         out["param_grads"] = run_param_grads(ctx, chunk, torch)
-        out["e2e"] = run_e2e(args, ctx, chunk, states, controls, g, torch)
+        out["chunk"]["e2e"] = run_e2e(args, ctx, chunk, states, controls, g, torch)
         out["plain_form"] = run_plain(args, scene, cfg, states, controls, g, torch)
         out["cpu_baseline"] = run_cpu_baseline(args)
         if args.terrain_worlds > 0:
@@ -290,6 +311,103 @@ def run_ours(args, rank, world_size, local_rank):
             out["serving"] = run_serving(args, torch)
     ctx.close()
     return out
+
+
+def run_optimisation(args, torch, rank, world_size):
+    """Config 3 as stated: the robot over the box obstacle, args.worlds worlds per GPU, FP32,
+    8-knot wheel-velocity splines per world (seeded), horizon T = 100 at h = 0.1, rollout
+    through the autograd.Function with checkpoints every 10 steps (the backward recomputes
+    each segment into the tape, then sweeps the adjoint back through it), loss = squared
+    chassis distance to (3, 0) summed over the worlds, Adam on the knots with lr 0.3
+    (Sec. IV-B).  A bench step is one optimisation iteration: W x T forward steps, W x T
+    recomputed steps and W x T adjoint steps; world-steps count W x T per iteration."""
+    from paper_2609_08800_gb300 import tune
+    from paper_2609_08800_gb300.autograd import CudaEngine, rollout
+    W, T = args.worlds, OPT_T
+    scene = S.robot_box_scene()
+    states = S.robot_box_states(scene, W, seed=rank)
+    knots0 = S.spline_knots(W, n_wheels=4, n_knots=8, seed=rank)
+    cfg = S.SolverConfig(tol=FP32_TOL)
+    eng = CudaEngine(scene, cfg, W, H, slots=CHUNK, dtype="f32")
+    threads = tune.apply(eng.ctx) or 64
+    B = torch.tensor(SP.basis(T, 8, H), dtype=torch.float32, device="cuda")          # [T, K]
+    s0 = torch.tensor(states, dtype=torch.float32, device="cuda")
+    knots = torch.tensor(knots0, dtype=torch.float32, device="cuda").requires_grad_(True)
+    opt = torch.optim.Adam([knots], lr=0.3)
+
+    phase_ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+
+    def iteration(s_init, mark=False):
+        opt.zero_grad(set_to_none=True)
+        controls = torch.einsum("tk,wjk->tjw", B, knots).contiguous()                  # [T, 4, W]
+        if mark:
+            phase_ev[0].record()
+        traj = rollout(s_init, controls, eng, segment=CHUNK)
+        sT = traj[T]
+        loss_w = (sT[0] - 3.0) ** 2 + sT[1] ** 2
+        if mark:
+            phase_ev[1].record()
+        # worlds whose rollout diverged (non-finite state) contribute no gradient
+        torch.where(torch.isfinite(loss_w), loss_w, torch.zeros_like(loss_w)).sum().backward()
+        if mark:
+            phase_ev[2].record()
+        opt.step()
+        return loss_w.detach()
+
+    def loss_stats(lw):
+        fin = torch.isfinite(lw)
+        return {"mean_finite": float(lw[fin].mean()), "non_finite_worlds": int((~fin).sum())}
+
+    first = None
+    for _ in range(args.warmup):
+        lw = iteration(s0)
+        first = lw if first is None else first
+    torch.cuda.synchronize()
+    dist_barrier()
+    clk_path = os.path.join(tempfile.gettempdir(), f"ostrich_opt_clocks_rank{rank}_{os.getpid()}.csv")
+    clk = sample_clocks_start(clk_path)
+    K = max(1, args.steps)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    a.record()
+    losses = []
+    for k in range(K):
+        losses.append(iteration(s0, mark=(k == K - 1)))
+    b.record()
+    torch.cuda.synchronize()
+    dist_barrier()
+    clocks = sample_clocks_stop(clk, clk_path, int(os.environ.get("LOCAL_RANK", "0")))
+    ms = dist_max(a.elapsed_time(b) / K)
+    fwd_ms, bwd_ms = phase_ev[0].elapsed_time(phase_ev[1]), phase_ev[1].elapsed_time(phase_ev[2])
+    # end to end through the public API: each iteration copies its initial states up from
+    # pinned host memory and reads the per-world losses and the updated knots back
+    hs0 = torch.tensor(states, dtype=torch.float32).pin_memory()
+    hloss = torch.empty(W, dtype=torch.float32).pin_memory()
+    hknots = torch.empty(knots.shape, dtype=torch.float32).pin_memory()
+    ds0 = torch.empty_like(s0)
+    n_e2e = min(K, 5)
+    torch.cuda.synchronize()
+    a2, b2 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a2.record()
+    for _ in range(n_e2e):
+        ds0.copy_(hs0, non_blocking=True)
+        lw = iteration(ds0)
+        hloss.copy_(lw, non_blocking=True)
+        hknots.copy_(knots.detach(), non_blocking=True)
+    b2.record()
+    torch.cuda.synchronize()
+    ms_e2e = dist_max(a2.elapsed_time(b2) / n_e2e)
+    eng.close()
+    ws = W * T * world_size
+    return {"value": ws / (ms * 1e-3), "ms_per_iteration": ms, "iterations": K, "warmup": args.warmup,
+            "threads_per_world": threads, "clocks": clocks,
+            "loss_first_warmup": None if first is None else loss_stats(first),
+            "loss_first_timed": loss_stats(losses[0]), "loss_last_timed": loss_stats(losses[-1]),
+            "last_iteration_ms": {"forward_rollout": fwd_ms, "backward_recompute_and_adjoint": bwd_ms},
+            "gpu_launches_per_iteration": 5 * T,
+            "e2e": {"value": ws / (ms_e2e * 1e-3), "unit": UNIT, "ms_per_iteration": ms_e2e, "iterations": n_e2e,
+                    "h2d_bytes_per_step": hs0.numel() * 4,
+                    "d2h_bytes_per_step": (hloss.numel() + hknots.numel()) * 4}}
 
 
 def run_param_grads(ctx, chunk, torch, reps=20):
@@ -459,10 +577,16 @@ def run_terrain(args, torch):
 
 
 def run_serving(args, torch):
-    """Poisson request stream (mean 200 requests/s; 1-512 worlds log-uniform; horizon
-    20-200 steps; box-drop, robot-over-box and mesh-terrain scenes; half forward-only,
-    half forward+adjoint) served by continuous batching, then the same stream by a FIFO
-    queue that serves one request at a time."""
+    """Config 5: a seeded Poisson stream (mean args.serve_rate req/s over args.serve_seconds of
+    arrivals; 1-512 worlds log-uniform; horizon 20-200 steps; box-drop, robot-over-box and
+    mesh-terrain scenes; half forward-only, half forward+adjoint) served by continuous
+    batching, then the same stream by a FIFO queue of batched requests and by the plain
+    form (one request at a time, one world per launch).  The stream offers more
+    world-steps per second than the GPU serves, so every queue grows while arrivals last:
+    each run stops at a wall-clock cutoff and reports its finished requests' p50/p99 and,
+    counting the unfinished ones at their censored latency (cutoff - arrival), lower
+    bounds on the stream's p50/p99.  Continuous batching is also run at
+    args.serve_rate_stable req/s, a load within its capacity."""
     import time as _time
     from paper_2609_08800_gb300 import serve, tune
     cfg = S.SolverConfig(tol=FP32_TOL)
@@ -473,20 +597,39 @@ def run_serving(args, torch):
         p = serve.Pool(kind, kcfg, 8192, h=H, K=CHUNK, t_max=200, hbm_share=0.2)
         tune.apply(p.ctx)
         pools.append(p)
-    out = {"stream": f"Poisson {args.serve_rate:g} req/s over {args.serve_seconds:g} s, seed 0, "
-                     "1-512 worlds (log-uniform), T 20-200, box-drop + robot-over-box + mesh terrain, half with adjoint"}
     warm = serve.poisson_stream(args.serve_rate, 0.05, seed=99, kinds=kinds, max_worlds=64, horizon=(20, 25))
     serve.Server(pools).run(warm)
-    for name, fifo in (("continuous_batching", False), ("fifo_queue", True)):
-        reqs = serve.poisson_stream(args.serve_rate, args.serve_seconds, seed=0, kinds=kinds)
-        srv = serve.Server(pools, fifo=fifo)
+    stated = serve.poisson_stream(args.serve_rate, args.serve_seconds, seed=0, kinds=kinds)
+    offered = sum(r.n * r.T for r in stated) / args.serve_seconds
+    out = {"stream": f"Poisson {args.serve_rate:g} req/s over {args.serve_seconds:g} s, seed 0, 1-512 worlds "
+                     "(log-uniform), T 20-200, box-drop + robot-over-box + mesh terrain, half with adjoint",
+           "requests_offered": len(stated), "offered_world_steps_per_s": offered}
+
+    def timed(server, reqs, cutoff):
+        for r in reqs:
+            r.s0 = r.controls = None
         t0 = _time.perf_counter()
-        done = srv.run(reqs, t0=t0)
+        done = server.run(reqs, t0=t0, deadline=cutoff)
         wall = _time.perf_counter() - t0
-        st = serve.summarize(done, wall)
+        st = serve.summarize(done, wall, getattr(server, "unfinished", ()), cutoff)
         st["wall_s"] = wall
-        st["ticks"] = srv.tick
-        out[name] = st
+        return st
+
+    cb = serve.Server(pools)
+    out["continuous_batching"] = timed(cb, stated, args.serve_seconds + args.serve_drain)
+    out["continuous_batching"]["ticks"] = cb.tick
+    stable = serve.poisson_stream(args.serve_rate_stable, args.serve_seconds_stable, seed=1, kinds=kinds)
+    out["continuous_batching_within_capacity"] = dict(
+        timed(serve.Server(pools), stable, args.serve_seconds_stable + args.serve_drain),
+        stream=f"Poisson {args.serve_rate_stable:g} req/s over {args.serve_seconds_stable:g} s, seed 1, otherwise as above",
+        offered_world_steps_per_s=sum(r.n * r.T for r in stable) / args.serve_seconds_stable)
+    out["fifo_queue"] = timed(serve.Server(pools, fifo=True), serve.poisson_stream(args.serve_rate, args.serve_seconds,
+                                                                                  seed=0, kinds=kinds),
+                              args.serve_baseline_cutoff)
+    out["plain_form"] = timed(serve.PlainServer(pools), serve.poisson_stream(args.serve_rate, args.serve_seconds,
+                                                                            seed=0, kinds=kinds),
+                              args.serve_baseline_cutoff)
+    out["plain_form"]["note"] = "one request at a time, one world per launch (the same kernels with W = 1)"
     for p in pools:
         p.ctx.close()
     return out
@@ -584,13 +727,19 @@ def dist_max(x):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=20, help="timed optimisation iterations (config 3: 20)")
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--worlds", type=int, default=8192)
     ap.add_argument("--terrain-worlds", type=int, default=2048, help="worlds of the mesh-terrain leg (0: skip)")
-    ap.add_argument("--serve-seconds", type=float, default=0.5, help="arrival window of the serving stream (0: skip)")
+    ap.add_argument("--serve-seconds", type=float, default=60.0, help="arrival window of the serving stream (0: skip)")
     ap.add_argument("--serve-rate", type=float, default=200.0)
+    ap.add_argument("--serve-drain", type=float, default=30.0,
+                    help="seconds allowed after the arrival window before a continuous-batching run is cut off")
+    ap.add_argument("--serve-rate-stable", type=float, default=50.0, help="a request rate within capacity")
+    ap.add_argument("--serve-seconds-stable", type=float, default=30.0)
+    ap.add_argument("--serve-baseline-cutoff", type=float, default=20.0,
+                    help="wall-clock cutoff of the FIFO-queue and plain-form runs of the stated stream")
     ap.add_argument("--threads", type=int, default=None, help="threads per world (default: autotuner table)")
     ap.add_argument("--plain-worlds", type=int, default=512)
     ap.add_argument("--cpu-worlds", type=int, default=24)

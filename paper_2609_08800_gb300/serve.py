@@ -398,14 +398,22 @@ class Server:
     def busy(self):
         return bool(self.queue) or any(p.active for p in self.pools.values())
 
-    def run(self, requests, t0=None, max_inflight_ticks=2):
-        """Serve `requests` (sorted by arrival time, seconds from t0) until all are done."""
+    def run(self, requests, t0=None, max_inflight_ticks=2, deadline=None):
+        """Serve `requests` (sorted by arrival time, seconds from t0) until all are done, or
+        until `deadline` seconds after t0: requests not finished by then (queued, or in
+        flight, whose launches are drained but whose results are dropped) are left in
+        `self.unfinished`."""
         pending = sorted(requests, key=lambda r: r.arrival)
         t0 = self.clock() if t0 is None else t0
         i = 0
         history = []
+        self.unfinished = []
         while i < len(pending) or self.busy():
             now = self.clock() - t0
+            if deadline is not None and now >= deadline:
+                self.unfinished = list(self.queue) + [r for p in self.pools.values() for r in p.active]
+                self.unfinished += pending[i:]
+                break
             while i < len(pending) and pending[i].arrival <= now:
                 self.submit(pending[i])
                 i += 1
@@ -431,8 +439,118 @@ class Server:
         return self.done
 
 
-def summarize(done, wall):
+def summarize(done, wall, unfinished=(), cutoff=None):
+    """Latency percentiles of the finished requests and world-steps/s.  With a cutoff, the
+    requests left unfinished get the censored latency cutoff - arrival (a lower bound on
+    their true latency, for those that had arrived), and `censored_p50_s` /
+    `censored_p99_s` over all arrived requests are lower bounds on the stream's p50/p99."""
     lat = np.array([r.latency for r in done]) if done else np.zeros(1)
     ws = sum(r.n * r.T for r in done)
-    return {"requests": len(done), "p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)),
-            "world_steps": ws, "world_steps_per_s": ws / wall if wall > 0 else 0.0}
+    out = {"requests": len(done), "p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)),
+           "world_steps": ws, "world_steps_per_s": ws / wall if wall > 0 else 0.0}
+    if cutoff is not None:
+        arrived = [r for r in unfinished if r.arrival <= cutoff]
+        cens = np.concatenate([lat if done else np.zeros(0), np.array([cutoff - r.arrival for r in arrived])])
+        out.update({"cutoff_s": cutoff, "unfinished": len(arrived), "not_arrived": len(unfinished) - len(arrived),
+                    "censored_p50_s": float(np.percentile(cens, 50)) if cens.size else 0.0,
+                    "censored_p99_s": float(np.percentile(cens, 99)) if cens.size else 0.0})
+    return out
+
+
+class PlainServer:
+    """The plain form of the same service: one request at a time in arrival order, and
+    within a request one world per launch (W = 1 contexts over the pool's columns), the
+    same steps, segment checkpoints and adjoint sweeps as the batched server.  It is the
+    baseline the continuous-batching latency is compared against."""
+
+    def __init__(self, pools, clock=time.perf_counter):
+        self.pools = {p.kind: p for p in pools}
+        self.clock = clock
+        self.done, self.unfinished = [], []
+
+    def _serve(self, r):
+        p = self.pools[r.kind]
+        if r.s0 is None:
+            r.s0, r.controls = request_inputs(r.kind, p.scene, r.n, r.T, r.seed, p.h)
+        dt, K, n = p.ctx.dtype, p.K, r.n
+        # one world per launch: a W = 1 context whose arrays are strided by the request's n
+        ctx = Context(p.scene, p.ctx.cfg, 1, dtype="f64" if dt == torch.float64 else "f32", tape_slots=K, ld=n,
+                      threads=getattr(p.ctx, "threads", None))
+        S0 = torch.from_numpy(np.ascontiguousarray(r.s0)).to(dtype=dt).pin_memory().to("cuda", non_blocking=True)
+        nsv = p.ctx.n_servo
+        CT = (torch.from_numpy(np.ascontiguousarray(r.controls)).to(dtype=dt).pin_memory().to("cuda", non_blocking=True)
+              if nsv else torch.zeros(r.T, 1, n, dtype=dt, device="cuda"))
+        n_seg = (r.T + K - 1) // K
+        ns = S0.shape[0]
+        st = torch.empty(2, ns, n, dtype=dt, device="cuda")
+        st[0] = S0
+        ck = torch.empty(n_seg, ns, n, dtype=dt, device="cuda")
+        g = torch.empty(2, ns, n, dtype=dt, device="cuda")
+        dct = torch.zeros(r.T, max(nsv, 1), n, dtype=dt, device="cuda")
+        fin = torch.empty(ns, n, dtype=dt, device="cuda")
+        for w in range(n):
+            cur = 0
+            for t in range(r.T):
+                if r.adjoint and t % K == 0:
+                    ck[t // K, :, w] = st[cur, :, w]
+                ctx.ostrich_step(_Column(st[cur], w), _Column(CT[t], w), p.h, _Column(st[1 - cur], w))
+                cur = 1 - cur
+            fin[:, w] = st[cur, :, w]
+            if not r.adjoint:
+                continue
+            _, gw = loss_grad(r.kind, st[cur, :, w:w + 1], p.nb)
+            g[0, :, w] = gw[:, 0]
+            gc = 0
+            for k in reversed(range(n_seg)):
+                t0, t1 = k * K, min(r.T, (k + 1) * K)
+                st[0, :, w] = ck[k, :, w]
+                cur = 0
+                for t in range(t0, t1):
+                    ctx.ostrich_step(_Column(st[cur], w), _Column(CT[t], w), p.h, _Column(st[1 - cur], w),
+                                     tape_slot=t - t0)
+                    cur = 1 - cur
+                for t in reversed(range(t0, t1)):
+                    ctx.ostrich_adjoint(t - t0, _Column(g[gc], w), p.h, _Column(g[1 - gc], w),
+                                        _Column(dct[t], w) if nsv else None)
+                    gc = 1 - gc
+            st[0, :, w] = g[gc, :, w]           # dL/ds0 of world w (st[0] is free again)
+        loss, _ = loss_grad(r.kind, fin, p.nb)
+        r.loss, r.final_state = loss.cpu(), fin.cpu()
+        if r.adjoint:
+            r.dstate0 = st[0].cpu()
+            r.dcontrols = dct[:, :nsv].cpu() if nsv else None
+        ctx.close()
+
+    def run(self, requests, t0=None, deadline=None):
+        pending = sorted(requests, key=lambda r: r.arrival)
+        t0 = self.clock() if t0 is None else t0
+        self.done, self.unfinished = [], []
+        for i, r in enumerate(pending):
+            now = self.clock() - t0
+            if deadline is not None and now >= deadline:
+                self.unfinished = pending[i:]
+                break
+            if r.arrival > now:
+                time.sleep(r.arrival - now)
+            self._serve(r)
+            torch.cuda.synchronize()
+            r.done_at = self.clock()
+            r.latency = r.done_at - t0 - r.arrival
+            self.done.append(r)
+        return self.done
+
+
+class _Column:
+    """Column c of a dense [rows, C] device tensor: the address a W = 1 context with
+    ld = C reads and writes (element c, then every C-th element)."""
+    is_cuda = True
+
+    def __init__(self, t, c):
+        assert t.is_contiguous()
+        self._p = t.data_ptr() + c * t.element_size()
+
+    def data_ptr(self):
+        return self._p
+
+    def is_contiguous(self):
+        return True

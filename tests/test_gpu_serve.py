@@ -135,3 +135,35 @@ def test_poisson_stream_completes(pools):
     assert st["requests"] == len(reqs)
     assert 0 < st["p50_s"] <= st["p99_s"] < 60
     assert all(np.isfinite(r.final_state.numpy()).all() for r in done)
+
+
+def test_plain_form_server_matches_batched(pools):
+    """The plain-form baseline (one request at a time, one world per launch) computes the
+    same service: each request's loss, final state, dL/ds0 and dL/dcontrols equal the
+    continuous-batching server's bit for bit (same kernels, same threads per world)."""
+    from paper_2609_08800_gb300 import serve
+    mk = lambda: [_req(serve, 0, "robot", 3, 23, True, 0.0, 5), _req(serve, 1, "box", 4, 21, True, 0.0, 6),  # noqa: E731
+                  _req(serve, 2, "robot", 2, 12, False, 0.0, 7)]
+    a = _serve(serve, pools, mk())
+    plain = serve.PlainServer(pools)
+    done = plain.run(mk())
+    assert len(done) == 3 and not plain.unfinished
+    for r in done:
+        q = a[r.rid]
+        assert torch.equal(r.loss, q.loss) and torch.equal(r.final_state, q.final_state), f"request {r.rid}"
+        if r.adjoint:
+            assert torch.equal(r.dstate0, q.dstate0), f"request {r.rid}: dL/ds0"
+            if q.dcontrols is not None:
+                assert torch.equal(r.dcontrols, q.dcontrols), f"request {r.rid}: dL/dcontrols"
+
+
+def test_server_cutoff_reports_unfinished(pools):
+    """A run cut off by its deadline returns the finished requests and leaves the rest,
+    queued or in flight, in `unfinished` (censored in the summary)."""
+    from paper_2609_08800_gb300 import serve
+    reqs = [_req(serve, k, "robot", 64, 200, True, 0.0, 40 + k) for k in range(6)]
+    srv = serve.Server(pools)
+    done = srv.run(reqs, deadline=0.05)
+    assert len(done) + len(srv.unfinished) == 6 and srv.unfinished
+    st = serve.summarize(done, 0.05, srv.unfinished, 0.05)
+    assert st["unfinished"] == len(srv.unfinished) and st["censored_p99_s"] >= 0.0

@@ -20,3 +20,19 @@ def test_poisson_stream_shape():
     kinds = [r.kind for r in a]
     for k in ("box", "robot", "terrain"):
         assert 0.25 < kinds.count(k) / len(kinds) < 0.42
+
+
+def test_summarize_censors_unfinished_requests():
+    """Requests left unfinished at a cutoff count with latency cutoff - arrival (a lower
+    bound), so the censored percentiles bound the stream's from below."""
+    done = [serve.Request(rid=k, kind="box", n=1, T=20, adjoint=False, arrival=0.1 * k) for k in range(4)]
+    for k, r in enumerate(done):
+        r.latency = 1.0 + k
+    late = [serve.Request(rid=10 + k, kind="box", n=2, T=30, adjoint=True, arrival=1.0 + k) for k in range(3)]
+    st = serve.summarize(done, 10.0, late, cutoff=3.5)
+    assert st["requests"] == 4 and st["world_steps"] == 80
+    assert st["unfinished"] == 3 and st["not_arrived"] == 0
+    cens = np.array([1.0, 2.0, 3.0, 4.0, 2.5, 1.5, 0.5])
+    assert st["censored_p50_s"] == np.percentile(cens, 50) and st["censored_p99_s"] == np.percentile(cens, 99)
+    st2 = serve.summarize(done, 10.0, late, cutoff=1.5)
+    assert st2["unfinished"] == 1 and st2["not_arrived"] == 2

@@ -46,9 +46,9 @@ def lib():
         L.oracle_layout.argtypes = [_dp, _fp, _ip]
         L.oracle_step.argtypes = [_dp, _fp, _dp, _dp, _dp, ctypes.c_double, _dp, _dp, _ip, _up, _dp]
         L.oracle_step_adjoint.argtypes = [_dp, _fp, _dp, _dp, _dp, ctypes.c_double, _dp, ctypes.c_int,
-                                          _dp, _dp, _ip, _up, _dp, _dp, _dp, _dp, _dp, _dp]
+                                          _dp, _dp, _ip, _up, _dp, _dp, _dp, _dp, _dp, _dp, _dp]
         L.oracle_adjoint_at.argtypes = [_dp, _fp, _dp, _dp, _dp, ctypes.c_double, _dp, _dp, _dp, ctypes.c_int,
-                                        _dp, _dp, _dp, _dp, _dp]
+                                        _dp, _dp, _dp, _dp, _dp, _dp]
         L.oracle_fb.argtypes = [ctypes.c_double, ctypes.c_double, ctypes.c_double, _dp]
         L.oracle_friction_W.argtypes = [ctypes.c_double] * 8
         L.oracle_friction_W.restype = ctypes.c_double
@@ -134,14 +134,15 @@ class Oracle:
         dstate = np.zeros(self.n_state); dubar = np.zeros(max(self.n_servo, 1))
         dkp = np.zeros(max(self.n_servo, 1)); dmass = np.zeros(self.scene.n_bodies)
         dinertia = np.zeros(3 * self.scene.n_bodies)
+        dmu = np.zeros(1)
         rc = lib().oracle_step_adjoint(*self._common(), _d(state), _d(ubar), float(h), _d(g), int(mode), _d(out),
                                        _d(imp), ids.ctypes.data_as(_ip), st.ctypes.data_as(_up), _d(dstate),
-                                       _d(dubar), _d(info), _d(dkp), _d(dmass), _d(dinertia))
+                                       _d(dubar), _d(info), _d(dkp), _d(dmass), _d(dinertia), _d(dmu))
         if rc != 0:
             raise RuntimeError("oracle_step_adjoint failed")
         return dict(state=out, impulses=imp, ids=ids[:self.n_slots], status=int(st[0]), iters=int(info[0]),
-                    residual=float(info[1]), dstate=dstate, dubar=dubar[:self.n_servo], dkp=dkp[:self.n_servo],
-                    dmass=dmass, dinertia=dinertia.reshape(-1, 3))
+                    residual=float(info[1]), ret_k=int(info[2]), dstate=dstate, dubar=dubar[:self.n_servo],
+                    dkp=dkp[:self.n_servo], dmass=dmass, dinertia=dinertia.reshape(-1, 3), dmu=float(dmu[0]))
 
     def adjoint_at(self, state, ubar, h, u, lam, dL_dnext, mode=ADJ_PAPER):
         """The adjoint of the step from `state`, taken at the given returned iterate
@@ -157,12 +158,13 @@ class Oracle:
         dstate = np.zeros(self.n_state); dubar = np.zeros(max(self.n_servo, 1))
         dkp = np.zeros(max(self.n_servo, 1)); dmass = np.zeros(self.scene.n_bodies)
         dinertia = np.zeros(3 * self.scene.n_bodies)
+        dmu = np.zeros(1)
         rc = lib().oracle_adjoint_at(*self._common(), _d(state), _d(ubar), float(h), _d(u), _d(lam), _d(g), int(mode),
-                                     _d(dstate), _d(dubar), _d(dkp), _d(dmass), _d(dinertia))
+                                     _d(dstate), _d(dubar), _d(dkp), _d(dmass), _d(dinertia), _d(dmu))
         if rc != 0:
             raise RuntimeError("oracle_adjoint_at failed")
         return dict(dstate=dstate, dubar=dubar[:self.n_servo], dkp=dkp[:self.n_servo], dmass=dmass,
-                    dinertia=dinertia.reshape(-1, 3))
+                    dinertia=dinertia.reshape(-1, 3), dmu=float(dmu[0]))
 
     def contacts(self, state, h):
         state = self._state(state)

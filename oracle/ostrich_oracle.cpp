@@ -636,7 +636,7 @@ inline void fb_grad(double a, double b, double eps, double& fa, double& fb_) {
 // the denominator is guarded (Sec. III-D); W >= 0 is the second safeguard (Sec. III-B).
 // The cone margin is a force; it enters the FB function scaled by h*what (what =
 // J_n M^-1 J_n^T at q-) so that both FB arguments are velocities, as for the normal row.
-template <class S> S friction_W(S vt1, S vt2, S ln, S lf1, S lf2, double mu, double eps, double hw) {
+template <class S, class Mu = double> S friction_W(S vt1, S vt2, S ln, S lf1, S lf2, Mu mu, double eps, double hw) {
   S vt = sqrt(vt1 * vt1 + vt2 * vt2 + S(eps * eps));
   S lfn = sqrt(lf1 * lf1 + lf2 * lf2 + S(eps * eps));
   S lnp = smax(ln, 0.0);
@@ -1124,7 +1124,7 @@ S psi(const Solver& Sv, const std::vector<double>& gq, const std::vector<double>
   return acc;
 }
 
-struct AdjOut { std::vector<double> dq, du, dubar, dkp, dmass, dinertia; };
+struct AdjOut { std::vector<double> dq, du, dubar, dkp, dmass, dinertia; double dmu = 0.0; };
 
 void adjoint(const Solver& Sv, const double* dL_dsp, int mode, AdjOut& out) {
   const OScene& sc = *Sv.W.s;
@@ -1241,6 +1241,33 @@ void adjoint(const Solver& Sv, const double* dL_dsp, int mode, AdjOut& out) {
     const double kp = sc.j[r.joint].kp;
     out.dkp[sc.servo_of_joint[r.joint]] = wr[i] * (-Sv.lam[r.lam] / (kp * kp));
   }
+  // Eq. (17) with xi = mu, the friction coefficient.  mu enters only the friction rows of
+  // Eq. (7), through W (the cone margin h what (mu lambda_n - |lambda_f|) and the
+  // denominator mu lambda_n) and through the positive row weight h what / (h what + W) of
+  // the residual whose Jacobian the exact adjoint takes.  The paper's adjoint holds W at
+  // its value at the returned iterate, so there the gradient is zero.
+  out.dmu = 0.0;
+  if (mode == ADJ_EXACT) {
+    std::vector<double> qpu(7 * nb);
+    kin_update(nb, Sv.qm.data(), Sv.u.data(), h, qpu.data());
+    Geo<double> Gu;
+    geometry(Sv.W, Sv.qm.data(), qpu.data(), Sv.u.data(), Gu);
+    for (size_t i = 0; i < m; ++i) {
+      const Row& r = Sv.W.rows[i];
+      if (r.type != ROW_FRIC || r.sub != 1) continue;
+      const Row& rn = Sv.W.rows[i - 1];
+      const double v[2] = {row_velocity_value(Sv.W, Sv.W.rows[i], Gu, Sv.u.data()),
+                           row_velocity_value(Sv.W, Sv.W.rows[i + 1], Gu, Sv.u.data())};
+      const double hw = h * Sv.W.what[r.slot];
+      Dual Wf = friction_W<Dual, Dual>(Dual(v[0]), Dual(v[1]), Dual(Sv.lam[rn.lam]), Dual(Sv.lam[rn.lam + 1]),
+                                       Dual(Sv.lam[rn.lam + 2]), Dual(sc.mu, 1.0), cfg.eps, hw);
+      for (int k = 0; k < 2; ++k) {
+        Dual rf = Dual(v[k]) + (Wf + Dual(cfg.kappa)) * Dual(Sv.lam[rn.lam + 1 + k]);
+        Dual rw = rf * (Dual(hw) / (Dual(hw) + Wf));
+        out.dmu += wr[i + k] * rw.d;
+      }
+    }
+  }
   for (int b = 0; b < nb; ++b) {
     double acc = 0.0;
     for (int k = 0; k < 3; ++k) acc += wu[6 * b + k] * (Sv.u[6 * b + k] - Sv.um[6 * b + k]);
@@ -1295,11 +1322,12 @@ int oracle_step(const double* scene, const float* heights, const double* cfgv, c
 // Forward step plus adjoint (mode 0: paper, frozen W, forward Schur matrix;
 // mode 1: exact IFT).  dL_dstate_next has the state layout; lambda entries ignored.
 // dL_dkp (n_servo), dL_dmass (nb) and dL_dinertia (3 nb, body-frame principal moments), the
-// servo-gain, body-mass and inertia gradients, may be null.
+// servo-gain, body-mass and inertia gradients, and dL_dmu (1), the friction-coefficient
+// gradient (zero in paper mode), may be null.
 int oracle_step_adjoint(const double* scene, const float* heights, const double* cfgv, const double* state_in,
                         const double* ubar, double h, const double* dL_dnext, int mode, double* state_out,
                         double* impulses, int32_t* ids, uint32_t* status, double* dL_dstate, double* dL_dubar,
-                        double* info, double* dL_dkp, double* dL_dmass, double* dL_dinertia) {
+                        double* info, double* dL_dkp, double* dL_dmass, double* dL_dinertia, double* dL_dmu) {
   OScene s; OCfg cfg;
   if (!parse_scene(scene, heights, s)) return 1;
   parse_cfg(cfgv, cfg);
@@ -1318,6 +1346,7 @@ int oracle_step_adjoint(const double* scene, const float* heights, const double*
   if (dL_dkp) for (int i = 0; i < s.n_servo; ++i) dL_dkp[i] = A.dkp[i];
   if (dL_dmass) for (int b = 0; b < s.nb; ++b) dL_dmass[b] = A.dmass[b];
   if (dL_dinertia) for (int i = 0; i < 3 * s.nb; ++i) dL_dinertia[i] = A.dinertia[i];
+  if (dL_dmu) *dL_dmu = A.dmu;
   return 0;
 }
 
@@ -1329,7 +1358,7 @@ int oracle_step_adjoint(const double* scene, const float* heights, const double*
 int oracle_adjoint_at(const double* scene, const float* heights, const double* cfgv, const double* state_in,
                       const double* ubar, double h, const double* u_ret, const double* lam_ret,
                       const double* dL_dnext, int mode, double* dL_dstate, double* dL_dubar, double* dL_dkp,
-                      double* dL_dmass, double* dL_dinertia) {
+                      double* dL_dmass, double* dL_dinertia, double* dL_dmu) {
   OScene s; OCfg cfg;
   if (!parse_scene(scene, heights, s)) return 1;
   parse_cfg(cfgv, cfg);
@@ -1346,6 +1375,7 @@ int oracle_adjoint_at(const double* scene, const float* heights, const double* c
   if (dL_dkp) for (int i = 0; i < s.n_servo; ++i) dL_dkp[i] = A.dkp[i];
   if (dL_dmass) for (int b = 0; b < s.nb; ++b) dL_dmass[b] = A.dmass[b];
   if (dL_dinertia) for (int i = 0; i < 3 * s.nb; ++i) dL_dinertia[i] = A.dinertia[i];
+  if (dL_dmu) *dL_dmu = A.dmu;
   return 0;
 }
 

@@ -852,3 +852,64 @@ def test_truncated_minus_full_is_the_lever_arm_term(kappa):
     expect[5] = -2.0 * h * lam_tot * hz * w[1]
     assert np.abs(expect[4:6]).min() > 1e-7                 # the case exercises the term
     np.testing.assert_allclose(d, expect, rtol=1e-6, atol=1e-9 * np.abs(expect).max())
+
+
+# --------------------------------------------------------------------------
+# friction-coefficient gradient (Eq. (17) with xi = mu)
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("v", [1.5, 3.0])
+def test_mu_gradient_sliding_box_closed_form(v):
+    """A flat box sliding at rest load loses mu g h of speed per step (Sec. III-B,
+    timestep-consistent sliding force), so dv+/dmu = -g h exactly; the exact adjoint gives
+    it, the paper's frozen W gives 0."""
+    sc = S.box_drop_scene()
+    h = 0.1
+    orc = O.Oracle(sc, _box_cfg())
+    s = S.box_drop_state(sc, 0.0, gap=0.0)[:, 0]
+    for _ in range(4):
+        s = orc.step(s, np.zeros(1), h)["state"]
+    s[7] = v
+    g = np.zeros(sc.n_state)
+    g[7] = 1.0
+    assert orc.step_adjoint(s, np.zeros(1), h, g, mode=O.ADJ_EXACT)["dmu"] == pytest.approx(-9.81 * h, rel=1e-7)
+    assert orc.step_adjoint(s, np.zeros(1), h, g, mode=O.ADJ_PAPER)["dmu"] == 0.0
+
+
+def test_mu_gradient_landing_step_closed_form():
+    """Config 1's landing step: the box lands (u_z+ = -0.5 m/s) while sliding, the friction
+    impulse is mu m (g h - 0.5), so dv_x+/dmu = -(g h - 0.5)."""
+    gold = json.load(open(os.path.join(GOLD, "box_drop_closed_form.json")))
+    sc, st = S.box_drop_inputs(0)
+    g = np.zeros(sc.n_state)
+    g[7] = 1.0
+    r = O.Oracle(sc, _box_cfg()).step_adjoint(st[:, 0], np.zeros(1), gold["h"], g, mode=O.ADJ_EXACT)
+    assert r["dmu"] == pytest.approx(gold["step1_du_x_sliding"] / gold["mu"], rel=1e-7)
+
+
+def test_mu_gradient_matches_central_differences_on_robot():
+    """The exact adjoint's dL/dmu against central differences of the converged step in mu,
+    on a skid-steering robot (left wheels forward, right wheels backward) whose eight rim
+    contacts all slide; the paper-mode gradient is zero there."""
+    import dataclasses
+    sc = S.robot_plane_scene()
+    h = 0.1
+    cfg = S.SolverConfig(budget=60, k_min=4, tol=1e-12, kappa=1e-4)
+    orc = O.Oracle(sc, cfg)
+    ub = np.array([3.0, -3.0, 3.0, -3.0])
+    s = S.robot_box_states(sc, 2, seed=0, phases=False)[:, 1]
+    for _ in range(2):
+        s = orc.step(s, ub, h)["state"]
+    gvec = np.random.default_rng(12).normal(size=sc.n_state)
+    gvec[13 * sc.n_bodies:] = 0.0
+    r = orc.step_adjoint(s, ub, h, gvec, mode=O.ADJ_EXACT)
+    lam = r["state"][sc.contact_lam_index:].reshape(-1, 3)
+    act = r["ids"] >= 0
+    assert act.sum() == 8 and (np.hypot(lam[act, 1], lam[act, 2]) > 0.99 * sc.mu * lam[act, 0]).all()
+    eps = 1e-5
+    lp = gvec @ O.Oracle(dataclasses.replace(sc, mu=sc.mu + eps), cfg).step(s, ub, h)["state"]
+    lm = gvec @ O.Oracle(dataclasses.replace(sc, mu=sc.mu - eps), cfg).step(s, ub, h)["state"]
+    fd = (lp - lm) / (2 * eps)
+    assert abs(fd) > 0.1
+    assert r["dmu"] == pytest.approx(fd, rel=1e-6)
+    assert orc.step_adjoint(s, ub, h, gvec, mode=O.ADJ_PAPER)["dmu"] == 0.0

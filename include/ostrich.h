@@ -51,6 +51,7 @@ enum { OSTRICH_F32 = 0, OSTRICH_F64 = 1 };
 enum { OSTRICH_ENV_PLANE = 0, OSTRICH_ENV_BOX = 1, OSTRICH_ENV_HEIGHTMAP = 2 };
 enum { OSTRICH_SHAPE_NONE = 0, OSTRICH_SHAPE_BOX = 1, OSTRICH_SHAPE_WHEEL = 2 };
 enum { OSTRICH_PULLBACK_FULL = 0, OSTRICH_PULLBACK_TRUNCATED = 1 };
+enum { OSTRICH_ADJ_PAPER = 0, OSTRICH_ADJ_EXACT = 1 };
 
 #define OSTRICH_MAX_BODIES 8
 #define OSTRICH_MAX_JOINTS 8
@@ -134,17 +135,34 @@ ostrich_status ostrich_adjoint(ostrich_ctx* ctx, int tape_slot, const void* dL_d
 
 /* ostrich_adjoint plus the gradients of the physical parameters (Eq. (17) with xi =
  * theta): dL/dk_p of each servo gain (n_servo x ld, servo order as the controls), dL/dm
- * of each body mass (nb x ld) and dL/dI of each body-frame principal moment (3 nb x ld,
- * body-major), element type as the context's, any may be NULL.  They contract the
- * step's adjoint with the explicit partials of the rows holding the parameter: the servo
- * row of Eq. (8) (-lambda_c / k_p^2) and the linear and angular rows of Eq. (10)
- * ((v+ - v-) - h g e_z; r_k (r_k . (w+ - w-)) + h (r_k . w-) (w- x r_k), r_k the k-th
- * column of R(q-)).  The FB scaling what = J M^-1 J^T, which also holds the mass
- * properties, is a step-start constant here, as the frozen W is.  Arguments and errors
- * otherwise as ostrich_adjoint. */
+ * of each body mass (nb x ld), dL/dI of each body-frame principal moment (3 nb x ld,
+ * body-major) and dL/dmu of the friction coefficient (one per world, n_worlds entries),
+ * element type as the context's, any may be NULL.  They contract the step's adjoint
+ * with the explicit partials of the rows holding the parameter: the servo row of Eq. (8)
+ * (-lambda_c / k_p^2), the linear and angular rows of Eq. (10) ((v+ - v-) - h g e_z;
+ * r_k (r_k . (w+ - w-)) + h (r_k . w-) (w- x r_k), r_k the k-th column of R(q-)) and the
+ * friction rows of Eq. (7) through W (exact mode; the paper's frozen W holds mu, so its
+ * mu gradient is 0).  The FB scaling what = J M^-1 J^T, which also holds the mass
+ * properties, is a step-start constant here.  Arguments and errors otherwise as
+ * ostrich_adjoint. */
 ostrich_status ostrich_adjoint_params(ostrich_ctx* ctx, int tape_slot, const void* dL_dstate_next, double h,
                                       void* dL_dstate, void* dL_dcontrols, void* dL_dkp, void* dL_dmass,
-                                      void* dL_dinertia, void* stream);
+                                      void* dL_dinertia, void* dL_dmu, void* stream);
+
+/* Adjoint mode of the context's ostrich_adjoint / _params / _list calls (Sec. III-D):
+ * OSTRICH_ADJ_PAPER (default) solves Eqs. (18)-(19) with the forward Schur factor at the
+ * returned iterate, W and the FB scalings frozen as the paper prescribes; OSTRICH_ADJ_EXACT
+ * solves the implicit-function theorem's transposed system with the full Jacobian of the
+ * residual in (u+, lambda+) -- W's dependence on the slip velocities and on lambda_n
+ * (Eqs. (6)-(7)), the velocity dependence of the friction and servo rows' Jacobians, and
+ * the geometric stiffness d(J^T lambda)/du of Eq. (10) -- by GMRES (restart 20, at most 60
+ * iterations) in the world's shared memory, right-preconditioned by the paper's matrix
+ * through the taped factor; its q- pull-back is always the full one.  krylov_iters: a
+ * device array of n_worlds int32 (or NULL) that receives, per world, the GMRES iterations
+ * of the exact mode, with bit 16 set when the relative residual did not reach 1e-6
+ * (FP32) / 1e-13 (FP64).  EINVAL for an unknown mode or when the exact mode's working
+ * set (about twice the paper mode's) exceeds the shared memory of one CTA. */
+ostrich_status ostrich_set_adjoint_mode(ostrich_ctx* ctx, int mode, int32_t* krylov_iters);
 
 /* Step of a selected subset of worlds (Sec. III-C, per world as ostrich_step): CTA b
  * steps world worlds[b] and, when tape_slots is not NULL and tape_slots[b] >= 0,

@@ -14,6 +14,7 @@
 namespace ost {
 template <class Real> cudaError_t launch_step(const DevScene&, const StepArgs&, int, cudaStream_t);
 template <class Real> cudaError_t launch_adjoint(const DevScene&, const AdjArgs&, int, cudaStream_t);
+template <class Real> size_t adj_smem_bytes(const DevScene&, int);
 }  // namespace ost
 
 struct ostrich_ctx {
@@ -26,6 +27,8 @@ struct ostrich_ctx {
   std::vector<double> slot_h;
   double* trace = nullptr;
   int schedule = 0;
+  int adj_mode = 0;                // 0: paper (frozen W), 1: exact IFT
+  int32_t* krylov = nullptr;       // exact mode: per-world GMRES iterations (caller's device array) or null
   int32_t* d_sched = nullptr;      // persistent schedule: [queue, cost[n_worlds], order[n_worlds]]
   char err[512] = {0};
   // device memory is released with the context, on every path out of ostrich_create too
@@ -187,6 +190,7 @@ ostrich_status ostrich_adjoint_list(ostrich_ctx* c, const void* dL_dnext, double
   a.tape = c->tape; a.dL_dnext = dL_dnext; a.dL_dstate = dL_dstate; a.dL_dcontrols = dL_dcontrols;
   a.ld = c->ld; a.n_worlds = c->n_worlds; a.world0 = 0; a.h = h;
   a.list = worlds; a.list_slot = tape_slots; a.n_list = n_list; a.tape_slots = c->tape_slots;
+  a.mode = c->adj_mode; a.krylov = c->krylov;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   cudaError_t e = c->dtype == OSTRICH_F64 ? ost::launch_adjoint<double>(c->sc, a, c->threads, st)
                                           : ost::launch_adjoint<float>(c->sc, a, c->threads, st);
@@ -194,14 +198,26 @@ ostrich_status ostrich_adjoint_list(ostrich_ctx* c, const void* dL_dnext, double
   return OSTRICH_OK;
 }
 
+ostrich_status ostrich_set_adjoint_mode(ostrich_ctx* c, int mode, int32_t* krylov_iters) {
+  if (!c) return OSTRICH_EINVAL;
+  if (mode != OSTRICH_ADJ_PAPER && mode != OSTRICH_ADJ_EXACT) return fail(c, OSTRICH_EINVAL, "unknown adjoint mode");
+  const size_t smem = c->dtype == OSTRICH_F64 ? ost::adj_smem_bytes<double>(c->sc, mode)
+                                              : ost::adj_smem_bytes<float>(c->sc, mode);
+  if (smem > ost::SMEM_CTA_MAX) return fail(c, OSTRICH_EINVAL, "the exact adjoint's working set exceeds shared memory");
+  c->adj_mode = mode;
+  c->krylov = krylov_iters;
+  return OSTRICH_OK;
+}
+
 ostrich_status ostrich_adjoint(ostrich_ctx* c, int tape_slot, const void* dL_dnext, double h, void* dL_dstate,
                                void* dL_dcontrols, void* stream) {
-  return ostrich_adjoint_params(c, tape_slot, dL_dnext, h, dL_dstate, dL_dcontrols, nullptr, nullptr, nullptr, stream);
+  return ostrich_adjoint_params(c, tape_slot, dL_dnext, h, dL_dstate, dL_dcontrols, nullptr, nullptr, nullptr, nullptr,
+                                stream);
 }
 
 ostrich_status ostrich_adjoint_params(ostrich_ctx* c, int tape_slot, const void* dL_dnext, double h, void* dL_dstate,
                                       void* dL_dcontrols, void* dL_dkp, void* dL_dmass, void* dL_dinertia,
-                                      void* stream) {
+                                      void* dL_dmu, void* stream) {
   if (!c) return OSTRICH_EINVAL;
   if (tape_slot < 0 || tape_slot >= c->tape_slots) return fail(c, OSTRICH_EINVAL, "tape_slot out of range");
   if (!c->slot_written[tape_slot]) return fail(c, OSTRICH_ETAPE, "tape slot holds no recorded step");
@@ -211,6 +227,7 @@ ostrich_status ostrich_adjoint_params(ostrich_ctx* c, int tape_slot, const void*
   a.tape = slot_ptr(c, tape_slot); a.dL_dnext = dL_dnext; a.dL_dstate = dL_dstate; a.dL_dcontrols = dL_dcontrols;
   a.ld = c->ld; a.n_worlds = c->n_worlds; a.world0 = 0; a.h = h;
   a.dL_dkp = c->sc.n_servo > 0 ? dL_dkp : nullptr; a.dL_dmass = dL_dmass; a.dL_dinertia = dL_dinertia;
+  a.dL_dmu = dL_dmu; a.mode = c->adj_mode; a.krylov = c->krylov;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   cudaError_t e = c->dtype == OSTRICH_F64 ? ost::launch_adjoint<double>(c->sc, a, c->threads, st)
                                           : ost::launch_adjoint<float>(c->sc, a, c->threads, st);

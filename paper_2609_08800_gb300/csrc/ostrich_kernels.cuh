@@ -1209,103 +1209,6 @@ static __global__ void lpt_order_kernel(const int32_t* cost, int n, int32_t* ord
 // ---------------------------------------------------------------------------
 // adjoint kernel
 // ---------------------------------------------------------------------------
-// Scalar Psi_row(q-) of the VJP of Eq. (17) for one constraint row, differentiated along
-// one coordinate (body db, component dc) of q-:  w_row * rlin_row - h lambda_row J_row . w_u.
-template <class Real>
-__device__ Real row_vjp(const DevScene& sc, const WS<Real>& w, int i, int db, int dc, const Real* wl, const Real* wu,
-                        bool trunc, double h) {
-  typedef dual<Real> D;
-  const int type = w.meta[4 * i] & 15, sub = w.meta[4 * i] >> 4;
-  const int b0 = w.meta[4 * i + 1], b1 = w.meta[4 * i + 2];
-  const Real hR = Real(h);
-  // q- (dual) and q+ (dual) of the row's bodies
-  D qm0[7], qp0[7], qm1[7], qp1[7];
-  for (int c = 0; c < 7; ++c) qm0[c] = D(w.qm[7 * b0 + c], (b0 == db && c == dc) ? Real(1) : Real(0));
-  kin_body<D, Real>(qm0, w.uk + 6 * b0, h, qp0);
-  if (b1 >= 0) {
-    for (int c = 0; c < 7; ++c) qm1[c] = D(w.qm[7 * b1 + c], (b1 == db && c == dc) ? Real(1) : Real(0));
-    kin_body<D, Real>(qm1, w.uk + 6 * b1, h, qp1);
-  }
-  vec3<Real> wk0 = v3(w.uk[6 * b0 + 3], w.uk[6 * b0 + 4], w.uk[6 * b0 + 5]);
-  vec3<Real> wu0l = v3(wu[6 * b0], wu[6 * b0 + 1], wu[6 * b0 + 2]), wu0a = v3(wu[6 * b0 + 3], wu[6 * b0 + 4], wu[6 * b0 + 5]);
-  const Real lam = w.lk[i];
-  D out(Real(0));
-  if (type == ROW_NORMAL || type == ROW_FRIC) {
-    const int sl = w.ref[i];
-    const int local = sl - sc.slot_base[b0];
-    vec3<D> p = v3(qp0[0], qp0[1], qp0[2]);
-    if (trunc) {
-      if (type == ROW_FRIC) return Real(0);
-      // material point and frame frozen at the converged state; first-order rigid motion
-      vec3<Real> n = v3(w.sn[3 * sl], w.sn[3 * sl + 1], w.sn[3 * sl + 2]);
-      Real qpv[7];
-      for (int c = 0; c < 7; ++c) qpv[c] = qp0[c].v;
-      vec3<Real> pv = v3(qpv[0], qpv[1], qpv[2]);
-      vec3<Real> xs = slot_point<Real>(sc, b0, local, pv, qpv + 3, n);
-      Real Rs[9];
-      qmat(qpv + 3, Rs);
-      vec3<Real> rho = mat3T<Real>(Rs, xs - pv);
-      vec3<D> x = p + qrot(qp0 + 3, lift<D>(rho));
-      D c = dot3(lift<D>(n), x) - D(w.sd[sl]);
-      return (wl[i] * c / D(hR)).d;
-    }
-    vec3<D> n; D d;
-    Real ns[3] = {w.sn[3 * sl], w.sn[3 * sl + 1], w.sn[3 * sl + 2]};
-    slot_frame2<D, Real>(sc, b0, local, w.sftype[sl], qm0, ns, w.sd[sl], w.sedge + 2 * sl, n, d);
-    vec3<D> x = slot_point<D>(sc, b0, local, p, qp0 + 3, n);
-    vec3<D> lev = x - p;
-    vec3<D> dir = n;
-    if (type == ROW_FRIC) {
-      vec3<D> t1, t2;
-      tangent_basis(n, t1, t2);
-      dir = sub == 1 ? t1 : t2;
-    }
-    vec3<D> ang = map_Et(cross3(lev, dir), wk0, h);
-    vec3<Real> ul = v3(w.uk[6 * b0], w.uk[6 * b0 + 1], w.uk[6 * b0 + 2]);
-    D Jw = dot3(dir, lift<D>(wu0l)) + dot3(ang, lift<D>(wu0a));
-    D rlin;
-    if (type == ROW_NORMAL) rlin = (dot3(n, x) - d) / D(hR);
-    else rlin = dot3(dir, lift<D>(ul)) + dot3(ang, lift<D>(wk0));
-    out = D(wl[i]) * rlin - D(hR * lam) * Jw;
-    return out.d;
-  }
-  // joint and servo rows (two bodies)
-  const int j = w.ref[i];
-  vec3<Real> wk1 = v3(w.uk[6 * b1 + 3], w.uk[6 * b1 + 4], w.uk[6 * b1 + 5]);
-  vec3<Real> wu1l = v3(wu[6 * b1], wu[6 * b1 + 1], wu[6 * b1 + 2]), wu1a = v3(wu[6 * b1 + 3], wu[6 * b1 + 4], wu[6 * b1 + 5]);
-  if (type == ROW_SERVO) {
-    vec3<D> ax = qrot(qp0 + 3, v3(D(sc.axp[j][0]), D(sc.axp[j][1]), D(sc.axp[j][2])));
-    vec3<D> a0 = map_Et(scale(ax, D(Real(-1))), wk0, h), a1 = map_Et(ax, wk1, h);
-    D v = dot3(a0, lift<D>(wk0)) + dot3(a1, lift<D>(wk1));
-    D Jw = dot3(a0, lift<D>(wu0a)) + dot3(a1, lift<D>(wu1a));
-    out = D(wl[i]) * v - D(hR * lam) * Jw;
-    return out.d;
-  }
-  vec3<D> pp = v3(qp0[0], qp0[1], qp0[2]), pc = v3(qp1[0], qp1[1], qp1[2]);
-  vec3<D> rp = qrot(qp0 + 3, v3(D(sc.ap[j][0]), D(sc.ap[j][1]), D(sc.ap[j][2])));
-  vec3<D> rc = qrot(qp1 + 3, v3(D(sc.ac[j][0]), D(sc.ac[j][1]), D(sc.ac[j][2])));
-  vec3<D> lin_p, ang_p, lin_c, ang_c;
-  D c;
-  if (sub < 3) {
-    vec3<D> e = v3(D(Real(sub == 0)), D(Real(sub == 1)), D(Real(sub == 2)));
-    vec3<D> gap = (pp + rp) - (pc + rc);
-    c = sub == 0 ? gap.x : (sub == 1 ? gap.y : gap.z);
-    lin_p = e; ang_p = cross3(rp, e); lin_c = scale(e, D(Real(-1))); ang_c = scale(cross3(rc, e), D(Real(-1)));
-  } else {
-    const double* pb = sub == 3 ? sc.p1[j] : sc.p2[j];
-    vec3<D> bw = qrot(qp0 + 3, v3(D(pb[0]), D(pb[1]), D(pb[2])));
-    vec3<D> aw = qrot(qp1 + 3, v3(D(sc.axc[j][0]), D(sc.axc[j][1]), D(sc.axc[j][2])));
-    vec3<D> ba = cross3(bw, aw);
-    c = dot3(bw, aw);
-    lin_p = v3(D(Real(0)), D(Real(0)), D(Real(0))); lin_c = lin_p;
-    ang_p = ba; ang_c = scale(ba, D(Real(-1)));
-  }
-  ang_p = map_Et(ang_p, wk0, h); ang_c = map_Et(ang_c, wk1, h);
-  D Jw = dot3(lin_p, lift<D>(wu0l)) + dot3(ang_p, lift<D>(wu0a)) + dot3(lin_c, lift<D>(wu1l)) + dot3(ang_c, lift<D>(wu1a));
-  out = D(wl[i]) * c / D(hR) - D(hR * lam) * Jw;
-  return out.d;
-}
-
 // Body part of Psi: g_q . q+(q-) + w_u . (M(q-)(u* - u-) - h f(q-, u-)), along (b, dc).
 template <class Real>
 __device__ Real body_vjp(const DevScene& sc, const WS<Real>& w, int b, int dc, const Real* gq, const Real* wu, double h) {
@@ -1333,13 +1236,21 @@ __device__ Real body_vjp(const DevScene& sc, const WS<Real>& w, int b, int dc, c
   return acc.d;
 }
 
-template <class Real>
+}  // namespace ost
+#include "ostrich_adjoint.cuh"
+namespace ost {
+
+// One world's adjoint (Sec. III-D) in mode MODE (ADJ_PAPER or ADJ_EXACT).
+template <class Real, int MODE>
 __global__ void __launch_bounds__(128, 3) adjoint_kernel(const DevScene scp, const AdjArgs a) {
   extern __shared__ __align__(16) char smem[];
   __shared__ __align__(16) DevScene ssc;
+  __shared__ int bgl[NB_CAP * GROUPS_PER_BODY], bgn[NB_CAP], item0[NB_CAP + 1];
   scene_to_shared(scp, ssc);
   const DevScene& sc = ssc;
   WS<Real> w = ws_carve<Real>(smem, sc);
+  ExWS<Real> ex = {};
+  if (MODE == ADJ_EXACT) ex = ex_carve<Real>(smem + ws_bytes<Real>(sc), sc);
   const int tid = threadIdx.x, nth = blockDim.x;
   const int world = a.list ? a.list[blockIdx.x] : a.world0 + blockIdx.x;
   if (world < 0 || world >= a.n_worlds) return;
@@ -1357,6 +1268,12 @@ __global__ void __launch_bounds__(128, 3) adjoint_kernel(const DevScene scp, con
   for (int i = tid; i < m; i += nth) w.lk[i] = tp[tl.off_lam + w.meta[4 * i + 3]];
   __syncthreads();
   evaluate(sc, w, w.uk, w.lk, h);      // J (with E at u*), poses at q+
+  if (tid == 0) {
+    body_groups(sc, w, bgl, bgn);
+    int acc = 0;
+    for (int b = 0; b < nb; ++b) { item0[b] = acc; acc += 7 * (bgn[b] + 1); }
+    item0[nb] = acc;
+  }
   // factor from the tape
   for (int i = tid; i < sc.n_groups * tri_size(sc.pg); i += nth) w.G[i] = tp[tl.off_G + i];
   for (int i = tid; i < sc.n_groups * sc.cmax * sc.ldg; i += nth) w.H[i] = tp[tl.off_H + i];
@@ -1389,41 +1306,62 @@ __global__ void __launch_bounds__(128, 3) adjoint_kernel(const DevScene scp, con
     for (int c = 0; c < 6; ++c) w.mr[6 * b + c] = mg[c];
   }
   __syncthreads();
-  // Eq. (18): A w_lambda = -h J M^-1 g, with the forward factor (the refinement's
-  // matrix-free product takes delta as the evaluation at the iterate formed it, scal[2])
   Real* wl = w.dl;
-  // the right-hand side is formed with exact products: its rounding would otherwise
-  // reach the null space of J^T, where A's eigenvalue is only kappa
-  for (int i = tid; i < m; i += nth) {
-    const Real* Ji = w.J + 12 * i;
-    int b0 = w.meta[4 * i + 1], b1 = w.meta[4 * i + 2];
-    acc2<Real> jm;
-    for (int k = 0; k < 6; ++k) jm.add_prod(Ji[k], w.mr[6 * b0 + k]);
-    if (b1 >= 0) for (int k = 0; k < 6; ++k) jm.add_prod(Ji[6 + k], w.mr[6 * b1 + k]);
-    w.rhs[i] = -hR * jm.value();
-  }
-  __syncthreads();
-  // refined until a correction no longer changes w_lambda at working precision (at most
-  // refine_adj sweeps)
-  schur_solve(sc, w, w.rhs, wl, w.f, w.lt, h, sc.refine_adj, Real(sizeof(Real) == 4 ? 1.2e-7 : 0.0));
-  // Eq. (19): w_u = -M^-1 (g + J^T w_lambda)
   Real* wu = w.ub;
-  jt_apply_acc(sc, w, wl, w.f);     // f is free now
-  __syncthreads();
-  for (int b = tid; b < nb; b += nth) {
-    Real t[6], o[6];
-    for (int c = 0; c < 6; ++c) t[c] = gu[6 * b + c] + w.f[6 * b + c];
-    minv6(sc, w, b, t, o);
-    for (int c = 0; c < 6; ++c) wu[6 * b + c] = -o[c];
+  if (MODE == ADJ_PAPER) {
+    // Eq. (18): A w_lambda = -h J M^-1 g, with the forward factor (the refinement's
+    // matrix-free product takes delta as the evaluation at the iterate formed it, scal[2]);
+    // the right-hand side is formed with exact products: its rounding would otherwise
+    // reach the null space of J^T, where A's eigenvalue is only kappa
+    for (int i = tid; i < m; i += nth) {
+      const Real* Ji = w.J + 12 * i;
+      int b0 = w.meta[4 * i + 1], b1 = w.meta[4 * i + 2];
+      acc2<Real> jm;
+      for (int k = 0; k < 6; ++k) jm.add_prod(Ji[k], w.mr[6 * b0 + k]);
+      if (b1 >= 0) for (int k = 0; k < 6; ++k) jm.add_prod(Ji[6 + k], w.mr[6 * b1 + k]);
+      w.rhs[i] = -hR * jm.value();
+    }
+    __syncthreads();
+    // refined until a correction no longer changes w_lambda at working precision (at most
+    // refine_adj sweeps)
+    schur_solve(sc, w, w.rhs, wl, w.f, w.lt, h, sc.refine_adj, Real(sizeof(Real) == 4 ? 1.2e-7 : 0.0));
+    // Eq. (19): w_u = -M^-1 (g + J^T w_lambda)
+    jt_apply_acc(sc, w, wl, w.f);     // f is free now
+    __syncthreads();
+    for (int b = tid; b < nb; b += nth) {
+      Real t[6], o[6];
+      for (int c = 0; c < 6; ++c) t[c] = gu[6 * b + c] + w.f[6 * b + c];
+      minv6(sc, w, b, t, o);
+      for (int c = 0; c < 6; ++c) wu[6 * b + c] = -o[c];
+    }
+    __syncthreads();
+  } else {
+    // exact IFT: local Jacobians of every group at the returned iterate, then GMRES on
+    // J_F^T [w_u; w_lambda] = [-g; 0] preconditioned by the paper's matrix
+    exact_slot_terms(sc, w, ex, h);
+    __syncthreads();
+    for (int task = tid; task < 6 * nb; task += nth) exact_task(sc, w, ex, bgl, bgn, task / 6, task % 6, h);
+    for (int i = tid; i < 6 * nb; i += nth) ex.r[i] = -gu[i];
+    for (int i = tid; i < m; i += nth) ex.r[6 * nb + i] = Real(0);
+    __syncthreads();
+    Real msum = Real(0);
+    for (int b = 0; b < nb; ++b) msum += Real(sc.mass[b]);
+    const Real sigma = msum / (Real(nb) * hR);
+    int conv = 0;
+    const int its = exact_gmres(sc, w, ex, h, sigma, Real(sizeof(Real) == 4 ? 1e-6 : 1e-13), &conv);
+    for (int i = tid; i < 6 * nb; i += nth) wu[i] = ex.x[i];
+    for (int i = tid; i < m; i += nth) wl[i] = ex.x[6 * nb + i];
+    if (tid == 0 && a.krylov) a.krylov[world] = its | (conv ? 0 : (1 << 16));
+    __syncthreads();
   }
-  __syncthreads();
   // Eq. (17) with xi = theta, the physical parameters: explicit partials of the rows
   // that hold them, contracted with the adjoint.  Servo gain k_p: the servo row of
   // Eq. (8) holds lambda_c / k_p, so d/dk_p = -lambda_c / k_p^2.  Body mass m_b: the
   // linear rows of Eq. (10), m_b (v - v-) - h m_b g, so d/dm_b = (v - v-) - h g e_z.
   // Principal moment I_k: the angular rows, I_w (w - w-) + h w- x (I_w w-) with
   // I_w = R diag(I) R^T at q-, so d/dI_k = r_k (r_k . (w - w-)) + h (r_k . w-) (w- x r_k),
-  // r_k the k-th column of R(q-).
+  // r_k the k-th column of R(q-).  Friction coefficient mu (exact mode; the paper's
+  // frozen W holds it): the friction rows of Eq. (7) through W.
   if (a.dL_dkp) {
     Real* dkp = reinterpret_cast<Real*>(a.dL_dkp);
     for (int i = mc + 5 * sc.nj + tid; i < m; i += nth) {
@@ -1457,6 +1395,24 @@ __global__ void __launch_bounds__(128, 3) adjoint_kernel(const DevScene scp, con
       }
     }
   }
+  if (a.dL_dmu) {
+    Real part = Real(0);
+    if (MODE == ADJ_EXACT) {
+      typedef dual<Real> D;
+      for (int sl = tid; sl < sc.n_slots; sl += nth) {
+        if (!w.sact[sl]) continue;
+        const int i = w.srow[sl], b = sc.slot_body[sl];
+        CGroup<Real> g;
+        contact_group<Real, Real>(sc, w, sl, b, w.qm + 7 * b, w.uk + 6 * b, h, g);
+        D rf[2];
+        friction_rows<D, Real>(sc, D(g.vel[1]), D(g.vel[2]), D(w.lk[i]), w.lk[i + 1], w.lk[i + 2],
+                               hR * w.swhat[sl], D(Real(sc.mu), Real(1)), rf);
+        part += wl[i + 1] * rf[0].d + wl[i + 2] * rf[1].d;
+      }
+    }
+    const Real tot = block_sum(w, part);
+    if (tid == 0) reinterpret_cast<Real*>(a.dL_dmu)[world] = tot;
+  }
   // dL/du- = -M w_u - h (df/du-)^T w_u ;  dL/dubar = -w_lambda of the servo rows
   Real* dout = reinterpret_cast<Real*>(a.dL_dstate);
   for (int b = tid; b < nb; b += nth) {
@@ -1476,31 +1432,26 @@ __global__ void __launch_bounds__(128, 3) adjoint_kernel(const DevScene scp, con
   Real* dctl = reinterpret_cast<Real*>(a.dL_dcontrols);
   if (dctl)
     for (int i = mc + 5 * sc.nj + tid; i < m; i += nth) dctl[(size_t)(i - mc - 5 * sc.nj) * ld + world] = -wl[i];
-  // dL/dq-: per-row and per-body dual-number derivatives, summed in a fixed order
-  const bool trunc = sc.pullback == 1;
-  Real* item = w.G;     // the factor (G, E, H, S, one carved run) is no longer needed:
-                        // m * 14 row items; nb * 7 body items go to rhs
-  for (int e = tid; e < m * 14; e += nth) {
-    int i = e / 14, r = e % 14, side = r / 7, c = r % 7;
-    int b = side == 0 ? w.meta[4 * i + 1] : w.meta[4 * i + 2];
-    item[e] = b >= 0 ? row_vjp(sc, w, i, b, c, wl, wu, trunc, h) : Real(0);
+  // dL/dq-: one work item per (body b, coordinate c of its q-, group touching b or the
+  // body's own terms), each a dual-number evaluation along that coordinate; the items of a
+  // coordinate are summed in a fixed order
+  const bool trunc = MODE == ADJ_PAPER && sc.pullback == 1;
+  Real* item = w.G;     // the factor (G, E, H, S, one carved run) is no longer needed;
+                        // sum_b 7 (groups_b + 1) <= 14 m_max items
+  const int n_items = item0[nb];
+  for (int e = tid; e < n_items; e += nth) {
+    int b = 0;
+    while (e >= item0[b + 1]) ++b;
+    const int r = e - item0[b], c = r / (bgn[b] + 1), k = r - c * (bgn[b] + 1);
+    item[e] = k == 0 ? body_vjp(sc, w, b, c, gq, wu, h)
+                     : group_vjp_q<Real, MODE>(sc, w, ex, bgl[b * GROUPS_PER_BODY + k - 1], b, c, wl, wu, trunc, h);
   }
-  Real* bitem = w.rhs;  // nb * 7 <= m_max is checked when the context is created
-  for (int e = tid; e < nb * 7; e += nth) bitem[e] = body_vjp(sc, w, e / 7, e % 7, gq, wu, h);
   __syncthreads();
-  const int ssdd = sc.ss > 0 ? sc.ss : 1;
   for (int e = tid; e < nb * 7; e += nth) {
-    int b = e / 7, c = e % 7;
+    const int b = e / 7, c = e % 7;
     acc2<Real> acc;        // the terms cancel strongly: compensated sum
-    acc.add(bitem[e]);
-    int g = w.bgrp[b];
-    if (g >= 0)
-      for (int i = w.g0[g]; i < w.g0[g] + w.gn[g]; ++i) acc.add(item[i * 14 + c]);
-    for (int t = 0; t < w.bsepn[b]; ++t) {
-      int i = w.bsep[b * ssdd + t];
-      int side = w.meta[4 * i + 1] == b ? 0 : 1;
-      acc.add(item[i * 14 + 7 * side + c]);
-    }
+    const int base = item0[b] + c * (bgn[b] + 1);
+    for (int k = 0; k <= bgn[b]; ++k) acc.add(item[base + k]);
     dout[(size_t)(7 * b + c) * ld + world] = acc.value();
   }
 }
@@ -1558,11 +1509,12 @@ cudaError_t launch_step(const DevScene& sc, const StepArgs& a, int threads, cuda
 
 template <class Real>
 cudaError_t launch_adjoint(const DevScene& sc, const AdjArgs& a, int threads, cudaStream_t st) {
-  static int done_dev[64] = {0};
-  static size_t done_size[64] = {0};
-  auto kernel = adjoint_kernel<Real>;
-  size_t smem = ws_bytes<Real>(sc);
-  cudaError_t e = ensure_smem(kernel, smem, done_dev, done_size);
+  static int done_dev[2][64] = {{0}};
+  static size_t done_size[2][64] = {{0}};
+  const int mode = a.mode == ADJ_EXACT ? ADJ_EXACT : ADJ_PAPER;
+  auto kernel = mode == ADJ_EXACT ? adjoint_kernel<Real, ADJ_EXACT> : adjoint_kernel<Real, ADJ_PAPER>;
+  const size_t smem = adj_smem_bytes<Real>(sc, mode);
+  cudaError_t e = ensure_smem(kernel, smem, done_dev[mode], done_size[mode]);
   if (e != cudaSuccess) return e;
   int n = a.list ? a.n_list : a.n_worlds - a.world0;
   if (n <= 0) return cudaSuccess;
@@ -1584,5 +1536,6 @@ template cudaError_t launch_step<OST_REAL>(const DevScene&, const StepArgs&, int
 template cudaError_t launch_adjoint<OST_REAL>(const DevScene&, const AdjArgs&, int, cudaStream_t);
 template size_t ws_bytes<OST_REAL>(const DevScene&);
 template size_t ws_used<OST_REAL>(const DevScene&);
+template size_t adj_smem_bytes<OST_REAL>(const DevScene&, int);
 
 }  // namespace ost

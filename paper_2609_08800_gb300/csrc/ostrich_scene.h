@@ -116,6 +116,9 @@ struct AdjArgs {
   // optional physical-parameter gradients: dL/dk_p per servo (n_servo x ld), dL/dm per
   // body (nb x ld), dL/dI per body-frame principal moment (3 nb x ld), or null
   void* dL_dkp = nullptr; void* dL_dmass = nullptr; void* dL_dinertia = nullptr;
+  void* dL_dmu = nullptr;       // optional: dL/dmu per world (n_worlds entries)
+  int mode = 0;                 // 0: the paper's adjoint (frozen W), 1: exact IFT
+  int32_t* krylov = nullptr;    // optional (exact mode): per world GMRES iterations | 1 << 16 if not converged
 };
 
 // Tape record of one world for one step: inputs, returned iterate and the Schur factor

@@ -19,6 +19,7 @@ LIB_PATH = os.path.join(HERE, "libostrich.so")
 
 OSTRICH_OK, OSTRICH_EINVAL, OSTRICH_ENOMEM, OSTRICH_ECUDA, OSTRICH_ETAPE = 0, 1, 2, 3, 4
 OSTRICH_F32, OSTRICH_F64 = 0, 1
+ADJ_PAPER, ADJ_EXACT = 0, 1
 MAX_BODIES = 8
 MAX_JOINTS = 8
 
@@ -69,7 +70,9 @@ def lib():
         L.ostrich_set_schedule.argtypes = [_vp, ctypes.c_int]
         L.ostrich_step.argtypes = [_vp, _vp, _vp, ctypes.c_double, _vp, _vp, _vp, _vp, _vp, ctypes.c_int, _vp]
         L.ostrich_adjoint.argtypes = [_vp, ctypes.c_int, _vp, ctypes.c_double, _vp, _vp, _vp]
-        L.ostrich_adjoint_params.argtypes = [_vp, ctypes.c_int, _vp, ctypes.c_double, _vp, _vp, _vp, _vp, _vp, _vp]
+        L.ostrich_adjoint_params.argtypes = [_vp, ctypes.c_int, _vp, ctypes.c_double, _vp, _vp, _vp, _vp, _vp, _vp, _vp]
+        L.ostrich_set_adjoint_mode.argtypes = [_vp, ctypes.c_int, _vp]
+        L.ostrich_set_adjoint_mode.restype = ctypes.c_int
         L.ostrich_step_list.argtypes = [_vp, _vp, _vp, ctypes.c_double, _vp, _vp, _vp, _vp, _vp, _vp, _vp,
                                         ctypes.c_int, _vp]
         L.ostrich_adjoint_list.argtypes = [_vp, _vp, ctypes.c_double, _vp, _vp, _vp, _vp, ctypes.c_int, _vp]
@@ -239,11 +242,17 @@ class Context:
                                           _ptr(dL_dcontrols), _stream(stream)), "ostrich_adjoint")
 
     def ostrich_adjoint_params(self, tape_slot, dL_dnext, h, dL_dstate, dL_dcontrols=None, dL_dkp=None,
-                               dL_dmass=None, dL_dinertia=None, stream=None):
+                               dL_dmass=None, dL_dinertia=None, dL_dmu=None, stream=None):
         self._check(lib().ostrich_adjoint_params(self._h, int(tape_slot), _ptr(dL_dnext), float(h), _ptr(dL_dstate),
                                                  _ptr(dL_dcontrols), _ptr(dL_dkp), _ptr(dL_dmass), _ptr(dL_dinertia),
-                                                 _stream(stream)),
+                                                 _ptr(dL_dmu), _stream(stream)),
                     "ostrich_adjoint_params")
+
+    def set_adjoint_mode(self, mode, krylov_iters=None):
+        """ADJ_PAPER (the paper's frozen-W adjoint, default) or ADJ_EXACT (the exact IFT by
+        GMRES on the taped factor); krylov_iters: optional int32 device tensor [n_worlds]."""
+        self._check(lib().ostrich_set_adjoint_mode(self._h, int(mode), _ptr(krylov_iters)), "ostrich_set_adjoint_mode")
+        self.adj_mode = int(mode)
 
     def ostrich_step_list(self, state_in, controls, h, state_out, worlds, tape_slots=None, impulses=None, ids=None,
                           status=None, iters=None, stream=None):
@@ -293,9 +302,10 @@ class Context:
         self.ostrich_adjoint(tape_slot, dL_dnext, h, ds, du, stream)
         return ds, du[:self.n_servo]
 
-    def adjoint_params(self, tape_slot, dL_dnext, h, stream=None):
+    def adjoint_params(self, tape_slot, dL_dnext, h, stream=None, with_mu=False):
         """The adjoint plus the physical-parameter gradients: (dL/dstate, dL/dcontrols,
-        dL/dk_p [n_servo, ld], dL/dm [nb, ld], dL/dI [nb, 3, ld] of the principal moments)."""
+        dL/dk_p [n_servo, ld], dL/dm [nb, ld], dL/dI [nb, 3, ld] of the principal moments),
+        and dL/dmu [n_worlds] last when with_mu."""
         import torch
         dev = dL_dnext.device
         ds = torch.empty(self.n_state, self.ld, dtype=self.dtype, device=dev)
@@ -303,8 +313,10 @@ class Context:
         dkp = torch.empty(max(self.n_servo, 1), self.ld, dtype=self.dtype, device=dev)
         dm = torch.empty(self.nb, self.ld, dtype=self.dtype, device=dev)
         di = torch.empty(self.nb, 3, self.ld, dtype=self.dtype, device=dev)
-        self.ostrich_adjoint_params(tape_slot, dL_dnext, h, ds, du, dkp, dm, di, stream)
-        return ds, du[:self.n_servo], dkp[:self.n_servo], dm, di
+        dmu = torch.empty(self.n_worlds, dtype=self.dtype, device=dev) if with_mu else None
+        self.ostrich_adjoint_params(tape_slot, dL_dnext, h, ds, du, dkp, dm, di, dmu, stream)
+        out = (ds, du[:self.n_servo], dkp[:self.n_servo], dm, di)
+        return out + (dmu,) if with_mu else out
 
     def close(self):
         if getattr(self, "_h", None):

@@ -58,7 +58,8 @@ def test_create_rejects_negative_budget(lib):
 
 def test_calls_on_a_null_context_return_einval(lib):
     assert lib.ostrich_adjoint(None, 0, None, 0.1, None, None, None) == OSTRICH_EINVAL
-    assert lib.ostrich_adjoint_params(None, 0, None, 0.1, None, None, None, None, None, None) == OSTRICH_EINVAL
+    assert lib.ostrich_adjoint_params(None, 0, None, 0.1, None, None, None, None, None, None, None) == OSTRICH_EINVAL
+    assert lib.ostrich_set_adjoint_mode(None, 1, None) == OSTRICH_EINVAL
     assert lib.ostrich_step(None, None, None, 0.1, None, None, None, None, None, -1, None) == OSTRICH_EINVAL
     assert lib.ostrich_tape_clear(None) == OSTRICH_EINVAL
 

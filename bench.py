@@ -301,7 +301,7 @@ def run_ours(args, rank, world_size, local_rank):
     if clocks:
         out["chunk"]["clocks"] = clocks
     if rank == 0 and not args.skip_extras:
-        out["param_grads"] = run_param_grads(ctx, chunk, torch)
+        out["adjoint_modes"] = run_param_grads(ctx, chunk, torch)
         out["chunk"]["e2e"] = run_e2e(args, ctx, chunk, states, controls, g, torch)
         out["plain_form"] = run_plain(args, scene, cfg, states, controls, g, torch)
         out["cpu_baseline"] = run_cpu_baseline(args)
@@ -351,6 +351,9 @@ def run_optimisation(args, torch, rank, world_size):
         torch.where(torch.isfinite(loss_w), loss_w, torch.zeros_like(loss_w)).sum().backward()
         if mark:
             phase_ev[2].record()
+        # a world whose rollout diverged keeps its knots (its adjoint ran through
+        # non-finite states)
+        torch.nan_to_num_(knots.grad, nan=0.0, posinf=0.0, neginf=0.0)
         opt.step()
         return loss_w.detach()
 
@@ -410,9 +413,12 @@ def run_optimisation(args, torch, rank, world_size):
                     "d2h_bytes_per_step": (hloss.numel() + hknots.numel()) * 4}}
 
 
-def run_param_grads(ctx, chunk, torch, reps=20):
-    """The adjoint launch of one recorded step with and without the physical-parameter
-    gradients (servo gains, body masses, inertias; Eq. (17) with xi = theta), CUDA events."""
+def run_param_grads(ctx, chunk, torch, reps=5):
+    """The adjoint launches of the chunk's ten recorded steps (slots 0-9, 8192 worlds) in
+    the paper's mode, in the paper's mode with the physical-parameter gradients (servo
+    gains, body masses, inertias, mu; Eq. (17) with xi = theta) and in the exact IFT mode,
+    timed with CUDA events; the exact mode's GMRES iterations per world."""
+    from paper_2609_08800_gb300.ostrich import ADJ_EXACT, ADJ_PAPER
     W = ctx.ld
     dev = "cuda"
     ds = torch.empty(ctx.n_state, W, dtype=torch.float32, device=dev)
@@ -420,24 +426,39 @@ def run_param_grads(ctx, chunk, torch, reps=20):
     dkp = torch.empty(ctx.n_servo, W, dtype=torch.float32, device=dev)
     dm = torch.empty(ctx.nb, W, dtype=torch.float32, device=dev)
     di = torch.empty(3 * ctx.nb, W, dtype=torch.float32, device=dev)
+    dmu = torch.empty(W, dtype=torch.float32, device=dev)
+    kry = torch.zeros(CHUNK, W, dtype=torch.int32, device=dev)
 
     def timed(fn):
-        for _ in range(3):
-            fn()
+        for t in range(CHUNK):
+            fn(t)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         torch.cuda.synchronize()
         e0.record()
         for _ in range(reps):
-            fn()
+            for t in range(CHUNK):
+                fn(t)
         e1.record()
         torch.cuda.synchronize()
-        return e0.elapsed_time(e1) / reps
+        return e0.elapsed_time(e1) / (reps * CHUNK)
 
-    plain = timed(lambda: ctx.ostrich_adjoint(0, chunk.g[1], H, ds, du))
-    params = timed(lambda: ctx.ostrich_adjoint_params(0, chunk.g[1], H, ds, du, dkp, dm, di))
-    return {"worlds": W, "adjoint_ms": plain, "adjoint_params_ms": params,
+    plain = timed(lambda t: ctx.ostrich_adjoint(t, chunk.g[t + 1], H, ds, du))
+    params = timed(lambda t: ctx.ostrich_adjoint_params(t, chunk.g[t + 1], H, ds, du, dkp, dm, di, dmu))
+
+    def exact(t):
+        ctx.set_adjoint_mode(ADJ_EXACT, kry[t])
+        ctx.ostrich_adjoint(t, chunk.g[t + 1], H, ds, du)
+
+    ex_ms = timed(exact)
+    ctx.set_adjoint_mode(ADJ_PAPER)
+    k = kry.cpu().numpy()
+    its = k & 0xFFFF
+    return {"worlds": W, "launches": f"the {CHUNK} recorded steps of the chunk, {reps} rounds",
+            "adjoint_ms": plain, "adjoint_params_ms": params, "adjoint_exact_ms": ex_ms,
+            "exact_krylov_iterations": {"mean": float(its.mean()), "median": float(np.median(its)),
+                                        "max": int(its.max()), "not_converged": int(((k >> 16) & 1).sum())},
             "outputs": f"dL/dk_p ({ctx.n_servo} servo gains), dL/dm ({ctx.nb} body masses), "
-                       f"dL/dI ({3 * ctx.nb} principal moments) per world"}
+                       f"dL/dI ({3 * ctx.nb} principal moments), dL/dmu per world"}
 
 
 def run_e2e(args, ctx, chunk, states, controls, g, torch):

@@ -66,7 +66,7 @@ def _d(a):
 
 
 def pack_scene(scene):
-    """Flat double array: header[14], bodies[nb*10], joints[nj*21]; heights (float32) apart."""
+    """Flat double array: header[14], bodies[nb*10], joints[nj*24]; heights (float32) apart."""
     env = scene.env
     hdr = [scene.n_bodies, len(scene.joints), env.kind, scene.mu, scene.gravity, *env.box,
            0 if env.heights is None else env.heights.shape[0], env.spacing, env.origin[0], env.origin[1]]
@@ -75,7 +75,7 @@ def pack_scene(scene):
         vals += [b.mass, *b.inertia, b.shape, *b.half_extents, b.radius, b.half_width]
     for j in scene.joints:
         vals += [j.parent, j.child, *j.anchor_parent, *j.anchor_child, *j.axis_parent, *j.axis_child,
-                 *j.perp_parent[0], *j.perp_parent[1], j.kp]
+                 *j.perp_parent[0], *j.perp_parent[1], j.kp, j.type, j.servo_mode, j.kd]
     p = np.ascontiguousarray(np.array(vals, dtype=np.float64))
     if env.heights is not None:
         hts = np.ascontiguousarray(env.heights.astype(np.float32).reshape(-1))

@@ -51,6 +51,11 @@ inline Dual operator/(Dual a, Dual b) { return Dual(a.v / b.v, (a.d * b.v - a.v 
 inline Dual& operator+=(Dual& a, Dual b) { a = a + b; return a; }
 inline Dual& operator-=(Dual& a, Dual b) { a = a - b; return a; }
 inline Dual sqrt(Dual a) { double s = std::sqrt(a.v); return Dual(s, a.d / (2.0 * s)); }
+inline Dual atan2(Dual y, Dual x) {
+  const double r2 = x.v * x.v + y.v * y.v;
+  return Dual(std::atan2(y.v, x.v), (x.v * y.d - y.v * x.d) / r2);
+}
+using std::atan2;
 inline double val(double x) { return x; }
 inline double val(const Dual& x) { return x.v; }
 using std::sqrt;
@@ -109,7 +114,9 @@ enum { ADJ_PAPER = 0, ADJ_EXACT = 1 };
 const int MAXB = 16, MAXJ = 16;
 
 struct OBody { double m, I[3]; int shape; double half[3]; double radius, hw; };
-struct OJoint { int parent, child; double ap[3], ac[3], axp[3], axc[3], p1[3], p2[3]; double kp; };
+// Joint: revolute (type 0) or prismatic (type 1); a servo row when kp > 0, velocity
+// target (mode 0) or position target (mode 1, damping kd).
+struct OJoint { int parent, child; double ap[3], ac[3], axp[3], axc[3], p1[3], p2[3]; double kp; int type, mode; double kd; };
 
 struct OScene {
   int nb = 0, nj = 0, env = 0;
@@ -129,8 +136,9 @@ struct OScene {
 
 struct OCfg { int budget, kmin, ls, pullback; double tol, delta_rel, kappa, eps, margin; };
 
-// flat scene format: header[14], then nb*10 body values, then nj*21 joint values
-// (parent, child, anchor_p[3], anchor_c[3], axis_p[3], axis_c[3], perp1_p[3], perp2_p[3], kp)
+// flat scene format: header[14], then nb*10 body values, then nj*24 joint values
+// (parent, child, anchor_p[3], anchor_c[3], axis_p[3], axis_c[3], perp1_p[3], perp2_p[3], kp,
+//  type, servo mode, kd)
 bool parse_scene(const double* p, const float* heights, OScene& s) {
   s.nb = (int)p[0]; s.nj = (int)p[1]; s.env = (int)p[2]; s.mu = p[3]; s.g = p[4];
   if (s.nb < 1 || s.nb > MAXB || s.nj < 0 || s.nj > MAXJ) return false;
@@ -142,14 +150,17 @@ bool parse_scene(const double* p, const float* heights, OScene& s) {
     b.m = q[0]; b.I[0] = q[1]; b.I[1] = q[2]; b.I[2] = q[3]; b.shape = (int)q[4];
     b.half[0] = q[5]; b.half[1] = q[6]; b.half[2] = q[7]; b.radius = q[8]; b.hw = q[9];
   }
-  for (int i = 0; i < s.nj; ++i, q += 21) {
+  for (int i = 0; i < s.nj; ++i, q += 24) {
     OJoint& jt = s.j[i];
     jt.parent = (int)q[0]; jt.child = (int)q[1];
     for (int k = 0; k < 3; ++k) {
       jt.ap[k] = q[2 + k]; jt.ac[k] = q[5 + k]; jt.axp[k] = q[8 + k]; jt.axc[k] = q[11 + k];
       jt.p1[k] = q[14 + k]; jt.p2[k] = q[17 + k];
     }
-    jt.kp = q[20];
+    jt.kp = q[20]; jt.type = (int)q[21]; jt.mode = (int)q[22]; jt.kd = q[23];
+    if (jt.type != 0 && jt.type != 1) return false;
+    if (jt.mode != 0 && jt.mode != 1) return false;
+    if (jt.kd < 0.0) return false;
   }
   s.nf = s.env == ENV_PLANE ? 1 : (s.env == ENV_BOX ? 4 : 8);
   // heightmap: at least one 2 x 2 cell block, face ids below 2^20 (contact id field)
@@ -550,6 +561,36 @@ template <class S> V3<S> apply_Et(const V3<S>& a, const V3<S>& wk, double h) {
   return (a + cross(a, wk) * hh) * (S(1.0) / den);
 }
 
+// The two world vectors of an orientation row, parent vector bw and child vector aw, whose
+// dot product the row holds at zero: revolute rows 3, 4 and prismatic rows 2, 3 align the
+// axes (perp1_p / perp2_p against axis_c); prismatic row 4 locks the twist about the axis
+// (perp2_p against the child's perp1, given in the child frame by the same coordinates).
+template <class S>
+void orientation_pair(const OJoint& jt, int sub, const Pose<S>& Pp, const Pose<S>& Pc, V3<S>& bw, V3<S>& aw) {
+  const int k = jt.type == 0 ? sub - 3 : sub - 2;          // 0, 1: alignment rows; 2: twist
+  if (k < 2) {
+    bw = mul(Pp.R, cvt<S>(k == 0 ? jt.p1 : jt.p2));
+    aw = mul(Pc.R, cvt<S>(jt.axc));
+  } else {
+    bw = mul(Pp.R, cvt<S>(jt.p2));
+    aw = mul(Pc.R, cvt<S>(jt.p1));
+  }
+}
+
+// Joint coordinate a position servo tracks (Eq. (8)), at poses Pp, Pc: the revolute angle
+// about the parent axis a from the parent's perp1 to the child's (atan2 of the child's
+// perp1 against perp1_p and a x perp1_p), or the prismatic slide a . d.
+template <class S> S joint_coordinate(const OJoint& jt, const Pose<S>& Pp, const Pose<S>& Pc) {
+  V3<S> a = mul(Pp.R, cvt<S>(jt.axp));
+  if (jt.type == 0) {
+    V3<S> f = mul(Pp.R, cvt<S>(jt.p1));
+    V3<S> e = mul(Pc.R, cvt<S>(jt.p1));
+    return atan2(dot(e, cross(a, f)), dot(e, f));
+  }
+  V3<S> rp = mul(Pp.R, cvt<S>(jt.ap)), rc = mul(Pc.R, cvt<S>(jt.ac));
+  return dot(a, (Pc.p + rc) - (Pp.p + rp));
+}
+
 template <class S> JRow<S> row_jacobian(const World& W, const Row& r, const Geo<S>& G) {
   const OScene& s = *W.s;
   JRow<S> J;
@@ -569,23 +610,44 @@ template <class S> JRow<S> row_jacobian(const World& W, const Row& r, const Geo<
     const OJoint& jt = s.j[r.joint];
     const Pose<S>& Pp = G.P[jt.parent];
     const Pose<S>& Pc = G.P[jt.child];
-    if (r.sub < 3) {
+    V3<S> rp = mul(Pp.R, cvt<S>(jt.ap)), rc = mul(Pc.R, cvt<S>(jt.ac));
+    if (jt.type == 0 && r.sub < 3) {
+      // revolute anchor rows: (p_p + r_p) - (p_c + r_c), component sub
       V3<S> e = mk(S(r.sub == 0 ? 1.0 : 0.0), S(r.sub == 1 ? 1.0 : 0.0), S(r.sub == 2 ? 1.0 : 0.0));
-      V3<S> rp = mul(Pp.R, cvt<S>(jt.ap)), rc = mul(Pc.R, cvt<S>(jt.ac));
       set0(e, cross(rp, e));
       set1(e * S(-1.0), cross(rc, e) * S(-1.0));
+    } else if (jt.type == 1 && r.sub < 2) {
+      // prismatic rows: the child anchor stays on the parent's axis line, b_k . d = 0 with
+      // b_k = R_p perp_k and d = (p_c + r_c) - (p_p + r_p)
+      V3<S> b = mul(Pp.R, cvt<S>(r.sub == 0 ? jt.p1 : jt.p2));
+      V3<S> d = (Pc.p + rc) - (Pp.p + rp);
+      set0(b * S(-1.0), cross(b, d + rp));
+      set1(b, cross(rc, b));
     } else {
-      V3<S> bw = mul(Pp.R, cvt<S>(r.sub == 3 ? jt.p1 : jt.p2));
-      V3<S> aw = mul(Pc.R, cvt<S>(jt.axc));
+      // orientation rows: parent vector . child vector = 0 (axis alignment: perp_k . axis_c;
+      // prismatic twist lock: perp2_p . perp1 of the child)
+      V3<S> bw, aw;
+      orientation_pair(jt, r.sub, Pp, Pc, bw, aw);
       V3<S> ba = cross(bw, aw);
       set0(zero, ba);
       set1(zero, ba * S(-1.0));
     }
   } else if (r.type == ROW_SERVO) {
     const OJoint& jt = s.j[r.joint];
-    V3<S> ax = mul(G.P[jt.parent].R, cvt<S>(jt.axp));
-    set0(zero, ax * S(-1.0));
-    set1(zero, ax);
+    const Pose<S>& Pp = G.P[jt.parent];
+    const Pose<S>& Pc = G.P[jt.child];
+    V3<S> ax = mul(Pp.R, cvt<S>(jt.axp));
+    if (jt.type == 0) {
+      // relative angular velocity about the axle
+      set0(zero, ax * S(-1.0));
+      set1(zero, ax);
+    } else {
+      // slide velocity along the axis: d/dt (a . d)
+      V3<S> rp = mul(Pp.R, cvt<S>(jt.ap)), rc = mul(Pc.R, cvt<S>(jt.ac));
+      V3<S> d = (Pc.p + rc) - (Pp.p + rp);
+      set0(ax * S(-1.0), cross(ax, d + rp));
+      set1(ax, cross(rc, ax));
+    }
   } else {
     V3<S> dir = r.type == ROW_NORMAL ? G.n[r.slot] : (r.sub == 1 ? G.t1[r.slot] : G.t2[r.slot]);
     V3<S> lever = G.x[r.slot] - G.P[r.b0].p;
@@ -601,12 +663,17 @@ template <class S> S row_position_value(const World& W, const Row& r, const Geo<
     const OJoint& jt = s.j[r.joint];
     const Pose<S>& Pp = G.P[jt.parent];
     const Pose<S>& Pc = G.P[jt.child];
-    if (r.sub < 3) {
-      V3<S> c = (Pp.p + mul(Pp.R, cvt<S>(jt.ap))) - (Pc.p + mul(Pc.R, cvt<S>(jt.ac)));
+    V3<S> rp = mul(Pp.R, cvt<S>(jt.ap)), rc = mul(Pc.R, cvt<S>(jt.ac));
+    if (jt.type == 0 && r.sub < 3) {
+      V3<S> c = (Pp.p + rp) - (Pc.p + rc);
       return r.sub == 0 ? c.x : (r.sub == 1 ? c.y : c.z);
     }
-    V3<S> bw = mul(Pp.R, cvt<S>(r.sub == 3 ? jt.p1 : jt.p2));
-    V3<S> aw = mul(Pc.R, cvt<S>(jt.axc));
+    if (jt.type == 1 && r.sub < 2) {
+      V3<S> b = mul(Pp.R, cvt<S>(r.sub == 0 ? jt.p1 : jt.p2));
+      return dot(b, (Pc.p + rc) - (Pp.p + rp));
+    }
+    V3<S> bw, aw;
+    orientation_pair(jt, r.sub, Pp, Pc, bw, aw);
     return dot(bw, aw);
   }
   // normal row
@@ -719,13 +786,26 @@ void evaluate(const World& W, const S* qm, const S* um, const S* ubar, const S* 
       E.r[i] = c / S(h); E.rlin[i] = E.r[i];
       E.C[i] = 0.0; E.rhat[i] = val(E.r[i]);
     } else if (r.type == ROW_SERVO) {
-      // Eq. (8), velocity target: J_c u + lambda_c / k_p - ubar
+      // Eq. (8): J_c u + alpha lambda_c + b_c.  Velocity target: alpha = 1/k_p,
+      // b_c = -ubar.  Position target: alpha = 1/(k_d + h k_p), b_c = the joint error at
+      // the step's start divided by h, (x(q-) - ubar)/h, so J_c u + b_c is the first-order
+      // joint error at q+ over h (the reading of "the joint error divided by h").
       const OJoint& jt = s.j[r.joint];
       S v = row_velocity_value(W, r, G, u);
       int si = s.servo_of_joint[r.joint];
-      E.r[i] = v + lam[r.lam] / S(jt.kp) - ubar[si];
-      E.rlin[i] = v - ubar[si];
-      E.C[i] = 1.0 / jt.kp; E.rhat[i] = val(E.r[i]);
+      double alpha;
+      S bc;
+      if (jt.mode == 0) {
+        alpha = 1.0 / jt.kp;
+        bc = S(0.0) - ubar[si];
+      } else {
+        alpha = 1.0 / (jt.kd + h * jt.kp);
+        Pose<S> Pp = pose_of(qm + 7 * jt.parent), Pc = pose_of(qm + 7 * jt.child);
+        bc = (joint_coordinate(jt, Pp, Pc) - ubar[si]) / S(h);
+      }
+      E.r[i] = v + lam[r.lam] * S(alpha) + bc;
+      E.rlin[i] = v + bc;
+      E.C[i] = alpha; E.rhat[i] = val(E.r[i]);
     } else if (r.type == ROW_NORMAL) {
       // Eq. (4): phi_eps(c_n/h + kappa lambda_n, h what lambda_n); both arguments in m/s
       S c;
@@ -1238,8 +1318,11 @@ void adjoint(const Solver& Sv, const double* dL_dsp, int mode, AdjOut& out) {
   for (size_t i = 0; i < m; ++i) {
     const Row& r = Sv.W.rows[i];
     if (r.type != ROW_SERVO) continue;
-    const double kp = sc.j[r.joint].kp;
-    out.dkp[sc.servo_of_joint[r.joint]] = wr[i] * (-Sv.lam[r.lam] / (kp * kp));
+    // alpha = 1/k_p (velocity target) or 1/(k_d + h k_p) (position target)
+    const OJoint& jt = sc.j[r.joint];
+    const double dalpha = jt.mode == 0 ? -1.0 / (jt.kp * jt.kp)
+                                       : -h / ((jt.kd + h * jt.kp) * (jt.kd + h * jt.kp));
+    out.dkp[sc.servo_of_joint[r.joint]] = wr[i] * Sv.lam[r.lam] * dalpha;
   }
   // Eq. (17) with xi = mu, the friction coefficient.  mu enters only the friction rows of
   // Eq. (7), through W (the cone margin h what (mu lambda_n - |lambda_f|) and the

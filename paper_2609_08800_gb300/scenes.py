@@ -61,12 +61,22 @@ class Body:
     half_width: float = 0.0                 # wheel half width along body y
 
 
+JOINT_REVOLUTE = 0
+JOINT_PRISMATIC = 1
+SERVO_VELOCITY = 0
+SERVO_POSITION = 1
+
+
 @dataclasses.dataclass
 class Joint:
-    """Revolute joint; the rotation axis is ``axis_parent`` in the parent frame
-    and ``axis_child`` in the child frame; ``perp_parent`` are two unit vectors
-    orthogonal to ``axis_parent`` (parent frame) used by the two alignment rows.
-    ``kp`` > 0 adds a velocity servo row on the joint."""
+    """Joint between two bodies.  Revolute: rotation about ``axis_parent`` (parent
+    frame) = ``axis_child`` (child frame) through the anchors.  Prismatic: translation
+    of the child's anchor along ``axis_parent`` with the orientations locked.
+    ``perp_parent`` are two unit vectors orthogonal to ``axis_parent`` (parent frame)
+    used by the alignment rows; the same coordinates name the child's reference
+    direction.  ``kp`` > 0 adds a servo row on the joint coordinate: a target velocity
+    (``servo_mode`` SERVO_VELOCITY, compliance 1/kp) or a target position
+    (SERVO_POSITION, compliance 1/(kd + h kp))."""
     parent: int
     child: int
     anchor_parent: tuple
@@ -75,6 +85,9 @@ class Joint:
     axis_child: tuple = (0.0, 1.0, 0.0)
     perp_parent: tuple = ((1.0, 0.0, 0.0), (0.0, 0.0, 1.0))
     kp: float = 0.0
+    type: int = JOINT_REVOLUTE
+    servo_mode: int = SERVO_VELOCITY
+    kd: float = 0.0
 
 
 @dataclasses.dataclass
@@ -237,6 +250,76 @@ def terrain_scene(mu: float = 1.0, n: int = 256, spacing: float = 0.05, seed: in
     bodies, joints = robot_bodies_joints()
     H, sp, origin = heightmap(n, spacing, seed=seed)
     return Scene("terrain", bodies, joints, Env(ENV_HEIGHTMAP, heights=H, spacing=sp, origin=origin), mu)
+
+
+CART_BASE = (1.0, 0.3, 0.1)      # base box (rail) extents, resting on the plane
+
+
+def rig_scene(mode: int = SERVO_POSITION, kp: float = 50.0, kd: float = 2.0, mu: float = 1.0) -> Scene:
+    """Servo test rig: a 1000 kg base box standing on the plane carries a 2 kg cart on a
+    prismatic joint along x and a 1 kg wheel cylinder on a revolute joint about y through
+    the wheel's centre; both joints have a servo of the given mode.  With the base held by
+    static friction each servo drives a single free coordinate."""
+    bx, by, bz = CART_BASE
+    base = Body(mass=1000.0, inertia=_box_inertia(1000.0, bx, by, bz), shape=SHAPE_BOX,
+                half_extents=(bx / 2, by / 2, bz / 2))
+    cart = Body(mass=2.0, inertia=_box_inertia(2.0, 0.2, 0.2, 0.1), shape=SHAPE_NONE)
+    wheel = Body(mass=1.0, inertia=_cyl_inertia_y(1.0, 0.15, 0.08), shape=SHAPE_NONE)
+    joints = [Joint(parent=0, child=1, anchor_parent=(0.0, 0.0, 0.15), anchor_child=(0.0, 0.0, 0.0),
+                    axis_parent=(1.0, 0.0, 0.0), axis_child=(1.0, 0.0, 0.0),
+                    perp_parent=((0.0, 1.0, 0.0), (0.0, 0.0, 1.0)), kp=kp, type=JOINT_PRISMATIC,
+                    servo_mode=mode, kd=kd),
+              Joint(parent=0, child=2, anchor_parent=(0.3, 0.3, 0.1), anchor_child=(0.0, 0.0, 0.0), kp=kp,
+                    servo_mode=mode, kd=kd)]
+    return Scene("rig", [base, cart, wheel], joints, Env(ENV_PLANE), mu)
+
+
+def rig_state(scene: Scene, slide: float = 0.0, angle: float = 0.0) -> np.ndarray:
+    """The rig at rest: base on the plane, the cart displaced by `slide` along the rail,
+    the wheel turned by `angle` about its axle."""
+    s = np.zeros((scene.n_state, 1))
+    bz = CART_BASE[2]
+    s[0:7, 0] = (0.0, 0.0, bz / 2, 1.0, 0.0, 0.0, 0.0)
+    s[7:14, 0] = (slide, 0.0, bz / 2 + 0.15, 1.0, 0.0, 0.0, 0.0)
+    s[14:21, 0] = (0.3, 0.3, bz / 2 + 0.1, math.cos(angle / 2), 0.0, math.sin(angle / 2), 0.0)
+    return s
+
+
+def cartpole_scene(kp: float = 20.0, mu: float = 1.0) -> Scene:
+    """Cart-pole: a 1000 kg base box standing on the plane is the rail; a 1 kg cart slides
+    on it along x (prismatic joint with a velocity servo, the control) and carries a
+    0.5 m, 0.2 kg pole on a revolute joint about y at the cart's centre (unactuated)."""
+    bx, by, bz = CART_BASE
+    base = Body(mass=1000.0, inertia=_box_inertia(1000.0, bx, by, bz), shape=SHAPE_BOX,
+                half_extents=(bx / 2, by / 2, bz / 2))
+    cart = Body(mass=1.0, inertia=_box_inertia(1.0, 0.2, 0.2, 0.1), shape=SHAPE_NONE)
+    L = 0.5
+    pole = Body(mass=0.2, inertia=_box_inertia(0.2, 0.02, 0.02, L), shape=SHAPE_NONE)
+    joints = [Joint(parent=0, child=1, anchor_parent=(0.0, 0.0, 0.15), anchor_child=(0.0, 0.0, 0.0),
+                    axis_parent=(1.0, 0.0, 0.0), axis_child=(1.0, 0.0, 0.0),
+                    perp_parent=((0.0, 1.0, 0.0), (0.0, 0.0, 1.0)), kp=kp, type=JOINT_PRISMATIC),
+              Joint(parent=1, child=2, anchor_parent=(0.0, 0.0, 0.0), anchor_child=(0.0, 0.0, -L / 2))]
+    return Scene("cartpole", [base, cart, pole], joints, Env(ENV_PLANE), mu)
+
+
+def cartpole_state(scene: Scene, tilt: float = 0.2, cart_v: float = 0.0, pole_w: float = 0.0) -> np.ndarray:
+    """Base on the plane, cart at the rail's centre, the pole tilted by `tilt` about y
+    (through the hinge), with cart velocity `cart_v` and pole angular velocity `pole_w`."""
+    s = np.zeros((scene.n_state, 1))
+    bz = CART_BASE[2]
+    L = 0.5
+    zc = bz / 2 + 0.15
+    s[0:7, 0] = (0.0, 0.0, bz / 2, 1.0, 0.0, 0.0, 0.0)
+    s[7:14, 0] = (0.0, 0.0, zc, 1.0, 0.0, 0.0, 0.0)
+    c = np.array([math.sin(tilt) * L / 2, 0.0, zc + math.cos(tilt) * L / 2])
+    s[14:21, 0] = (*c, math.cos(tilt / 2), 0.0, math.sin(tilt / 2), 0.0)
+    nb = scene.n_bodies
+    s[7 * nb + 6, 0] = cart_v                      # cart v_x
+    # the pole turns about the hinge: v = w x (c - hinge), w = (0, pole_w, 0)
+    s[7 * nb + 12: 7 * nb + 15, 0] = np.cross([0.0, pole_w, 0.0], c - np.array([0.0, 0.0, zc]))
+    s[7 * nb + 12, 0] += cart_v
+    s[7 * nb + 16, 0] = pole_w
+    return s
 
 
 # ---------------------------------------------------------------------------

@@ -7,7 +7,7 @@
  * implicit map s+ = s+(s-, a) defined by the stacked residual r(s+, s-, a) = 0 of
  * Eqs. (9)-(11) (backward-Euler kinematics Eq. (1), implicit dynamics Eq. (2),
  * joint rows Eq. (3), Fischer-Burmeister normal contact Eq. (4), friction Eq. (7),
- * implicit velocity servos Eq. (8)); the adjoint maps dL/ds+ to dL/ds- and dL/da
+ * implicit velocity or position servos Eq. (8)); the adjoint maps dL/ds+ to dL/ds- and dL/da
  * through Eqs. (16)-(19) with the Schur factor of the forward step.
  *
  * Layout.  Every state, control, impulse and gradient array is a device pointer
@@ -15,7 +15,8 @@
  * c of world w sits at ptr[c * ld + w], ld >= n_worlds (ld is fixed at create).
  *   state   = [q: 7 per body (p, quaternion w x y z)] [u: 6 per body (v, w_world)]
  *             [lambda: 5 per joint, 1 per servo, 3 per contact slot]        (n_state)
- *   controls: one target joint velocity per servo (rad/s)                     (n_servo)
+ *   controls: one target per servo: joint rate (rad/s, m/s) or joint position
+ *             (rad, m) by the servo's mode                                   (n_servo)
  *   impulses: h * lambda in the lambda layout, zero on inactive rows          (m_max)
  *   contact ids: per slot (body << 24 | rim_or_corner << 20 | feature), -1 if inactive
  * Element type is float for OSTRICH_F32 contexts and double for OSTRICH_F64.
@@ -65,14 +66,27 @@ typedef struct {
   double radius, half_width;
 } ostrich_body_desc;
 
-/* Revolute joint (Eq. (3), 3 anchor + 2 axis-alignment rows, no compliance); kp > 0
- * adds a velocity servo row (Eq. (8), compliance 1/kp). */
+/* Joint between two bodies (Eq. (3), five rows, no compliance).  type
+ * OSTRICH_JOINT_REVOLUTE: 3 anchor rows + 2 axis-alignment rows (perp1/perp2_parent
+ * against axis_child); OSTRICH_JOINT_PRISMATIC: the child anchor held on the parent's
+ * axis line (2 rows along perp1/perp2_parent), 2 axis-alignment rows and a twist lock
+ * (perp2_parent against the child's perp1, the same coordinates in the child frame).
+ * kp > 0 adds a servo row on the joint coordinate (Eq. (8)): servo_mode
+ * OSTRICH_SERVO_VELOCITY tracks a target rate (compliance 1/kp); OSTRICH_SERVO_POSITION
+ * tracks a target angle / slide (compliance 1/(kd + h kp), bias (x(q-) - target)/h, x the
+ * angle about axis_parent from perp1_parent to the child's perp1, or the slide
+ * axis . (child anchor - parent anchor)).  Zero-initialised fields give a revolute
+ * joint with a velocity servo. */
+enum { OSTRICH_JOINT_REVOLUTE = 0, OSTRICH_JOINT_PRISMATIC = 1 };
+enum { OSTRICH_SERVO_VELOCITY = 0, OSTRICH_SERVO_POSITION = 1 };
 typedef struct {
   int parent, child;
   double anchor_parent[3], anchor_child[3];
   double axis_parent[3], axis_child[3];
   double perp1_parent[3], perp2_parent[3];
   double kp;
+  int type, servo_mode;
+  double kd;
 } ostrich_joint_desc;
 
 /* Scene shared by all worlds of a context.  heights: host pointer to hm_n*hm_n

@@ -90,49 +90,47 @@ __device__ __forceinline__ S friction_rows(const DevScene& sc, S v1, S v2, S ln,
 }
 
 template <class S> struct JGroup {
-  vec3<S> lin_p[5], ang_p[5], lin_c[5], ang_c[5];
+  vec3<S> lin_p[5], ang_p[5], lin_c[5], ang_c[5];   // through E
   S c[5];
-  vec3<S> sa_p, sa_c;   // servo row: angular parts on parent and child
-  S sv;                 // servo row: relative joint velocity
+  vec3<S> sl_p, sa_p, sl_c, sa_c;   // servo row: linear and angular parts (angular through E)
+  S sv;                             // servo row: joint rate J_c u
 };
 
-// Revolute joint j between parent and child at q- and u+ (in S): the five position rows
-// and the servo row, as evaluate() forms them.
+// Joint j between parent and child at q- and u+ (in S): the five position rows and the
+// servo row, as evaluate() forms them (same geometry helpers).
 template <class S>
 __device__ __forceinline__ void joint_group(const DevScene& sc, int j, const S* qmp, const S* up, const S* qmc,
                                             const S* uc, double h, JGroup<S>& o) {
-  S qpp[7], qpc[7];
+  S qpp[7], qpc[7], Rp[9], Rc[9];
   kin_body<S, S>(qmp, up, h, qpp);
   kin_body<S, S>(qmc, uc, h, qpc);
+  qmat(qpp + 3, Rp);
+  qmat(qpc + 3, Rc);
   const vec3<S> pp = v3(qpp[0], qpp[1], qpp[2]), pc = v3(qpc[0], qpc[1], qpc[2]);
-  const vec3<S> rp = qrot(qpp + 3, v3(S(sc.ap[j][0]), S(sc.ap[j][1]), S(sc.ap[j][2])));
-  const vec3<S> rc = qrot(qpc + 3, v3(S(sc.ac[j][0]), S(sc.ac[j][1]), S(sc.ac[j][2])));
   const vec3<S> wp = v3(up[3], up[4], up[5]), wc = v3(uc[3], uc[4], uc[5]);
-  const vec3<S> gap = (pp + rp) - (pc + rc);
-  const vec3<S> aw = qrot(qpc + 3, v3(S(sc.axc[j][0]), S(sc.axc[j][1]), S(sc.axc[j][2])));
-  const S zero = S(0.0);
+  JRows<S> jr;
+  joint_rows_geom<S>(sc, j, pp, Rp, pc, Rc, jr);
   for (int k = 0; k < 5; ++k) {
-    vec3<S> lp, ap_, lc, ac_;
-    if (k < 3) {
-      const vec3<S> e = v3(S(k == 0 ? 1.0 : 0.0), S(k == 1 ? 1.0 : 0.0), S(k == 2 ? 1.0 : 0.0));
-      lp = e; ap_ = cross3(rp, e); lc = scale(e, S(-1.0)); ac_ = scale(cross3(rc, e), S(-1.0));
-      o.c[k] = k == 0 ? gap.x : (k == 1 ? gap.y : gap.z);
-    } else {
-      const double* pb = k == 3 ? sc.p1[j] : sc.p2[j];
-      const vec3<S> bw = qrot(qpp + 3, v3(S(pb[0]), S(pb[1]), S(pb[2])));
-      const vec3<S> ba = cross3(bw, aw);
-      lp = v3(zero, zero, zero); lc = lp;
-      ap_ = ba; ac_ = scale(ba, S(-1.0));
-      o.c[k] = dot3(bw, aw);
-    }
-    o.lin_p[k] = lp; o.lin_c[k] = lc;
-    o.ang_p[k] = map_Et(ap_, wp, h);
-    o.ang_c[k] = map_Et(ac_, wc, h);
+    o.lin_p[k] = jr.lin_p[k]; o.lin_c[k] = jr.lin_c[k]; o.c[k] = jr.c[k];
+    o.ang_p[k] = map_Et(jr.ang_p[k], wp, h);
+    o.ang_c[k] = map_Et(jr.ang_c[k], wc, h);
   }
-  const vec3<S> ax = qrot(qpp + 3, v3(S(sc.axp[j][0]), S(sc.axp[j][1]), S(sc.axp[j][2])));
-  o.sa_p = map_Et(scale(ax, S(-1.0)), wp, h);
-  o.sa_c = map_Et(ax, wc, h);
-  o.sv = dot3(o.sa_p, wp) + dot3(o.sa_c, wc);
+  SRow<S> sr;
+  servo_row_geom<S>(sc, j, pp, Rp, pc, Rc, sr);
+  o.sl_p = sr.lin_p; o.sl_c = sr.lin_c;
+  o.sa_p = map_Et(sr.ang_p, wp, h);
+  o.sa_c = map_Et(sr.ang_c, wc, h);
+  o.sv = dot3(o.sl_p, v3(up[0], up[1], up[2])) + dot3(o.sa_p, wp) + dot3(o.sl_c, v3(uc[0], uc[1], uc[2])) +
+         dot3(o.sa_c, wc);
+}
+
+// The joint coordinate at q- (in S), for a position servo's bias (x(q-) - target)/h.
+template <class S>
+__device__ __forceinline__ S joint_coord_qm(const DevScene& sc, int j, const S* qmp, const S* qmc) {
+  S Rp[9], Rc[9];
+  qmat(qmp + 3, Rp);
+  qmat(qmc + 3, Rc);
+  return joint_coord<S>(sc, j, v3(qmp[0], qmp[1], qmp[2]), Rp, v3(qmc[0], qmc[1], qmc[2]), Rc);
 }
 
 // ---------------------------------------------------------------------------
@@ -278,8 +276,10 @@ __device__ Real group_vjp_q(const DevScene& sc, const WS<Real>& w, const ExWS<Re
   }
   const int is = servo_row(sc, w, j);
   if (is >= 0) {
-    const D Jw = dot3(g.sa_p, wpa) + dot3(g.sa_c, wca);
+    const D Jw = dot3(g.sl_p, wpl) + dot3(g.sa_p, wpa) + dot3(g.sl_c, wcl) + dot3(g.sa_c, wca);
     acc = acc + D(wl[is]) * g.sv - D(hR * w.lk[is]) * Jw;
+    // a position target's bias (x(q-) - target)/h holds q- directly
+    if (sc.smode[j] == SERVO_POSITION) acc = acc + D(wl[is]) * joint_coord_qm<D>(sc, j, qmp, qmc) / D(hR);
   }
   return acc.d;
 }
@@ -347,7 +347,9 @@ __device__ void exact_task(const DevScene& sc, const WS<Real>& w, const ExWS<Rea
       if (is >= 0) {
         ex.G[12 * is + side + c] = g.sv.d;
         const Real s = -hR * w.lk[is];
+        Kp[0] += s * g.sl_p.x.d; Kp[6] += s * g.sl_p.y.d; Kp[12] += s * g.sl_p.z.d;
         Kp[18] += s * g.sa_p.x.d; Kp[24] += s * g.sa_p.y.d; Kp[30] += s * g.sa_p.z.d;
+        Kch[0] += s * g.sl_c.x.d; Kch[6] += s * g.sl_c.y.d; Kch[12] += s * g.sl_c.z.d;
         Kch[18] += s * g.sa_c.x.d; Kch[24] += s * g.sa_c.y.d; Kch[30] += s * g.sa_c.z.d;
       }
     }

@@ -32,6 +32,7 @@ namespace ost {
 template <class Real> struct WS {
   // bodies
   Real *qm, *um, *ubar, *uk, *ut, *ub, *du, *f, *rdyn, *mr, *Iw, *Iwi, *R, *qp;
+  Real *sbc;      // per servo: the bias b_c of Eq. (8) (-target, or (x(q-) - target)/h)
   // rows
   Real *J, *C, *rhat, *r2, *lk, *lt, *lb, *dl, *rhs;
   int16_t *meta;  // 4 per row: type | sub << 4, b0, b1 (or -1), lam index (state lambda block)
@@ -74,6 +75,7 @@ template <class Real> __host__ __device__ WS<Real> ws_carve(char* base, const De
   w.mr = carve<Real>(p, 6 * nb);
   w.Iw = carve<Real>(p, 9 * nb); w.Iwi = carve<Real>(p, 9 * nb); w.R = carve<Real>(p, 9 * nb);
   w.qp = carve<Real>(p, 7 * nb);
+  w.sbc = carve<Real>(p, s.n_servo + 1);
   w.J = carve<Real>(p, 12 * m);
   w.C = carve<Real>(p, m); w.rhat = carve<Real>(p, m); w.r2 = carve<Real>(p, m); w.lk = carve<Real>(p, m);
   w.lt = carve<Real>(p, m); w.lb = carve<Real>(p, m); w.dl = carve<Real>(p, m); w.rhs = carve<Real>(p, m);
@@ -205,6 +207,107 @@ template <class S, class Real> __device__ __forceinline__ void slot_frame2(const
 }
 
 // ---------------------------------------------------------------------------
+// joint geometry in any scalar type S, from body positions and rotation matrices
+// ---------------------------------------------------------------------------
+// The five rows of joint j (Eq. (3)): Jacobian parts before the rotation-rate map E and the
+// constraint values.  Revolute: anchor rows (p_p + r_p) - (p_c + r_c) by component, then the
+// alignment rows perp_k,p . axis_c.  Prismatic: b_k . d (b_k = R_p perp_k, d = (p_c + r_c) -
+// (p_p + r_p)), the alignment rows, and the twist lock perp2_p . perp1_c.
+template <class S> struct JRows {
+  vec3<S> lin_p[5], ang_p[5], lin_c[5], ang_c[5];
+  S c[5];
+};
+
+template <class S>
+__device__ __forceinline__ void joint_rows_geom(const DevScene& sc, int j, vec3<S> pp, const S* Rp, vec3<S> pc,
+                                                const S* Rc, JRows<S>& o) {
+  const vec3<S> rp = mat3<S>(Rp, v3(S(sc.ap[j][0]), S(sc.ap[j][1]), S(sc.ap[j][2])));
+  const vec3<S> rc = mat3<S>(Rc, v3(S(sc.ac[j][0]), S(sc.ac[j][1]), S(sc.ac[j][2])));
+  const vec3<S> z = v3(S(0.0), S(0.0), S(0.0));
+  const bool rev = sc.jtype[j] == JOINT_REVOLUTE;
+  const vec3<S> d = (pc + rc) - (pp + rp);
+  for (int k = 0; k < 5; ++k) {
+    if (rev && k < 3) {
+      const vec3<S> e = v3(S(k == 0 ? 1.0 : 0.0), S(k == 1 ? 1.0 : 0.0), S(k == 2 ? 1.0 : 0.0));
+      o.lin_p[k] = e; o.ang_p[k] = cross3(rp, e);
+      o.lin_c[k] = scale(e, S(-1.0)); o.ang_c[k] = scale(cross3(rc, e), S(-1.0));
+      o.c[k] = k == 0 ? S(0.0) - d.x : (k == 1 ? S(0.0) - d.y : S(0.0) - d.z);
+    } else if (!rev && k < 2) {
+      const double* pk = k == 0 ? sc.p1[j] : sc.p2[j];
+      const vec3<S> b = mat3<S>(Rp, v3(S(pk[0]), S(pk[1]), S(pk[2])));
+      o.lin_p[k] = scale(b, S(-1.0)); o.ang_p[k] = cross3(b, d + rp);
+      o.lin_c[k] = b; o.ang_c[k] = cross3(rc, b);
+      o.c[k] = dot3(b, d);
+    } else {
+      const int q = rev ? k - 3 : k - 2;        // 0, 1: axis alignment; 2: twist lock
+      const double* pb = q == 0 ? sc.p1[j] : sc.p2[j];
+      const double* pa = q < 2 ? sc.axc[j] : sc.p1[j];
+      const vec3<S> bw = mat3<S>(Rp, v3(S(pb[0]), S(pb[1]), S(pb[2])));
+      const vec3<S> aw = mat3<S>(Rc, v3(S(pa[0]), S(pa[1]), S(pa[2])));
+      const vec3<S> ba = cross3(bw, aw);
+      o.lin_p[k] = z; o.lin_c[k] = z;
+      o.ang_p[k] = ba; o.ang_c[k] = scale(ba, S(-1.0));
+      o.c[k] = dot3(bw, aw);
+    }
+  }
+}
+
+// Servo row of joint j (Eq. (8)): Jacobian parts before E of the joint rate, the relative
+// angular velocity about the parent axis (revolute) or the slide rate d/dt (a . d)
+// (prismatic).
+template <class S> struct SRow { vec3<S> lin_p, ang_p, lin_c, ang_c; };
+
+template <class S>
+__device__ __forceinline__ void servo_row_geom(const DevScene& sc, int j, vec3<S> pp, const S* Rp, vec3<S> pc,
+                                               const S* Rc, SRow<S>& o) {
+  const vec3<S> a = mat3<S>(Rp, v3(S(sc.axp[j][0]), S(sc.axp[j][1]), S(sc.axp[j][2])));
+  if (sc.jtype[j] == JOINT_REVOLUTE) {
+    o.lin_p = v3(S(0.0), S(0.0), S(0.0)); o.lin_c = o.lin_p;
+    o.ang_p = scale(a, S(-1.0)); o.ang_c = a;
+  } else {
+    const vec3<S> rp = mat3<S>(Rp, v3(S(sc.ap[j][0]), S(sc.ap[j][1]), S(sc.ap[j][2])));
+    const vec3<S> rc = mat3<S>(Rc, v3(S(sc.ac[j][0]), S(sc.ac[j][1]), S(sc.ac[j][2])));
+    const vec3<S> d = (pc + rc) - (pp + rp);
+    o.lin_p = scale(a, S(-1.0)); o.ang_p = cross3(a, d + rp);
+    o.lin_c = a; o.ang_c = cross3(rc, a);
+  }
+}
+
+// The joint coordinate a position servo tracks: the revolute angle about the parent axis a
+// from perp1_p to the child's perp1 (atan2), or the prismatic slide a . d.
+__device__ __forceinline__ float satan2(float y, float x) { return atan2f(y, x); }
+__device__ __forceinline__ double satan2(double y, double x) { return atan2(y, x); }
+template <class T> __device__ __forceinline__ dual<T> satan2(dual<T> y, dual<T> x) {
+  const T r2 = x.v * x.v + y.v * y.v;
+  return dual<T>(satan2(y.v, x.v), (x.v * y.d - y.v * x.d) / r2);
+}
+
+template <class S>
+__device__ __forceinline__ S joint_coord(const DevScene& sc, int j, vec3<S> pp, const S* Rp, vec3<S> pc, const S* Rc) {
+  const vec3<S> a = mat3<S>(Rp, v3(S(sc.axp[j][0]), S(sc.axp[j][1]), S(sc.axp[j][2])));
+  if (sc.jtype[j] == JOINT_REVOLUTE) {
+    const vec3<S> f = mat3<S>(Rp, v3(S(sc.p1[j][0]), S(sc.p1[j][1]), S(sc.p1[j][2])));
+    const vec3<S> e = mat3<S>(Rc, v3(S(sc.p1[j][0]), S(sc.p1[j][1]), S(sc.p1[j][2])));
+    return satan2(dot3(e, cross3(a, f)), dot3(e, f));
+  }
+  const vec3<S> rp = mat3<S>(Rp, v3(S(sc.ap[j][0]), S(sc.ap[j][1]), S(sc.ap[j][2])));
+  const vec3<S> rc = mat3<S>(Rc, v3(S(sc.ac[j][0]), S(sc.ac[j][1]), S(sc.ac[j][2])));
+  return dot3(a, (pc + rc) - (pp + rp));
+}
+
+// Servo compliance alpha of Eq. (8): 1/kp (velocity target), 1/(kd + h kp) (position).
+__device__ __forceinline__ double servo_alpha(const DevScene& sc, int j, double h) {
+  return sc.smode[j] == SERVO_POSITION ? 1.0 / (sc.kd[j] + h * sc.kp[j]) : 1.0 / sc.kp[j];
+}
+
+// Joint of the k-th servo.
+__device__ __forceinline__ int servo_joint(const DevScene& sc, int k) {
+  int j = 0, cnt = -1;
+  for (j = 0; j < sc.nj; ++j) if (sc.servo_of[j] >= 0 && ++cnt == k) break;
+  return j;
+}
+
+// ---------------------------------------------------------------------------
 // per-world setup: load inputs, contacts, rows, masses, warm start
 // ---------------------------------------------------------------------------
 // element i of an input vector lives at p[i * stride] (stride = ld for the structure-of-
@@ -294,6 +397,18 @@ __device__ void world_setup(const DevScene& sc, WS<Real>& w, Src<Real> qmv, Src<
     w.uk[6 * b + 5] = w.um[6 * b + 5] + Real(h) * dw.z;
   }
   __syncthreads();
+  // servo biases b_c of Eq. (8): -target (velocity target) or (x(q-) - target)/h (position
+  // target, x the joint coordinate at the step's start; w.R holds R(q-) here)
+  for (int k = tid; k < sc.n_servo; k += nth) {
+    const int j = servo_joint(sc, k), bp = sc.jp[j], bc = sc.jc[j];
+    if (sc.smode[j] == SERVO_POSITION) {
+      const Real x = joint_coord<Real>(sc, j, v3(w.qm[7 * bp], w.qm[7 * bp + 1], w.qm[7 * bp + 2]), w.R + 9 * bp,
+                                       v3(w.qm[7 * bc], w.qm[7 * bc + 1], w.qm[7 * bc + 2]), w.R + 9 * bc);
+      w.sbc[k] = (x - w.ubar[k]) / Real(h);
+    } else {
+      w.sbc[k] = -w.ubar[k];
+    }
+  }
   // row compaction (one thread, fixed order): groups of contact rows, then separator
   if (tid == 0) {
     int m = 0;
@@ -471,58 +586,42 @@ __device__ Real evaluate(const DevScene& sc, WS<Real>& w, const Real* u, const R
       Real e1 = l1 / lfn, e2 = l2 / lfn;
       w.srad[3 * sl] = rho * e1 * e1; w.srad[3 * sl + 1] = rho * e1 * e2; w.srad[3 * sl + 2] = rho * e2 * e2;
     } else if (it < sc.n_slots + sc.nj) {
-      int j = it - sc.n_slots;
-      int i0 = mc + 5 * j;
-      int bp = sc.jp[j], bc = sc.jc[j];
-      vec3<Real> pp = v3(w.qp[7 * bp], w.qp[7 * bp + 1], w.qp[7 * bp + 2]);
-      vec3<Real> pc = v3(w.qp[7 * bc], w.qp[7 * bc + 1], w.qp[7 * bc + 2]);
-      vec3<Real> rp = mat3<Real>(w.R + 9 * bp, v3(Real(sc.ap[j][0]), Real(sc.ap[j][1]), Real(sc.ap[j][2])));
-      vec3<Real> rc = mat3<Real>(w.R + 9 * bc, v3(Real(sc.ac[j][0]), Real(sc.ac[j][1]), Real(sc.ac[j][2])));
-      vec3<Real> wp = v3(u[6 * bp + 3], u[6 * bp + 4], u[6 * bp + 5]);
-      vec3<Real> wc = v3(u[6 * bc + 3], u[6 * bc + 4], u[6 * bc + 5]);
-      vec3<Real> gap = (pp + rp) - (pc + rc);
-      Real gv[3] = {gap.x, gap.y, gap.z};
-      vec3<Real> aw = mat3<Real>(w.R + 9 * bc, v3(Real(sc.axc[j][0]), Real(sc.axc[j][1]), Real(sc.axc[j][2])));
+      const int j = it - sc.n_slots;
+      const int i0 = mc + 5 * j;
+      const int bp = sc.jp[j], bc = sc.jc[j];
+      JRows<Real> jr;
+      joint_rows_geom<Real>(sc, j, v3(w.qp[7 * bp], w.qp[7 * bp + 1], w.qp[7 * bp + 2]), w.R + 9 * bp,
+                            v3(w.qp[7 * bc], w.qp[7 * bc + 1], w.qp[7 * bc + 2]), w.R + 9 * bc, jr);
+      const vec3<Real> wp = v3(u[6 * bp + 3], u[6 * bp + 4], u[6 * bp + 5]);
+      const vec3<Real> wc = v3(u[6 * bc + 3], u[6 * bc + 4], u[6 * bc + 5]);
       for (int k = 0; k < 5; ++k) {
-        vec3<Real> lin_p, ang_p, lin_c, ang_c;
-        Real c;
-        if (k < 3) {
-          vec3<Real> e = v3(Real(k == 0), Real(k == 1), Real(k == 2));
-          lin_p = e; ang_p = cross3(rp, e); lin_c = scale(e, Real(-1)); ang_c = scale(cross3(rc, e), Real(-1));
-          c = gv[k];
-        } else {
-          const double* pb = k == 3 ? sc.p1[j] : sc.p2[j];
-          vec3<Real> bw = mat3<Real>(w.R + 9 * bp, v3(Real(pb[0]), Real(pb[1]), Real(pb[2])));
-          vec3<Real> ba = cross3(bw, aw);
-          lin_p = v3(Real(0), Real(0), Real(0)); lin_c = lin_p;
-          ang_p = ba; ang_c = scale(ba, Real(-1));
-          c = dot3(bw, aw);
-        }
-        ang_p = map_Et(ang_p, wp, h); ang_c = map_Et(ang_c, wc, h);
-        int i = i0 + k;
+        const vec3<Real> ap_ = map_Et(jr.ang_p[k], wp, h), ac_ = map_Et(jr.ang_c[k], wc, h);
+        const int i = i0 + k;
         Real* Jr = w.J + 12 * i;
-        Jr[0] = lin_p.x; Jr[1] = lin_p.y; Jr[2] = lin_p.z; Jr[3] = ang_p.x; Jr[4] = ang_p.y; Jr[5] = ang_p.z;
-        Jr[6] = lin_c.x; Jr[7] = lin_c.y; Jr[8] = lin_c.z; Jr[9] = ang_c.x; Jr[10] = ang_c.y; Jr[11] = ang_c.z;
-        w.r2[i] = c / hR; w.rhat[i] = c / hR; w.C[i] = Real(0);
+        Jr[0] = jr.lin_p[k].x; Jr[1] = jr.lin_p[k].y; Jr[2] = jr.lin_p[k].z; Jr[3] = ap_.x; Jr[4] = ap_.y; Jr[5] = ap_.z;
+        Jr[6] = jr.lin_c[k].x; Jr[7] = jr.lin_c[k].y; Jr[8] = jr.lin_c[k].z; Jr[9] = ac_.x; Jr[10] = ac_.y; Jr[11] = ac_.z;
+        w.r2[i] = jr.c[k] / hR; w.rhat[i] = jr.c[k] / hR; w.C[i] = Real(0);
       }
     } else {
-      int k = it - sc.n_slots - sc.nj;
-      // k-th servo: find its joint
-      int j = 0, cnt = -1;
-      for (j = 0; j < sc.nj; ++j) if (sc.servo_of[j] >= 0 && ++cnt == k) break;
-      int i = mc + 5 * sc.nj + k;
-      int bp = sc.jp[j], bc = sc.jc[j];
-      vec3<Real> ax = mat3<Real>(w.R + 9 * bp, v3(Real(sc.axp[j][0]), Real(sc.axp[j][1]), Real(sc.axp[j][2])));
-      vec3<Real> wp = v3(u[6 * bp + 3], u[6 * bp + 4], u[6 * bp + 5]);
-      vec3<Real> wc = v3(u[6 * bc + 3], u[6 * bc + 4], u[6 * bc + 5]);
-      vec3<Real> ap_ = map_Et(scale(ax, Real(-1)), wp, h), ac_ = map_Et(ax, wc, h);
+      // k-th servo, Eq. (8): J_c u + alpha lambda_c + b_c
+      const int k = it - sc.n_slots - sc.nj;
+      const int j = servo_joint(sc, k);
+      const int i = mc + 5 * sc.nj + k;
+      const int bp = sc.jp[j], bc = sc.jc[j];
+      SRow<Real> sr;
+      servo_row_geom<Real>(sc, j, v3(w.qp[7 * bp], w.qp[7 * bp + 1], w.qp[7 * bp + 2]), w.R + 9 * bp,
+                           v3(w.qp[7 * bc], w.qp[7 * bc + 1], w.qp[7 * bc + 2]), w.R + 9 * bc, sr);
+      const vec3<Real> wp = v3(u[6 * bp + 3], u[6 * bp + 4], u[6 * bp + 5]);
+      const vec3<Real> wc = v3(u[6 * bc + 3], u[6 * bc + 4], u[6 * bc + 5]);
+      const vec3<Real> ap_ = map_Et(sr.ang_p, wp, h), ac_ = map_Et(sr.ang_c, wc, h);
       Real* Jr = w.J + 12 * i;
-      Jr[0] = 0; Jr[1] = 0; Jr[2] = 0; Jr[3] = ap_.x; Jr[4] = ap_.y; Jr[5] = ap_.z;
-      Jr[6] = 0; Jr[7] = 0; Jr[8] = 0; Jr[9] = ac_.x; Jr[10] = ac_.y; Jr[11] = ac_.z;
-      Real v = dot3(ap_, wp) + dot3(ac_, wc);
-      Real kp = Real(sc.kp[j]);
-      Real r = v + lam[i] / kp - w.ubar[sc.servo_of[j]];
-      w.r2[i] = r; w.rhat[i] = r; w.C[i] = Real(1) / kp;
+      Jr[0] = sr.lin_p.x; Jr[1] = sr.lin_p.y; Jr[2] = sr.lin_p.z; Jr[3] = ap_.x; Jr[4] = ap_.y; Jr[5] = ap_.z;
+      Jr[6] = sr.lin_c.x; Jr[7] = sr.lin_c.y; Jr[8] = sr.lin_c.z; Jr[9] = ac_.x; Jr[10] = ac_.y; Jr[11] = ac_.z;
+      Real v = Real(0);
+      for (int q = 0; q < 6; ++q) v += Jr[q] * u[6 * bp + q] + Jr[6 + q] * u[6 * bc + q];
+      const Real alpha = Real(servo_alpha(sc, j, h));
+      const Real r = v + alpha * lam[i] + w.sbc[k];
+      w.r2[i] = r; w.rhat[i] = r; w.C[i] = alpha;
     }
   }
   __syncthreads();
@@ -1365,8 +1464,11 @@ __global__ void __launch_bounds__(128, 3) adjoint_kernel(const DevScene scp, con
   if (a.dL_dkp) {
     Real* dkp = reinterpret_cast<Real*>(a.dL_dkp);
     for (int i = mc + 5 * sc.nj + tid; i < m; i += nth) {
-      const Real kp = Real(sc.kp[w.ref[i]]);
-      dkp[(size_t)(i - mc - 5 * sc.nj) * ld + world] = wl[i] * (-w.lk[i] / (kp * kp));
+      // d alpha / d k_p: -1/k_p^2 (velocity target), -h/(k_d + h k_p)^2 (position target)
+      const int j = w.ref[i];
+      const Real al = Real(servo_alpha(sc, j, h));
+      const Real dal = sc.smode[j] == SERVO_POSITION ? -hR * al * al : -al * al;
+      dkp[(size_t)(i - mc - 5 * sc.nj) * ld + world] = wl[i] * w.lk[i] * dal;
     }
   }
   if (a.dL_dmass) {
@@ -1430,8 +1532,9 @@ __global__ void __launch_bounds__(128, 3) adjoint_kernel(const DevScene scp, con
   }
   for (int i = tid; i < sc.m_max; i += nth) dout[(size_t)(13 * nb + i) * ld + world] = Real(0);
   Real* dctl = reinterpret_cast<Real*>(a.dL_dcontrols);
-  if (dctl)
-    for (int i = mc + 5 * sc.nj + tid; i < m; i += nth) dctl[(size_t)(i - mc - 5 * sc.nj) * ld + world] = -wl[i];
+  if (dctl)   // d b_c / d target: -1 (velocity target), -1/h (position target)
+    for (int i = mc + 5 * sc.nj + tid; i < m; i += nth)
+      dctl[(size_t)(i - mc - 5 * sc.nj) * ld + world] = sc.smode[w.ref[i]] == SERVO_POSITION ? -wl[i] / hR : -wl[i];
   // dL/dq-: one work item per (body b, coordinate c of its q-, group touching b or the
   // body's own terms), each a dual-number evaluation along that coordinate; the items of a
   // coordinate are summed in a fixed order

@@ -13,6 +13,8 @@ constexpr int SEP_CAP = 5 * NJ_CAP + NJ_CAP;   // separator rows per world
 enum { SHAPE_NONE = 0, SHAPE_BOX = 1, SHAPE_WHEEL = 2 };
 enum { ENV_PLANE = 0, ENV_BOX = 1, ENV_HEIGHTMAP = 2 };
 enum { ROW_JOINT = 0, ROW_SERVO = 1, ROW_NORMAL = 2, ROW_FRIC = 3 };
+enum { JOINT_REVOLUTE = 0, JOINT_PRISMATIC = 1 };
+enum { SERVO_VELOCITY = 0, SERVO_POSITION = 1 };
 
 // Everything a kernel needs to know about the scene and the solver settings.
 // Passed by value as a kernel parameter.
@@ -29,6 +31,9 @@ struct DevScene {
   // joints
   int jp[NJ_CAP], jc[NJ_CAP], servo_of[NJ_CAP];
   double ap[NJ_CAP][3], ac[NJ_CAP][3], axp[NJ_CAP][3], axc[NJ_CAP][3], p1[NJ_CAP][3], p2[NJ_CAP][3], kp[NJ_CAP];
+  double kd[NJ_CAP];
+  int jtype[NJ_CAP];   // JOINT_REVOLUTE / JOINT_PRISMATIC
+  int smode[NJ_CAP];   // SERVO_VELOCITY / SERVO_POSITION
   // solver settings
   int budget, kmin, ls, pullback;
   double tol, delta_rel, kappa, eps, margin;

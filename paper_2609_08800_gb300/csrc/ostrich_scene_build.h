@@ -61,7 +61,10 @@ inline ostrich_status build_scene(const ostrich_scene_desc* d, const ostrich_sol
       s.axp[j][k] = jd.axis_parent[k]; s.axc[j][k] = jd.axis_child[k];
       s.p1[j][k] = jd.perp1_parent[k]; s.p2[j][k] = jd.perp2_parent[k];
     }
-    s.kp[j] = jd.kp;
+    if (jd.type != JOINT_REVOLUTE && jd.type != JOINT_PRISMATIC) return OSTRICH_EINVAL;
+    if (jd.servo_mode != SERVO_VELOCITY && jd.servo_mode != SERVO_POSITION) return OSTRICH_EINVAL;
+    if (!(jd.kd >= 0)) return OSTRICH_EINVAL;
+    s.kp[j] = jd.kp; s.kd[j] = jd.kd; s.jtype[j] = jd.type; s.smode[j] = jd.servo_mode;
     s.servo_of[j] = jd.kp > 0 ? s.n_servo++ : -1;
   }
   s.m_max = 5 * s.nj + s.n_servo + 3 * s.n_slots;

@@ -34,7 +34,7 @@ class BodyDesc(ctypes.Structure):
 class JointDesc(ctypes.Structure):
     _fields_ = [("parent", ctypes.c_int), ("child", ctypes.c_int), ("anchor_parent", _d3), ("anchor_child", _d3),
                 ("axis_parent", _d3), ("axis_child", _d3), ("perp1_parent", _d3), ("perp2_parent", _d3),
-                ("kp", ctypes.c_double)]
+                ("kp", ctypes.c_double), ("type", ctypes.c_int), ("servo_mode", ctypes.c_int), ("kd", ctypes.c_double)]
 
 
 class SceneDesc(ctypes.Structure):
@@ -130,6 +130,7 @@ def scene_desc(scene: "S.Scene") -> SceneDesc:
         jd.perp1_parent[:] = j.perp_parent[0]
         jd.perp2_parent[:] = j.perp_parent[1]
         jd.kp = j.kp
+        jd.type, jd.servo_mode, jd.kd = j.type, j.servo_mode, j.kd
     return d
 
 

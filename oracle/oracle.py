@@ -54,6 +54,7 @@ def lib():
         L.oracle_friction_W.restype = ctypes.c_double
         L.oracle_rotate.argtypes = [_dp, _dp, _dp]
         L.oracle_lu_solve.argtypes = [ctypes.c_int, _dp, _dp, _dp]
+        L.oracle_pcr.argtypes = [ctypes.c_int, _dp, _dp, ctypes.c_int, _ip, ctypes.c_int, ctypes.c_double, _dp, _ip]
         L.oracle_contacts.argtypes = [_dp, _fp, _dp, _dp, ctypes.c_double, _ip, _ip, _dp]
         L.oracle_rows.argtypes = [_dp, _fp, _dp, _dp, _dp, ctypes.c_double, _dp, _dp, ctypes.c_int,
                                   _ip, _dp, _dp, _dp, _dp, _dp]
@@ -86,7 +87,8 @@ def pack_scene(scene):
 
 def pack_cfg(cfg):
     return np.array([cfg.budget, cfg.k_min, cfg.tol, cfg.delta_rel, cfg.kappa, cfg.eps_fb, cfg.margin,
-                     cfg.line_search, cfg.pullback], dtype=np.float64)
+                     cfg.line_search, cfg.pullback, cfg.linear_solver, cfg.precond, cfg.pcr_iters,
+                     cfg.pcr_iters_adj, cfg.pcr_rtol_adj if cfg.pcr_rtol_adj > 0 else 1e-12], dtype=np.float64)
 
 
 class Oracle:
@@ -213,6 +215,18 @@ def lu_solve(A, b):
     if rc != 0:
         raise np.linalg.LinAlgError("singular")
     return x
+
+
+def pcr(A, b, kind=0, blocks=None, iters=16, rtol=0.0):
+    """Preconditioned conjugate residual on a dense SPD system (kind 0 Jacobi, 1 block
+    Jacobi over the row blocks `blocks`): (x, iterations, converged)."""
+    A = np.ascontiguousarray(A, dtype=np.float64); b = np.ascontiguousarray(b, dtype=np.float64)
+    n = len(b)
+    blk = np.ascontiguousarray(np.zeros(n) if blocks is None else blocks, dtype=np.int32)
+    x = np.zeros(n); conv = np.zeros(1, dtype=np.int32)
+    k = lib().oracle_pcr(n, _d(A), _d(b), int(kind), blk.ctypes.data_as(_ip), int(iters), float(rtol), _d(x),
+                         conv.ctypes.data_as(_ip))
+    return x, int(k), bool(conv[0])
 
 
 def rollout(orc: Oracle, state, controls, h, T):

@@ -11,7 +11,9 @@
 //               admissibility safeguards, implicit velocity servo Eq. (8);
 //   Sec. III-C  stacked residual Eqs. (9)-(11), kinematic substitution, Schur step
 //               Eq. (12) and back-substitution Eq. (13), solved with a dense LU
-//               factorisation (no structure exploited), best-iterate backtracking;
+//               factorisation (no structure exploited) or, as the paper solves it, by
+//               preconditioned conjugate residuals (Jacobi or block-Jacobi
+//               preconditioner), best-iterate backtracking;
 //   Sec. III-D  IFT adjoint Eqs. (14)-(19) reusing the Schur matrix at the returned
 //               iterate; the vector-Jacobian products Eq. (17) (position pull-back
 //               included) are forward-mode dual-number derivatives of one residual
@@ -134,7 +136,16 @@ struct OScene {
   int lam_contact(int s) const { return 5 * nj + n_servo + 3 * s; }
 };
 
-struct OCfg { int budget, kmin, ls, pullback; double tol, delta_rel, kappa, eps, margin; };
+// lin: 0 dense LU of the Schur matrix, 1 preconditioned conjugate residual (Sec. III-C);
+// pc: the PCR preconditioner (0 Jacobi, 1 block Jacobi); pcr_iters: PCR iterations per Newton
+// step; pcr_iters_adj / pcr_rtol_adj: the adjoint's PCR solve (at most that many iterations,
+// stopping once |r| <= rtol |b|)
+enum { LIN_DIRECT = 0, LIN_PCR = 1 };
+enum { PC_JACOBI = 0, PC_BLOCK = 1 };
+struct OCfg {
+  int budget, kmin, ls, pullback; double tol, delta_rel, kappa, eps, margin;
+  int lin = LIN_DIRECT, pc = PC_JACOBI, pcr_iters = 16, pcr_iters_adj = 256; double pcr_rtol_adj = 1e-12;
+};
 
 // flat scene format: header[14], then nb*10 body values, then nj*24 joint values
 // (parent, child, anchor_p[3], anchor_c[3], axis_p[3], axis_c[3], perp1_p[3], perp2_p[3], kp,
@@ -180,6 +191,8 @@ bool parse_scene(const double* p, const float* heights, OScene& s) {
 void parse_cfg(const double* c, OCfg& o) {
   o.budget = (int)c[0]; o.kmin = (int)c[1]; o.tol = c[2]; o.delta_rel = c[3]; o.kappa = c[4];
   o.eps = c[5]; o.margin = c[6]; o.ls = (int)c[7]; o.pullback = (int)c[8];
+  o.lin = (int)c[9]; o.pc = (int)c[10]; o.pcr_iters = (int)c[11]; o.pcr_iters_adj = (int)c[12];
+  o.pcr_rtol_adj = c[13];
 }
 
 // ---------------------------------------------------------------------------
@@ -906,6 +919,90 @@ bool lu_solve(int n, std::vector<double> A, std::vector<double>& b) {
 }
 
 // ---------------------------------------------------------------------------
+// preconditioned conjugate residual (Sec. III-C solves Eq. (12) with it)
+// ---------------------------------------------------------------------------
+// The conjugate residual method for a symmetric positive definite A with a symmetric
+// positive definite preconditioner P (dense, row-major, n x n), from x0 = 0:
+//   r0 = b, z0 = P r0, p0 = z0;  per iteration k
+//   alpha = (z_k, A z_k) / (A p_k, P A p_k)
+//   x += alpha p_k,  r -= alpha A p_k,  z -= alpha P A p_k      (z_k = P r_k throughout)
+//   beta = (z_k+1, A z_k+1) / (z_k, A z_k),  p_k+1 = z_k+1 + beta p_k,  A p_k+1 = A z_k+1 + beta A p_k.
+// x_k minimises |L^T (b - A x)|_2, P = L L^T, over the Krylov space K_k(P A, P b) (the
+// textbook method, e.g. Saad, Iterative Methods for Sparse Linear Systems, Sec. 6.8 and
+// 9.2).  At most `iters` iterations; with rtol > 0 it stops after the first iteration with
+// |r_k| <= rtol |b| (r from the recurrence) and sets *conv.  It stops early, too, when a
+// denominator is not positive (the exact solution reached, or breakdown).  Returns the
+// iterations taken.
+int pcr(int n, const std::vector<double>& A, const std::vector<double>& P, const std::vector<double>& b,
+        std::vector<double>& x, int iters, double rtol, bool* conv) {
+  auto mv = [n](const std::vector<double>& M, const std::vector<double>& v, std::vector<double>& o) {
+    for (int i = 0; i < n; ++i) {
+      double acc = 0.0;
+      for (int j = 0; j < n; ++j) acc += M[i * n + j] * v[j];
+      o[i] = acc;
+    }
+  };
+  auto dot = [n](const std::vector<double>& a, const std::vector<double>& c) {
+    double acc = 0.0;
+    for (int i = 0; i < n; ++i) acc += a[i] * c[i];
+    return acc;
+  };
+  x.assign(n, 0.0);
+  std::vector<double> r = b, z(n), p(n), Az(n), Ap(n), q(n);
+  if (conv) *conv = false;
+  const double bb = dot(b, b);
+  if (bb == 0.0) { if (conv) *conv = true; return 0; }
+  mv(P, r, z);
+  p = z;
+  mv(A, z, Az);
+  Ap = Az;
+  double rho = dot(z, Az);
+  int k = 0;
+  for (; k < iters; ++k) {
+    mv(P, Ap, q);
+    const double den = dot(Ap, q);
+    if (!(den > 0.0) || !(rho > 0.0)) break;
+    const double alpha = rho / den;
+    for (int i = 0; i < n; ++i) { x[i] += alpha * p[i]; r[i] -= alpha * Ap[i]; z[i] -= alpha * q[i]; }
+    mv(A, z, Az);
+    const double rho1 = dot(z, Az);
+    const double beta = rho1 / rho;
+    rho = rho1;
+    for (int i = 0; i < n; ++i) { p[i] = z[i] + beta * p[i]; Ap[i] = Az[i] + beta * Ap[i]; }
+    if (rtol > 0.0 && dot(r, r) <= rtol * rtol * bb) { if (conv) *conv = true; ++k; break; }
+  }
+  return k;
+}
+
+// The preconditioner P as a dense matrix: Jacobi, P = diag(A)^-1, or block Jacobi, P the
+// inverse of A's diagonal blocks, block[i] naming the block of row i.  (The paper names
+// no preconditioner; these two are the readings built.)
+std::vector<double> precond_matrix(int n, const std::vector<double>& A, const std::vector<int>& block, int kind) {
+  std::vector<double> P(n * n, 0.0);
+  if (kind == PC_JACOBI) {
+    for (int i = 0; i < n; ++i) P[i * n + i] = 1.0 / A[i * n + i];
+    return P;
+  }
+  std::vector<int> seen;
+  for (int i = 0; i < n; ++i) {
+    if (std::find(seen.begin(), seen.end(), block[i]) != seen.end()) continue;
+    seen.push_back(block[i]);
+    std::vector<int> idx;
+    for (int j = 0; j < n; ++j) if (block[j] == block[i]) idx.push_back(j);
+    const int nk = (int)idx.size();
+    std::vector<double> Ab(nk * nk);
+    for (int a = 0; a < nk; ++a) for (int c = 0; c < nk; ++c) Ab[a * nk + c] = A[idx[a] * n + idx[c]];
+    for (int c = 0; c < nk; ++c) {      // column c of the block's inverse
+      std::vector<double> e(nk, 0.0);
+      e[c] = 1.0;
+      lu_solve(nk, Ab, e);
+      for (int a = 0; a < nk; ++a) P[idx[a] * n + idx[c]] = e[a];
+    }
+  }
+  return P;
+}
+
+// ---------------------------------------------------------------------------
 // the per-world solver
 // ---------------------------------------------------------------------------
 struct Solver {
@@ -1052,6 +1149,33 @@ void j_apply(const Solver& S, const Eval<double>& E, const double* v, double* ou
   }
 }
 
+// Block of each row for the block-Jacobi preconditioner: the contact rows of one body
+// (normal and friction rows of all its contacts) form a block, the joint and servo rows
+// together another.
+std::vector<int> row_blocks(const Solver& S) {
+  std::vector<int> blk(S.W.rows.size());
+  for (size_t i = 0; i < blk.size(); ++i) {
+    const Row& r = S.W.rows[i];
+    blk[i] = (r.type == ROW_NORMAL || r.type == ROW_FRIC) ? r.b0 : -1;
+  }
+  return blk;
+}
+
+// A x = b for the Schur matrix of Eq. (12) by the configured method: dense LU, or PCR
+// (Newton steps: cfg.pcr_iters iterations; the adjoint: up to cfg.pcr_iters_adj, stopping
+// at |r| <= cfg.pcr_rtol_adj |b|).  Returns false when LU meets a singular matrix.
+bool schur_linear_solve(const Solver& S, const std::vector<double>& A, const std::vector<double>& b,
+                        std::vector<double>& x, bool adjoint) {
+  const OCfg& cfg = *S.W.cfg;
+  const int m = (int)b.size();
+  if (m == 0) { x.clear(); return true; }
+  if (cfg.lin != LIN_PCR) { x = b; return lu_solve(m, A, x); }
+  const std::vector<double> P = precond_matrix(m, A, row_blocks(S), cfg.pc);
+  if (adjoint) pcr(m, A, P, b, x, cfg.pcr_iters_adj, cfg.pcr_rtol_adj, nullptr);
+  else pcr(m, A, P, b, x, cfg.pcr_iters, 0.0, nullptr);
+  return true;
+}
+
 // Newton iterate container
 struct Iter { std::vector<double> u, lam; Eval<double> E; };
 
@@ -1086,8 +1210,7 @@ void solve_step(Solver& S) {
     std::vector<double> jm(m);
     j_apply(S, cur.E, mr.data(), jm.data());
     for (size_t i = 0; i < m; ++i) rhs[i] = jm[i] - cur.E.rhat[i];
-    dl = rhs;
-    bool ok = m == 0 ? true : lu_solve((int)m, A, dl);
+    bool ok = schur_linear_solve(S, A, rhs, dl, false);
     if (!ok) for (size_t i = 0; i < m; ++i) dl[i] = NAN;
     // Eq. (13): du = M^-1 (h J^T dl - r_dyn)
     std::vector<double> jtdl(nu);
@@ -1242,7 +1365,8 @@ void adjoint(const Solver& Sv, const double* dL_dsp, int mode, AdjOut& out) {
     minv_apply(Sv, g.data(), mg.data());
     j_apply(Sv, E, mg.data(), jmg.data());
     for (size_t i = 0; i < m; ++i) wl[i] = -h * jmg[i];
-    if (m) lu_solve((int)m, A, wl);
+    std::vector<double> rhs = wl;
+    schur_linear_solve(Sv, A, rhs, wl, true);
     // Eq. (19): w_u = -M^-1 (g + J^T w_lambda)
     std::vector<double> jtw(nu), t(nu);
     jt_apply(Sv, E, wl.data(), jtw.data());
@@ -1484,6 +1608,20 @@ int oracle_lu_solve(int n, const double* A, const double* b, double* x) {
   bool ok = lu_solve(n, AA, bb);
   for (int i = 0; i < n; ++i) x[i] = bb[i];
   return ok ? 0 : 1;
+}
+
+// PCR on a dense system, for the pins: P from precond_matrix(kind, block) (block: n ids).
+// Returns the iterations taken; conv_out (may be null) receives 1 when |r| <= rtol |b|.
+int oracle_pcr(int n, const double* A, const double* b, int kind, const int32_t* block, int iters, double rtol,
+               double* x, int32_t* conv_out) {
+  std::vector<double> AA(A, A + n * n), bb(b, b + n), xx;
+  std::vector<int> blk(block, block + n);
+  const std::vector<double> P = precond_matrix(n, AA, blk, kind);
+  bool conv = false;
+  const int k = pcr(n, AA, P, bb, xx, iters, rtol, &conv);
+  for (int i = 0; i < n; ++i) x[i] = xx[i];
+  if (conv_out) *conv_out = conv ? 1 : 0;
+  return k;
 }
 
 // Contact slot table at q-: per slot active flag, packed id, normal and offset.

@@ -101,6 +101,10 @@ class Env:
     origin: tuple = (0.0, 0.0)
 
 
+LIN_DIRECT, LIN_PCR = 0, 1
+PC_JACOBI, PC_BLOCK = 0, 1
+
+
 @dataclasses.dataclass
 class SolverConfig:
     budget: int = 16          # Newton iterations per step (Sec. IV-B: 16)
@@ -112,6 +116,13 @@ class SolverConfig:
     margin: float = 0.02      # contact activation margin (m)
     line_search: int = 0      # 0: full steps + best iterate (Sec. III-C); 1: backtracking alpha in {1,1/2,1/4,1/8}
     pullback: int = PULLBACK_FULL
+    # Schur solve of Eq. (12): LIN_DIRECT (block-arrowhead Cholesky factor) or LIN_PCR
+    # (matrix-free preconditioned conjugate residual, the paper's solver)
+    linear_solver: int = 0
+    precond: int = 0          # PCR preconditioner: PC_JACOBI or PC_BLOCK
+    pcr_iters: int = 16       # PCR iterations per Newton step (Sec. IV-B: 16)
+    pcr_iters_adj: int = 256  # at most this many PCR iterations in the adjoint's solve
+    pcr_rtol_adj: float = 0.0  # adjoint PCR stops at |r| <= rtol |b|; 0: 1e-6 (FP32), 1e-12 (FP64)
 
 
 @dataclasses.dataclass

@@ -307,6 +307,8 @@ def run_ours(args, rank, world_size, local_rank):
         out["cpu_baseline"] = run_cpu_baseline(args)
         if args.terrain_worlds > 0:
             out["terrain"] = run_terrain(args, torch)
+        if args.linear_solvers:
+            out["linear_solvers"] = run_linear_solvers(args, torch)
         if args.serve_seconds > 0:
             out["serving"] = run_serving(args, torch)
     ctx.close()
@@ -459,6 +461,78 @@ def run_param_grads(ctx, chunk, torch, reps=5):
                                         "max": int(its.max()), "not_converged": int(((k >> 16) & 1).sum())},
             "outputs": f"dL/dk_p ({ctx.n_servo} servo gains), dL/dm ({ctx.nb} body masses), "
                        f"dL/dI ({3 * ctx.nb} principal moments), dL/dmu per world"}
+
+
+def run_linear_solvers(args, torch, reps=3):
+    """The Schur solve of Eq. (12) by the direct block-arrowhead factor against the paper's
+    matrix-free PCR (Sec. III-C; 16 PCR iterations per Newton step in Sec. IV-B) with the
+    Jacobi and the block-Jacobi preconditioner, on the robot over the box (args.worlds
+    worlds) and the mesh terrain (args.terrain_worlds worlds, truncated pull-back), FP32,
+    budget 16: per configuration the 10-step chunk (forward with the tape, then the
+    adjoint, whose PCR solve runs to 1e-10), 2 warm-up and `reps` timed chunks; the share
+    of steps whose Newton iteration met the tolerance within the budget, and the adjoint's
+    PCR iterations."""
+    from paper_2609_08800_gb300.ostrich import Context
+    configs = [("direct", {}),
+               ("pcr_jacobi_16", dict(linear_solver=S.LIN_PCR, precond=S.PC_JACOBI, pcr_iters=16)),
+               ("pcr_block_16", dict(linear_solver=S.LIN_PCR, precond=S.PC_BLOCK, pcr_iters=16)),
+               ("pcr_jacobi_64", dict(linear_solver=S.LIN_PCR, precond=S.PC_JACOBI, pcr_iters=64)),
+               ("pcr_block_32", dict(linear_solver=S.LIN_PCR, precond=S.PC_BLOCK, pcr_iters=32))]
+    out = {}
+    legs = [("robot_over_box", args.worlds)]
+    if args.terrain_worlds > 0:
+        legs.append(("mesh_terrain", args.terrain_worlds))
+    for leg, W in legs:
+        if leg == "robot_over_box":
+            scene, states, controls, g = make_inputs(W, seed=0)
+            pull = S.PULLBACK_FULL
+        else:
+            scene = S.terrain_scene()
+            states = S.terrain_states(scene, W, seed=0)
+            knots = S.spline_knots(W, n_wheels=4, n_knots=8, seed=1)
+            controls = np.ascontiguousarray(np.einsum("tk,wjk->tjw", SP.basis(100, 8, H), knots))[:CHUNK]
+            controls = controls.astype(np.float32)
+            g = np.zeros((scene.n_state, W))
+            pull = S.PULLBACK_TRUNCATED
+        res = {"worlds": W}
+        for name, kw in configs:
+            cfg = S.SolverConfig(tol=FP32_TOL, pullback=pull, **kw)
+            ctx = Context(scene, cfg, W, dtype="f32", tape_slots=CHUNK, threads=64 if leg == "robot_over_box" else 128)
+            kry = torch.zeros(W, dtype=torch.int32, device="cuda")
+            ctx.set_adjoint_mode(0, kry)
+            chunk = Chunk(ctx, torch, W)
+            s0 = torch.tensor(states, dtype=torch.float32, device="cuda")
+            ctl = torch.tensor(controls, dtype=torch.float32, device="cuda")
+            gT = torch.tensor(g, dtype=torch.float32, device="cuda")
+            if leg == "mesh_terrain":
+                chunk.run(s0, ctl, gT)                      # landing, then chunks from the landed states
+                s0 = chunk.states[CHUNK].clone()
+                gT[0] = 2.0 * (s0[0] - 3.0)
+                gT[1] = 2.0 * s0[1]
+            for _ in range(2):
+                chunk.run(s0, ctl, gT)
+            torch.cuda.synchronize()
+            evs = [[[torch.cuda.Event(enable_timing=True) for _ in range(2)] for _ in range(CHUNK)] for _ in range(reps)]
+            eva = [[[torch.cuda.Event(enable_timing=True) for _ in range(2)] for _ in range(CHUNK)] for _ in range(reps)]
+            for k in range(reps):
+                chunk.run(s0, ctl, gT, evs[k], eva[k])
+            torch.cuda.synchronize()
+            it = np.stack([t.cpu().numpy() for t in chunk.iters]) & 0xFFFF
+            step_ms = statistics.mean(e[0].elapsed_time(e[1]) for k in range(reps) for e in evs[k])
+            adj_ms = statistics.mean(e[0].elapsed_time(e[1]) for k in range(reps) for e in eva[k])
+            kr = kry.cpu().numpy()
+            r = {"step_ms": step_ms, "adjoint_ms": adj_ms,
+                 "world_steps_per_s": W * CHUNK / ((step_ms + adj_ms) * CHUNK * 1e-3),
+                 "newton_iters_mean": float(it.mean()), "converged_within_budget": float((it < cfg.budget).mean())}
+            if kw:
+                r["adjoint_pcr_iters_mean"] = float((kr & 0xFFFF).mean())
+                r["adjoint_pcr_not_converged"] = int(((kr >> 16) & 1).sum())
+            res[name] = r
+            ctx.close()
+        out[leg] = res
+    out["settings"] = "FP32, Newton budget 16, tol 1e-4 m/s, h = 0.1; robot 64 and terrain 128 threads per world, " \
+                      "one CTA per world; adjoint PCR restarted on the true residual to |r| <= 1e-10 |b| (at most 256 iterations)"
+    return out
 
 
 def run_e2e(args, ctx, chunk, states, controls, g, torch):
@@ -762,6 +836,8 @@ def main():
     ap.add_argument("--serve-baseline-cutoff", type=float, default=20.0,
                     help="wall-clock cutoff of the FIFO-queue and plain-form runs of the stated stream")
     ap.add_argument("--threads", type=int, default=None, help="threads per world (default: autotuner table)")
+    ap.add_argument("--linear-solvers", type=int, default=1,
+                    help="1: time the direct factor against PCR (robot and terrain legs); 0: skip")
     ap.add_argument("--plain-worlds", type=int, default=512)
     ap.add_argument("--cpu-worlds", type=int, default=24)
     ap.add_argument("--cpu-procs", type=int, default=0,

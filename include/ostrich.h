@@ -53,6 +53,10 @@ enum { OSTRICH_ENV_PLANE = 0, OSTRICH_ENV_BOX = 1, OSTRICH_ENV_HEIGHTMAP = 2 };
 enum { OSTRICH_SHAPE_NONE = 0, OSTRICH_SHAPE_BOX = 1, OSTRICH_SHAPE_WHEEL = 2 };
 enum { OSTRICH_PULLBACK_FULL = 0, OSTRICH_PULLBACK_TRUNCATED = 1 };
 enum { OSTRICH_ADJ_PAPER = 0, OSTRICH_ADJ_EXACT = 1 };
+/* Linear solver of the Schur system Eq. (12) (ostrich_set_linear_solver) and the PCR
+ * preconditioner. */
+enum { OSTRICH_LIN_DIRECT = 0, OSTRICH_LIN_PCR = 1 };
+enum { OSTRICH_PC_JACOBI = 0, OSTRICH_PC_BLOCK = 1 };
 
 #define OSTRICH_MAX_BODIES 8
 #define OSTRICH_MAX_JOINTS 8
@@ -174,9 +178,38 @@ ostrich_status ostrich_adjoint_params(ostrich_ctx* ctx, int tape_slot, const voi
  * through the taped factor; its q- pull-back is always the full one.  krylov_iters: a
  * device array of n_worlds int32 (or NULL) that receives, per world, the GMRES iterations
  * of the exact mode, with bit 16 set when the relative residual did not reach 1e-6
- * (FP32) / 1e-13 (FP64).  EINVAL for an unknown mode or when the exact mode's working
+ * (FP32) / 1e-13 (FP64); under the PCR solver (ostrich_set_linear_solver) the paper mode
+ * writes its PCR iterations there the same way.  EINVAL for an unknown mode or when the exact mode's working
  * set (about twice the paper mode's) exceeds the shared memory of one CTA. */
 ostrich_status ostrich_set_adjoint_mode(ostrich_ctx* ctx, int mode, int32_t* krylov_iters);
+
+/* Linear solver of the Schur system A dl = rhs of Eq. (12), A = h J M^-1 J^T + C + delta I,
+ * in the context's steps and adjoints (Sec. III-C, III-D).
+ *   OSTRICH_LIN_DIRECT (default): the block-arrowhead Cholesky factor, formed at every Newton
+ *     iterate and recorded on the tape at the returned iterate for the adjoint.
+ *   OSTRICH_LIN_PCR: the paper's matrix-free preconditioned conjugate residual: iters
+ *     iterations per Newton step from dl = 0, each one product with A formed from the rows
+ *     (never assembled) and one application of the preconditioner, precond =
+ *     OSTRICH_PC_JACOBI (the inverse diagonal of A) or OSTRICH_PC_BLOCK (the inverse of each
+ *     contact group's diagonal block and of the joint/servo block, by in-place Cholesky).
+ *     Nothing but the iterate is taped; the paper-mode adjoint forms the same operator and
+ *     preconditioner at the taped iterate and solves with PCR, restarted on the true
+ *     residual (formed with compensated sums) until |r| <= adj_rtol |rhs|, until a restart
+ *     no longer changes the solution at working precision, or after adj_iters PCR iterations
+ *     in all (krylov_iters of ostrich_set_adjoint_mode, when given, receives the iterations
+ *     per world, bit 16 set if neither test was met).
+ *     The exact-mode adjoint forms the direct factor at the taped iterate as its GMRES
+ *     preconditioner.
+ * iters and adj_iters >= 1; adj_rtol >= 0 (0: 1e-10 for FP32, 1e-12 for FP64; the Schur
+ * matrix's condition number, up to ~1e6 with contact compliance, turns a residual of rtol
+ * into a solution error of up to cond x rtol).  Both
+ * solvers reach the same solution of each step when its Newton iteration converges; PCR
+ * with few iterations leaves inexact Newton steps and so needs more of them.  A change of
+ * the solver discards what the tape holds (its slots read as unwritten).  EINVAL for an
+ * unknown solver or preconditioner, counts below 1, or a PCR working set (7 m_max values
+ * more per world) beyond the shared memory of one CTA. */
+ostrich_status ostrich_set_linear_solver(ostrich_ctx* ctx, int solver, int precond, int iters, int adj_iters,
+                                         double adj_rtol);
 
 /* Step of a selected subset of worlds (Sec. III-C, per world as ostrich_step): CTA b
  * steps world worlds[b] and, when tape_slots is not NULL and tape_slots[b] >= 0,

@@ -2,6 +2,7 @@
 // argument checks and kernel launches.  Every step of the path runs in the CUDA
 // kernels of ostrich_kernels.cuh; this file only validates and dispatches.
 #include <cuda_runtime.h>
+#include <algorithm>
 #include <cstdio>
 #include <cstring>
 #include <new>
@@ -28,7 +29,8 @@ struct ostrich_ctx {
   double* trace = nullptr;
   int schedule = 0;
   int adj_mode = 0;                // 0: paper (frozen W), 1: exact IFT
-  int32_t* krylov = nullptr;       // exact mode: per-world GMRES iterations (caller's device array) or null
+  int32_t* krylov = nullptr;       // per-world Krylov iterations of the adjoint (GMRES of the exact mode, PCR of
+                                   // the PCR solver's paper mode; the caller's device array) or null
   int32_t* d_sched = nullptr;      // persistent schedule: [queue, cost[n_worlds], order[n_worlds]]
   char err[512] = {0};
   // device memory is released with the context, on every path out of ostrich_create too
@@ -206,6 +208,26 @@ ostrich_status ostrich_set_adjoint_mode(ostrich_ctx* c, int mode, int32_t* krylo
   if (smem > ost::SMEM_CTA_MAX) return fail(c, OSTRICH_EINVAL, "the exact adjoint's working set exceeds shared memory");
   c->adj_mode = mode;
   c->krylov = krylov_iters;
+  return OSTRICH_OK;
+}
+
+ostrich_status ostrich_set_linear_solver(ostrich_ctx* c, int solver, int precond, int iters, int adj_iters,
+                                         double adj_rtol) {
+  if (!c) return OSTRICH_EINVAL;
+  if (solver != OSTRICH_LIN_DIRECT && solver != OSTRICH_LIN_PCR) return fail(c, OSTRICH_EINVAL, "unknown linear solver");
+  if (precond != OSTRICH_PC_JACOBI && precond != OSTRICH_PC_BLOCK) return fail(c, OSTRICH_EINVAL, "unknown preconditioner");
+  if (iters < 1 || adj_iters < 1 || !(adj_rtol >= 0)) return fail(c, OSTRICH_EINVAL, "PCR counts must be >= 1");
+  ost::DevScene s = c->sc;
+  s.lin = solver; s.pc = precond; s.pcr_iters = iters; s.pcr_iters_adj = adj_iters;
+  s.pcr_rtol_adj = adj_rtol > 0 ? adj_rtol : (c->dtype == OSTRICH_F32 ? 1e-10 : 1e-12);
+  const bool f64 = c->dtype == OSTRICH_F64;
+  const size_t ws = f64 ? ost::ws_bytes<double>(s) : ost::ws_bytes<float>(s);
+  const size_t used = f64 ? ost::ws_used<double>(s) : ost::ws_used<float>(s);
+  const size_t adj = f64 ? ost::adj_smem_bytes<double>(s, c->adj_mode) : ost::adj_smem_bytes<float>(s, c->adj_mode);
+  if (ws > ost::SMEM_CTA_MAX || used > ws || adj > ost::SMEM_CTA_MAX)
+    return fail(c, OSTRICH_EINVAL, "the PCR working set exceeds shared memory");
+  c->sc = s;
+  std::fill(c->slot_written.begin(), c->slot_written.end(), (unsigned char)0);
   return OSTRICH_OK;
 }
 

@@ -53,6 +53,7 @@ template <class Real> struct WS {
   int *ints;      // [0] rows, [1] contact rows, [2] items, [3] converged, [4] best_k, [5] iters, [6] status,
                   // [7] contact-generation status bits (4: candidates beyond the slots)
   Real *scal;     // [0] merit cur, [1] best merit, [2] delta, [3] merit trial
+  Real *pcr;      // PCR mode: r, z, p, A p, A z, P A p and the Jacobi diagonal, m_max each
 };
 
 template <class T> __host__ __device__ __forceinline__ T* carve(char*& p, int n) {
@@ -95,6 +96,7 @@ template <class Real> __host__ __device__ WS<Real> ws_carve(char* base, const De
   w.prow = carve<Real>(p, 4 * (pg > ss ? pg : ss));
   w.tmp = carve<Real>(p, m); w.tmp2 = carve<Real>(p, m);
   w.red = carve<Real>(p, 64); w.ints = carve<int>(p, 16); w.scal = carve<Real>(p, 8);
+  w.pcr = s.lin == LIN_PCR ? carve<Real>(p, 7 * m) : nullptr;
   return w;
 }
 
@@ -104,7 +106,7 @@ template <class Real> __host__ __device__ WS<Real> ws_carve(char* base, const De
 template <class Real> __host__ __device__ size_t ws_bytes(const DevScene& s) {
   char* base = reinterpret_cast<char*>(uintptr_t(16));
   WS<Real> w = ws_carve<Real>(base, s);
-  size_t used = (size_t)(reinterpret_cast<char*>(w.scal + 8) - base);
+  size_t used = (size_t)(reinterpret_cast<char*>(w.pcr ? w.pcr + 7 * s.m_max : w.scal + 8) - base);
   return (used + 15) & ~(size_t)15;
 }
 
@@ -801,82 +803,131 @@ template <int TEAM, class Real> __device__ void chol_inv_inplace(Real* A, int n,
   }
 }
 
-// The same in-place L^-1 by the whole CTA, two pivots per round: every thread forms the
-// 2 x 2 pivot block (k, k+1) itself; pass 1 gives columns k and k+1 of L (colbuf,
-// colbuf + n) and finishes rows k and k+1 of L^-1; pass 2 applies both rank-one updates
-// (k, then k+1) to the trailing block and to the rows of L^-1 below.  Each element sees
-// the same operations in the same order as one pivot per round; half the barriers.
-// colbuf holds 2 n values.
-template <class Real> __device__ void chol_inv_inplace2(Real* A, int n, Real* colbuf) {
+// One round of P pivots (k .. k+P-1) of the in-place L^-1 by the whole CTA, P <= 4.  Every
+// thread forms the P x P pivot block itself: the inverse pivots ip[p] = 1/L[k+p][k+p], the
+// block's L below the diagonal and its inverse X.  Pass 1 gives columns k .. k+P-1 of L
+// below the block (colbuf, n values per column) and finishes rows k .. k+P-1 of L^-1 left
+// of it; pass 2 applies the P rank-one updates, in pivot order, to the trailing block and
+// to the rows of L^-1 below.  Every element receives the operations of the one-pivot-per-
+// round factor in the same order (k ascending); a round costs two barriers.
+template <int P, class Real> __device__ void chol_round(Real* A, int n, int k, Real* colbuf) {
   const int t = threadIdx.x, T = blockDim.x;
-  Real* c0 = colbuf;
-  Real* c1 = colbuf + n;
+  Real a[P][P], l[P][P], x[P][P], xt[P][P], ip[P];
+#pragma unroll
+  for (int p = 0; p < P; ++p)
+#pragma unroll
+    for (int q = 0; q < P; ++q) { a[p][q] = q <= p ? A[tri(k + p, k + q)] : Real(0); xt[p][q] = Real(0); }
+#pragma unroll
+  for (int p = 0; p < P; ++p) {
+    ip[p] = pivot_rsqrt(a[p][p] > Real(0) ? a[p][p] : Real(1e-30));
+#pragma unroll
+    for (int r = p + 1; r < P; ++r) l[r][p] = a[r][p] * ip[p];
+#pragma unroll
+    for (int r = p + 1; r < P; ++r)
+#pragma unroll
+      for (int c = p + 1; c <= r; ++c) a[r][c] = a[r][c] - l[r][p] * l[c][p];
+  }
+#pragma unroll
+  for (int p = 0; p < P; ++p) {
+#pragma unroll
+    for (int q = 0; q < p; ++q) x[p][q] = xt[p][q] * ip[p];
+    x[p][p] = ip[p];
+#pragma unroll
+    for (int r = p + 1; r < P; ++r) {
+#pragma unroll
+      for (int q = 0; q < p; ++q) xt[r][q] = xt[r][q] - l[r][p] * x[p][q];
+      xt[r][p] = Real(0) - l[r][p] * x[p][p];
+    }
+  }
+  // pass 1 writes neither the pivot block nor any entry another thread reads in this pass
+  for (int e = t; e < n; e += T) {
+    if (e >= k + P) {
+      Real v[P];
+#pragma unroll
+      for (int p = 0; p < P; ++p) v[p] = A[tri(e, k + p)];
+#pragma unroll
+      for (int p = 0; p < P; ++p) {
+        const Real c = v[p] * ip[p];
+        colbuf[p * n + e] = c;
+#pragma unroll
+        for (int r = p + 1; r < P; ++r) v[r] = v[r] - c * l[r][p];
+      }
+    } else if (e < k) {
+      Real y[P];
+#pragma unroll
+      for (int p = 0; p < P; ++p) y[p] = A[tri(k + p, e)];
+#pragma unroll
+      for (int p = 0; p < P; ++p) {
+        const Real xe = y[p] * ip[p];
+        A[tri(k + p, e)] = xe;
+#pragma unroll
+        for (int r = p + 1; r < P; ++r) y[r] = y[r] - l[r][p] * xe;
+      }
+    }
+  }
+  __syncthreads();
+  if (t == 0) {
+#pragma unroll
+    for (int p = 0; p < P; ++p)
+#pragma unroll
+      for (int q = 0; q <= p; ++q) A[tri(k + p, k + q)] = x[p][q];
+  }
+  const int nw = T >> 5, lane = t & 31;
+  for (int j = lane; j < n; j += 32) {
+    // the P multipliers of column j, the first pivot that updates it (columns of the pivot
+    // block took the earlier pivots' updates into colbuf) and whether the entry keeps its value
+    Real m[P];
+    int qs = 0;
+    bool keep = true;
+    if (j < k) {
+#pragma unroll
+      for (int p = 0; p < P; ++p) m[p] = A[tri(k + p, j)];
+    } else if (j < k + P) {
+      qs = j - k;
+      keep = false;
+#pragma unroll
+      for (int p = 0; p < P; ++p) {
+        Real xv = Real(0);
+#pragma unroll
+        for (int q = 0; q < P; ++q) if (q == j - k && q <= p) xv = x[p][q];
+        m[p] = xv;
+      }
+    } else {
+#pragma unroll
+      for (int p = 0; p < P; ++p) m[p] = colbuf[p * n + j];
+    }
+    int i = (k + P > j ? k + P : j) + (t >> 5);
+    for (; i + 3 * nw < n; i += 4 * nw) {                  // four independent rows per pass
+      int ii[4] = {i, i + nw, i + 2 * nw, i + 3 * nw};
+      Real v[4];
+#pragma unroll
+      for (int r = 0; r < 4; ++r) v[r] = keep ? A[tri(ii[r], j)] : Real(0);
+#pragma unroll
+      for (int p = 0; p < P; ++p)
+        if (p >= qs)
+#pragma unroll
+          for (int r = 0; r < 4; ++r) v[r] = v[r] - colbuf[p * n + ii[r]] * m[p];
+#pragma unroll
+      for (int r = 0; r < 4; ++r) A[tri(ii[r], j)] = v[r];
+    }
+    for (; i < n; i += nw) {
+      Real v = keep ? A[tri(i, j)] : Real(0);
+#pragma unroll
+      for (int p = 0; p < P; ++p)
+        if (p >= qs) v = v - colbuf[p * n + i] * m[p];
+      A[tri(i, j)] = v;
+    }
+  }
+  __syncthreads();
+}
+
+// In-place L^-1 of an n x n SPD block by the whole CTA: four pivots per round, the
+// remainder two and one at a time.  colbuf holds 4 n values.
+template <class Real> __device__ void chol_inv_inplace4(Real* A, int n, Real* colbuf) {
   int k = 0;
-  for (; k + 1 < n; k += 2) {
-    const int k1 = k + 1;
-    const Real a00 = A[tri(k, k)];
-    const Real i0 = pivot_rsqrt(a00 > Real(0) ? a00 : Real(1e-30));
-    const Real l10 = A[tri(k1, k)] * i0;                   // L[k+1][k]
-    const Real a11 = A[tri(k1, k1)] - l10 * l10;
-    const Real i1 = pivot_rsqrt(a11 > Real(0) ? a11 : Real(1e-30));
-    const Real x10 = (-(l10 * i0)) * i1;                   // X[k+1][k]
-    // pass 1 writes neither the pivot block (its entries are written in pass 2) nor any
-    // entry another thread reads in this pass
-    for (int e = t; e < n; e += T) {
-      if (e > k1) {
-        const Real l0 = A[tri(e, k)] * i0;
-        c0[e] = l0;
-        c1[e] = (A[tri(e, k1)] - l0 * l10) * i1;
-      } else if (e < k) {
-        const Real xk = A[tri(k, e)] * i0;
-        A[tri(k, e)] = xk;
-        A[tri(k1, e)] = (A[tri(k1, e)] - l10 * xk) * i1;
-      }
-    }
-    __syncthreads();
-    if (t == 0) { A[tri(k, k)] = i0; A[tri(k1, k)] = x10; A[tri(k1, k1)] = i1; }
-    const int nw = T >> 5, lane = t & 31;
-    for (int j = lane; j < n; j += 32) {
-      // multipliers of l_ik and l_i(k+1) for column j, and whether the entry keeps its value
-      Real m0, m1;
-      bool keep = true;
-      if (j < k) { m0 = A[tri(k, j)]; m1 = A[tri(k1, j)]; }
-      else if (j == k) { m0 = i0; m1 = x10; keep = false; }
-      else if (j == k1) { m0 = Real(0); m1 = i1; keep = false; }
-      else { m0 = c0[j]; m1 = c1[j]; }
-      int i = (k1 + 1 > j ? k1 + 1 : j) + (t >> 5);
-      for (; i + 3 * nw < n; i += 4 * nw) {                 // four independent rows per pass
-        const int ia = i + nw, ib = ia + nw, ic = ib + nw;
-        Real* p0 = A + tri(i, j);
-        Real* p1 = A + tri(ia, j);
-        Real* p2 = A + tri(ib, j);
-        Real* p3 = A + tri(ic, j);
-        const Real a0 = c0[i], a1 = c0[ia], a2 = c0[ib], a3 = c0[ic];
-        const Real b0 = c1[i], b1 = c1[ia], b2 = c1[ib], b3 = c1[ic];
-        Real v0 = keep ? *p0 : Real(0), v1 = keep ? *p1 : Real(0);
-        Real v2 = keep ? *p2 : Real(0), v3 = keep ? *p3 : Real(0);
-        if (j != k1) { v0 = v0 - a0 * m0; v1 = v1 - a1 * m0; v2 = v2 - a2 * m0; v3 = v3 - a3 * m0; }
-        *p0 = v0 - b0 * m1; *p1 = v1 - b1 * m1; *p2 = v2 - b2 * m1; *p3 = v3 - b3 * m1;
-      }
-      for (; i < n; i += nw) {
-        Real* aij = A + tri(i, j);
-        Real v = keep ? *aij : Real(0);
-        if (j != k1) v = v - c0[i] * m0;
-        v = v - c1[i] * m1;
-        *aij = v;
-      }
-    }
-    __syncthreads();
-  }
-  if (k < n) {                                             // odd n: the last pivot alone
-    const Real akk = A[tri(k, k)];
-    const Real inv = pivot_rsqrt(akk > Real(0) ? akk : Real(1e-30));
-    __syncthreads();
-    for (int e = t; e < k; e += T) A[tri(k, e)] *= inv;
-    __syncthreads();
-    if (t == 0) A[tri(k, k)] = inv;
-    __syncthreads();
-  }
+  for (; k + 3 < n; k += 4) chol_round<4>(A, n, k, colbuf);
+  for (; k + 1 < n; k += 2) chol_round<2>(A, n, k, colbuf);
+  if (k < n) chol_round<1>(A, n, k, colbuf);
 }
 
 // Block-arrowhead factorisation kept in inverse form for row-parallel solves:
@@ -930,7 +981,7 @@ template <class Real> __device__ void factor(const DevScene& sc, WS<Real>& w, do
     __syncthreads();
   }
   // Lsi = L_s^-1 in place over S, the whole CTA
-  if (ss > 0) chol_inv_inplace2(w.S, ss, w.prow);
+  if (ss > 0) chol_inv_inplace4(w.S, ss, w.prow);
 }
 
 // v <- A^-1 v with the inverse-form block-arrowhead factor (row-parallel phases)
@@ -1099,6 +1150,258 @@ __device__ void schur_solve(const DevScene& sc, WS<Real>& w, const Real* b, Real
 }
 
 // ---------------------------------------------------------------------------
+// matrix-free Schur operator and preconditioned conjugate residual (Sec. III-C)
+// ---------------------------------------------------------------------------
+// out = A v, A = h J M^-1 J^T + C + delta I (+ the radial friction blocks), from the rows:
+// t6 = J^T v per body component (a thread per component, over the rows touching the
+// body), then per row h J_i M^-1 t6 plus the diagonal and radial terms.  ACC: exact
+// products and compensated sums throughout (the adjoint's solve).  Returns this thread's
+// part of v . out; the caller reduces it (the rows are written by their owning threads).
+template <class Real, bool ACC>
+__device__ Real schur_apply(const DevScene& sc, WS<Real>& w, const Real* v, Real* out, Real* t6, double h) {
+  const int tid = threadIdx.x, nth = blockDim.x, m = w.ints[0];
+  const int ssd = sc.ss > 0 ? sc.ss : 1;
+  for (int task = tid; task < 6 * sc.nb; task += nth) {
+    const int b = task / 6, k = task - 6 * (task / 6);
+    acc2<Real> ca;
+    Real acc = Real(0);
+    const int g = w.bgrp[b];
+    if (g >= 0)
+      for (int i = w.g0[g]; i < w.g0[g] + w.gn[g]; ++i) {
+        if (ACC) ca.add_prod(w.J[12 * i + k], v[i]);
+        else acc += w.J[12 * i + k] * v[i];
+      }
+    for (int t = 0; t < w.bsepn[b]; ++t) {
+      const int i = w.bsep[b * ssd + t];
+      const Real jv = w.J[12 * i + (w.meta[4 * i + 1] == b ? 0 : 6) + k];
+      if (ACC) ca.add_prod(jv, v[i]);
+      else acc += jv * v[i];
+    }
+    t6[task] = ACC ? ca.value() : acc;
+  }
+  __syncthreads();
+  const Real hR = Real(h), delta = w.scal[2];
+  Real part = Real(0);
+  for (int i = tid; i < m; i += nth) {
+    const Real* Ji = w.J + 12 * i;
+    acc2<Real> ca;
+    Real ax = Real(0);
+    for (int side = 0; side < 2; ++side) {
+      const int b = w.meta[4 * i + 1 + side];
+      if (b < 0) continue;
+      Real o[6];
+      minv6(sc, w, b, t6 + 6 * b, o);
+      for (int q = 0; q < 6; ++q) {
+        if (ACC) ca.add_prod(Ji[6 * side + q], o[q]);
+        else ax += Ji[6 * side + q] * o[q];
+      }
+    }
+    Real y;
+    const int t = w.meta[4 * i] & 15, sub = w.meta[4 * i] >> 4;
+    if (ACC) {
+      acc2<Real> ya;
+      ya.add_prod(hR, ca.s);
+      ya.add_prod(hR, ca.c);
+      ya.add_prod(w.C[i] + delta, v[i]);
+      if (t == ROW_FRIC) {
+        const Real* rd = w.srad + 3 * w.ref[i];
+        if (sub == 1) { ya.add_prod(rd[0], v[i]); ya.add_prod(rd[1], v[i + 1]); }
+        else { ya.add_prod(rd[1], v[i - 1]); ya.add_prod(rd[2], v[i]); }
+      }
+      y = ya.value();
+    } else {
+      y = hR * ax + (w.C[i] + delta) * v[i];
+      if (t == ROW_FRIC) {
+        const Real* rd = w.srad + 3 * w.ref[i];
+        y += sub == 1 ? rd[0] * v[i] + rd[1] * v[i + 1] : rd[1] * v[i - 1] + rd[2] * v[i];
+      }
+    }
+    out[i] = y;
+    part += v[i] * y;
+  }
+  return part;
+}
+
+// Jacobi preconditioner: the inverse diagonal of A, stored per row by the row's thread
+template <class Real> __device__ void pcr_jacobi(const DevScene& sc, WS<Real>& w, double h) {
+  const int tid = threadIdx.x, nth = blockDim.x, m = w.ints[0];
+  const Real hR = Real(h), delta = w.scal[2];
+  Real* pd = w.pcr + 6 * sc.m_max;
+  for (int i = tid; i < m; i += nth) {
+    const Real* Ji = w.J + 12 * i;
+    Real Yi[12];
+    minv_row(sc, w, i, Yi);
+    Real d = hR * (rowdot(Ji, 0, Yi, 0) + rowdot(Ji, 6, Yi, 6)) + w.C[i] + delta;
+    if ((w.meta[4 * i] & 15) == ROW_FRIC) d += w.srad[3 * w.ref[i] + ((w.meta[4 * i] >> 4) == 1 ? 0 : 2)];
+    pd[i] = Real(1) / d;
+  }
+}
+
+// Block-Jacobi preconditioner: each contact group's block and the (unreduced) separator
+// block of A, as assembled, factored in place to their inverse Cholesky factors (G, S)
+template <class Real> __device__ void factor_blocks(const DevScene& sc, WS<Real>& w) {
+  const int tid = threadIdx.x, nth = blockDim.x, wid = tid >> 5, nw = (blockDim.x + 31) >> 5;
+  const int pg = sc.pg, ss = sc.ss, gstr = tri_size(pg), rb = pg > ss ? pg : ss;
+  if (nth <= 64) {
+    const int team = tid >> 4, nteams = nth >> 4;
+    for (int g = team; g < sc.n_groups; g += nteams)
+      chol_inv_inplace<2>(w.G + g * gstr, w.gn[g], w.prow + team * rb);
+  } else {
+    for (int g = wid; g < sc.n_groups; g += nw) chol_inv_inplace<0>(w.G + g * gstr, w.gn[g], w.prow + (wid & 3) * rb);
+  }
+  __syncthreads();
+  if (ss > 0) chol_inv_inplace4(w.S, ss, w.prow);
+}
+
+// out = P v.  Jacobi: per row, by the row's thread (no synchronisation).  Block Jacobi:
+// L^-T L^-1 v per block (reads other rows of v: synchronises on entry and between the two
+// triangular products); out is written by the rows' threads.
+template <class Real> __device__ void pcr_precond(const DevScene& sc, WS<Real>& w, const Real* v, Real* out) {
+  const int tid = threadIdx.x, nth = blockDim.x, m = w.ints[0], mc = w.ints[1];
+  if (sc.pc == PC_JACOBI) {
+    const Real* pd = w.pcr + 6 * sc.m_max;
+    for (int i = tid; i < m; i += nth) out[i] = pd[i] * v[i];
+    return;
+  }
+  const int gstr = tri_size(sc.pg), ss = sc.ss;
+  Real* y = w.tmp;
+  __syncthreads();
+  for (int r = tid; r < m; r += nth) {
+    Real acc = Real(0);
+    if (r < mc) {
+      const int g = w.rgrp[r], r0 = w.g0[g], i = r - r0;
+      const Real* Li = w.G + g * gstr + tri(i, 0);
+      for (int l = 0; l <= i; ++l) acc += Li[l] * v[r0 + l];
+    } else {
+      const int a = r - mc;
+      const Real* La = w.S + tri(a, 0);
+      for (int b = 0; b <= a; ++b) acc += La[b] * v[mc + b];
+    }
+    y[r] = acc;
+  }
+  __syncthreads();
+  for (int r = tid; r < m; r += nth) {
+    Real acc = Real(0);
+    if (r < mc) {
+      const int g = w.rgrp[r], r0 = w.g0[g], i = r - r0, n = w.gn[g];
+      const Real* Lb = w.G + g * gstr;
+      for (int l = i; l < n; ++l) acc += Lb[tri(l, i)] * y[r0 + l];
+    } else {
+      const int a = r - mc;
+      for (int b = a; b < ss; ++b) acc += w.S[tri(b, a)] * y[mc + b];
+    }
+    out[r] = acc;
+  }
+}
+
+// Preconditioned conjugate residual on A x = b from x = 0 (A SPD, P SPD):
+//   r = b, z = P r, p = z;  per iteration
+//   alpha = (z, A z) / (A p, P A p);  x += alpha p;  r -= alpha A p;  z -= alpha P A p
+//   beta = (z', A z') / (z, A z);  p = z' + beta p;  A p = A z' + beta A p
+// one operator product and one preconditioner application per iteration; x_k minimises
+// |L^T (b - A x)| (P = L L^T) over K_k(P A, P b).  At most `iters` iterations; with rtol > 0
+// it stops after the first iteration with |r| <= rtol |b| and sets *conv.  Breakdown (a
+// denominator that is not positive: the exact solution reached) stops it too.  Every
+// decision is taken on block-reduced values, so all threads leave together.  t6: 6 nb
+// scratch.  Returns the iterations taken.
+template <class Real, bool ACC>
+__device__ int pcr_solve(const DevScene& sc, WS<Real>& w, const Real* b, Real* x, int iters, Real rtol, Real* t6,
+                         double h, int* conv) {
+  const int tid = threadIdx.x, nth = blockDim.x, m = w.ints[0], M = sc.m_max;
+  Real *r = w.pcr, *z = r + M, *p = z + M, *Ap = p + M, *Az = Ap + M, *q = Az + M;
+  Real bb = Real(0);
+  for (int i = tid; i < m; i += nth) { x[i] = Real(0); r[i] = b[i]; bb += b[i] * b[i]; }
+  pcr_precond(sc, w, r, z);
+  __syncthreads();
+  Real rho = schur_apply<Real, ACC>(sc, w, z, Az, t6, h);
+  for (int i = tid; i < m; i += nth) { p[i] = z[i]; Ap[i] = Az[i]; }
+  block_sum2(w, rho, bb);
+  *conv = 0;
+  if (!(bb > Real(0))) { *conv = 1; return 0; }
+  const Real target = rtol * rtol * bb;
+  int k = 0;
+  for (; k < iters; ++k) {
+    pcr_precond(sc, w, Ap, q);
+    Real den = Real(0);
+    for (int i = tid; i < m; i += nth) den += Ap[i] * q[i];
+    den = block_sum(w, den);
+    if (!(den > Real(0)) || !(rho > Real(0))) break;
+    const Real alpha = rho / den;
+    Real rr = Real(0);
+    for (int i = tid; i < m; i += nth) {
+      x[i] += alpha * p[i];
+      r[i] -= alpha * Ap[i];
+      z[i] -= alpha * q[i];
+      rr += r[i] * r[i];
+    }
+    __syncthreads();
+    Real rho1 = schur_apply<Real, ACC>(sc, w, z, Az, t6, h);
+    block_sum2(w, rho1, rr);
+    const Real beta = rho1 / rho;
+    rho = rho1;
+    for (int i = tid; i < m; i += nth) { p[i] = z[i] + beta * p[i]; Ap[i] = Az[i] + beta * Ap[i]; }
+    if (rtol > Real(0) && rr <= target) { *conv = 1; ++k; break; }
+  }
+  __syncthreads();
+  return k;
+}
+
+// The adjoint's PCR solve, restarted on the true residual: x = 0, r = b; then up to 8
+// times: PCR on A dx = r (asking for |r'| <= max(rtol |b| / |r|, floor) |r|, floor 1e-4 in
+// FP32: what one FP32 run's recurrence reliably attains), x += dx, and the true residual
+// r = b - A x formed with the compensated product.  It stops when |r| <= rtol |b|, when a
+// correction no longer changes x at working precision (max |dx| <= 2^-23 max |x| in FP32,
+// 2^-52 in FP64), or after `iters` PCR iterations in all.  The Schur matrix's condition
+// number (~1e5-1e6 with contact compliance) turns a residual of rtol into a solution error
+// of up to cond x rtol, hence the FP32 default rtol of 1e-10, far below what one FP32 run
+// reaches.  dx, rt: m-row scratch.  Returns the PCR iterations; *conv = 1 when either
+// stopping test was met.
+template <class Real>
+__device__ int pcr_solve_refined(const DevScene& sc, WS<Real>& w, const Real* b, Real* x, int iters, Real rtol,
+                                 Real* t6, Real* dx, Real* rt, double h, int* conv) {
+  const int tid = threadIdx.x, nth = blockDim.x, m = w.ints[0];
+  const Real floor = sizeof(Real) == 4 ? Real(1e-4) : Real(0);
+  const Real ulp = sizeof(Real) == 4 ? Real(1.1920929e-7) : Real(2.220446049250313e-16);
+  Real bb = Real(0);
+  for (int i = tid; i < m; i += nth) { x[i] = Real(0); rt[i] = b[i]; bb += b[i] * b[i]; }
+  bb = block_sum(w, bb);
+  Real rr = bb;
+  Real* Ax = w.pcr + 4 * sc.m_max;     // free between PCR runs
+  int its = 0;
+  *conv = 0;
+  for (int restart = 0; restart < 8; ++restart) {
+    if (!(rr > rtol * rtol * bb)) { *conv = 1; break; }
+    if (its >= iters) break;
+    int c2 = 0;
+    Real inner = rtol * ssqrt(bb / rr);
+    if (inner < floor) inner = floor;
+    its += pcr_solve<Real, true>(sc, w, rt, dx, iters - its, inner, t6, h, &c2);
+    Real dmax = Real(0), xmax = Real(0);
+    for (int i = tid; i < m; i += nth) {
+      x[i] += dx[i];
+      dmax = fmax(dmax, fabs(dx[i]));
+      xmax = fmax(xmax, fabs(x[i]));
+    }
+    __syncthreads();
+    schur_apply<Real, true>(sc, w, x, Ax, t6, h);
+    Real r2 = Real(0);
+    for (int i = tid; i < m; i += nth) {
+      acc2<Real> r;
+      r.add(b[i]);
+      r.add(-Ax[i]);
+      rt[i] = r.value();
+      r2 += rt[i] * rt[i];
+    }
+    rr = block_sum(w, r2);
+    dmax = block_max(w, dmax);
+    xmax = block_max(w, xmax);
+    if (restart > 0 && dmax <= ulp * xmax) { *conv = 1; break; }
+  }
+  if (!(rr > rtol * rtol * bb)) *conv = 1;
+  return its;
+}
+
+// ---------------------------------------------------------------------------
 // forward step kernel
 // ---------------------------------------------------------------------------
 // The scene lives in shared memory during a launch: kernels index its per-body and
@@ -1153,9 +1456,17 @@ __device__ __forceinline__ void step_world(const DevScene& sc, WS<Real>& w, cons
       for (int i = tid; i < m; i += nth) w.lb[i] = w.lk[i];
     }
     if (merit < tol2) { conv = 1; break; }
-    // Schur step, Eq. (12): (h J M^-1 J^T + C + delta) dl = J M^-1 r_dyn - rhat
-    assemble(sc, w, h);
-    factor(sc, w, h);
+    // Schur step, Eq. (12): (h J M^-1 J^T + C + delta) dl = J M^-1 r_dyn - rhat, by the
+    // block-arrowhead factor or by PCR (the preconditioner formed at this iterate)
+    if (sc.lin == LIN_DIRECT) {
+      assemble(sc, w, h);
+      factor(sc, w, h);
+    } else if (sc.pc == PC_BLOCK) {
+      assemble(sc, w, h);
+      factor_blocks(sc, w);
+    } else {
+      pcr_jacobi(sc, w, h);
+    }
     for (int i = tid; i < m; i += nth) {
       const Real* Ji = w.J + 12 * i;
       int b0 = w.meta[4 * i + 1], b1 = w.meta[4 * i + 2];
@@ -1166,7 +1477,12 @@ __device__ __forceinline__ void step_world(const DevScene& sc, WS<Real>& w, cons
       w.rhs[i] = jm.value();
     }
     __syncthreads();
-    schur_solve(sc, w, w.rhs, w.dl, w.du, w.lt, h, sc.refine);
+    if (sc.lin == LIN_DIRECT) {
+      schur_solve(sc, w, w.rhs, w.dl, w.du, w.lt, h, sc.refine);
+    } else {
+      int pconv;
+      pcr_solve<Real, false>(sc, w, w.rhs, w.dl, sc.pcr_iters, Real(0), w.du, h, &pconv);
+    }
     // Eq. (13): du = M^-1 (h J^T dl - r_dyn)
     jt_apply(sc, w, w.dl, w.du);
     __syncthreads();
@@ -1210,8 +1526,12 @@ __device__ __forceinline__ void step_world(const DevScene& sc, WS<Real>& w, cons
   if (!(mret == mret) || !(fabs((double)mret) < 1e300)) status |= 2u;
   status |= (uint32_t)w.ints[7];
   if (tpw) {
-    assemble(sc, w, h);
-    factor(sc, w, h);
+    // the direct mode records the factor at the returned iterate; PCR records no matrix
+    // (the adjoint forms its operator and preconditioner at the taped iterate)
+    if (sc.lin == LIN_DIRECT) {
+      assemble(sc, w, h);
+      factor(sc, w, h);
+    }
     Real* tp = tpw;
     for (int i = tid; i < 7 * nb; i += nth) tp[tl.off_qm + i] = w.qm[i];
     for (int i = tid; i < 6 * nb; i += nth) { tp[tl.off_um + i] = w.um[i]; tp[tl.off_u + i] = w.uk[i]; }
@@ -1219,9 +1539,11 @@ __device__ __forceinline__ void step_world(const DevScene& sc, WS<Real>& w, cons
     for (int i = tid; i < sc.m_max; i += nth) tp[tl.off_lam + i] = Real(0);
     __syncthreads();
     for (int i = tid; i < m; i += nth) tp[tl.off_lam + w.meta[4 * i + 3]] = w.lk[i];
-    for (int i = tid; i < sc.n_groups * tri_size(sc.pg); i += nth) tp[tl.off_G + i] = w.G[i];
-    for (int i = tid; i < sc.n_groups * sc.cmax * sc.ldg; i += nth) tp[tl.off_H + i] = w.H[i];
-    for (int i = tid; i < tri_size(sc.ss); i += nth) tp[tl.off_S + i] = w.S[i];
+    if (sc.lin == LIN_DIRECT) {
+      for (int i = tid; i < sc.n_groups * tri_size(sc.pg); i += nth) tp[tl.off_G + i] = w.G[i];
+      for (int i = tid; i < sc.n_groups * sc.cmax * sc.ldg; i += nth) tp[tl.off_H + i] = w.H[i];
+      for (int i = tid; i < tri_size(sc.ss); i += nth) tp[tl.off_S + i] = w.S[i];
+    }
   }
   // outputs: q+ (normalised quaternions), u+, lambda+, impulses h lambda, contact ids
   Real* so = reinterpret_cast<Real*>(a.state_out);
@@ -1373,10 +1695,23 @@ __global__ void __launch_bounds__(128, 3) adjoint_kernel(const DevScene scp, con
     for (int b = 0; b < nb; ++b) { item0[b] = acc; acc += 7 * (bgn[b] + 1); }
     item0[nb] = acc;
   }
-  // factor from the tape
-  for (int i = tid; i < sc.n_groups * tri_size(sc.pg); i += nth) w.G[i] = tp[tl.off_G + i];
-  for (int i = tid; i < sc.n_groups * sc.cmax * sc.ldg; i += nth) w.H[i] = tp[tl.off_H + i];
-  for (int i = tid; i < tri_size(sc.ss); i += nth) w.S[i] = tp[tl.off_S + i];
+  if (sc.lin == LIN_DIRECT) {
+    // factor from the tape
+    for (int i = tid; i < sc.n_groups * tri_size(sc.pg); i += nth) w.G[i] = tp[tl.off_G + i];
+    for (int i = tid; i < sc.n_groups * sc.cmax * sc.ldg; i += nth) w.H[i] = tp[tl.off_H + i];
+    for (int i = tid; i < tri_size(sc.ss); i += nth) w.S[i] = tp[tl.off_S + i];
+  } else if (MODE == ADJ_EXACT) {
+    // PCR mode tapes no factor: the exact mode's GMRES preconditioner is the direct factor,
+    // formed here at the taped iterate
+    assemble(sc, w, h);
+    factor(sc, w, h);
+  } else if (sc.pc == PC_BLOCK) {
+    // the PCR operator and preconditioner of the forward pass, at the taped iterate
+    assemble(sc, w, h);
+    factor_blocks(sc, w);
+  } else {
+    pcr_jacobi(sc, w, h);
+  }
   // incoming cotangent: normalisation Jacobian of the output quaternions, then g
   Real* gq = w.lb;      // the best-iterate buffer is free in the adjoint; m_max >= 7 nb
   Real* gu = w.du;
@@ -1421,9 +1756,17 @@ __global__ void __launch_bounds__(128, 3) adjoint_kernel(const DevScene scp, con
       w.rhs[i] = -hR * jm.value();
     }
     __syncthreads();
-    // refined until a correction no longer changes w_lambda at working precision (at most
-    // refine_adj sweeps)
-    schur_solve(sc, w, w.rhs, wl, w.f, w.lt, h, sc.refine_adj, Real(sizeof(Real) == 4 ? 1.2e-7 : 0.0));
+    if (sc.lin == LIN_DIRECT) {
+      // refined until a correction no longer changes w_lambda at working precision (at
+      // most refine_adj sweeps)
+      schur_solve(sc, w, w.rhs, wl, w.f, w.lt, h, sc.refine_adj, Real(sizeof(Real) == 4 ? 1.2e-7 : 0.0));
+    } else {
+      // a single PCR solve with the forward pass's operator and preconditioner (Sec. III-D)
+      int pconv = 0;
+      const int its = pcr_solve_refined<Real>(sc, w, w.rhs, wl, sc.pcr_iters_adj, Real(sc.pcr_rtol_adj), w.f, w.lt,
+                                              w.tmp2, h, &pconv);
+      if (tid == 0 && a.krylov) a.krylov[world] = its | (pconv ? 0 : (1 << 16));
+    }
     // Eq. (19): w_u = -M^-1 (g + J^T w_lambda)
     jt_apply_acc(sc, w, wl, w.f);     // f is free now
     __syncthreads();
@@ -1632,7 +1975,7 @@ template <class Real> size_t ws_used(const DevScene& s) {
   alignas(16) static char probe[16];
   char* base = probe;
   WS<Real> w = ws_carve<Real>(base, s);
-  return (size_t)(reinterpret_cast<char*>(w.scal + 8) - base);
+  return (size_t)(reinterpret_cast<char*>(w.pcr ? w.pcr + 7 * s.m_max : w.scal + 8) - base);
 }
 
 template cudaError_t launch_step<OST_REAL>(const DevScene&, const StepArgs&, int, cudaStream_t);

@@ -15,6 +15,8 @@ enum { ENV_PLANE = 0, ENV_BOX = 1, ENV_HEIGHTMAP = 2 };
 enum { ROW_JOINT = 0, ROW_SERVO = 1, ROW_NORMAL = 2, ROW_FRIC = 3 };
 enum { JOINT_REVOLUTE = 0, JOINT_PRISMATIC = 1 };
 enum { SERVO_VELOCITY = 0, SERVO_POSITION = 1 };
+enum { LIN_DIRECT = 0, LIN_PCR = 1 };     // Schur solve: block-arrowhead factor / PCR
+enum { PC_JACOBI = 0, PC_BLOCK = 1 };     // PCR preconditioner
 
 // Everything a kernel needs to know about the scene and the solver settings.
 // Passed by value as a kernel parameter.
@@ -39,6 +41,11 @@ struct DevScene {
   double tol, delta_rel, kappa, eps, margin;
   int refine;     // iterative-refinement sweeps after each forward (Newton-step) Schur solve
   int refine_adj; // iterative-refinement sweeps after the adjoint's Schur solve
+  // linear solver of Eq. (12): LIN_DIRECT, or LIN_PCR (matrix-free preconditioned conjugate
+  // residual with preconditioner pc; pcr_iters iterations per Newton step; the adjoint's
+  // solve stops at |r| <= pcr_rtol_adj |b| or after pcr_iters_adj iterations)
+  int lin, pc, pcr_iters, pcr_iters_adj;
+  double pcr_rtol_adj;
   // layout caps derived from the scene
   int n_groups;   // bodies that carry contact slots (leaf blocks of the Schur matrix)
   int pg;         // largest leaf block (3 x slots of one body)
@@ -123,7 +130,7 @@ struct AdjArgs {
   void* dL_dkp = nullptr; void* dL_dmass = nullptr; void* dL_dinertia = nullptr;
   void* dL_dmu = nullptr;       // optional: dL/dmu per world (n_worlds entries)
   int mode = 0;                 // 0: the paper's adjoint (frozen W), 1: exact IFT
-  int32_t* krylov = nullptr;    // optional (exact mode): per world GMRES iterations | 1 << 16 if not converged
+  int32_t* krylov = nullptr;    // optional: per world Krylov iterations (GMRES, or the PCR solve) | 1 << 16 if not converged
 };
 
 // Tape record of one world for one step: inputs, returned iterate and the Schur factor

@@ -80,6 +80,9 @@ inline ostrich_status build_scene(const ostrich_scene_desc* d, const ostrich_sol
   // same residuals), so its solves are not refined.
   s.refine = 0;
   s.refine_adj = dtype == OSTRICH_F32 ? 8 : 0;
+  // the direct factor by default; PCR is selected on a context (ostrich_set_linear_solver)
+  s.lin = LIN_DIRECT; s.pc = PC_JACOBI; s.pcr_iters = 16; s.pcr_iters_adj = 256;
+  s.pcr_rtol_adj = dtype == OSTRICH_F32 ? 1e-10 : 1e-12;
   const size_t smem = dtype == OSTRICH_F64 ? ws_bytes<double>(s) : ws_bytes<float>(s);
   const size_t used = dtype == OSTRICH_F64 ? ws_used<double>(s) : ws_used<float>(s);
   if (smem > SMEM_CTA_MAX || used > smem) return OSTRICH_EINVAL;

@@ -20,6 +20,8 @@ LIB_PATH = os.path.join(HERE, "libostrich.so")
 OSTRICH_OK, OSTRICH_EINVAL, OSTRICH_ENOMEM, OSTRICH_ECUDA, OSTRICH_ETAPE = 0, 1, 2, 3, 4
 OSTRICH_F32, OSTRICH_F64 = 0, 1
 ADJ_PAPER, ADJ_EXACT = 0, 1
+LIN_DIRECT, LIN_PCR = 0, 1
+PC_JACOBI, PC_BLOCK = 0, 1
 MAX_BODIES = 8
 MAX_JOINTS = 8
 
@@ -72,6 +74,8 @@ def lib():
         L.ostrich_adjoint.argtypes = [_vp, ctypes.c_int, _vp, ctypes.c_double, _vp, _vp, _vp]
         L.ostrich_adjoint_params.argtypes = [_vp, ctypes.c_int, _vp, ctypes.c_double, _vp, _vp, _vp, _vp, _vp, _vp, _vp]
         L.ostrich_set_adjoint_mode.argtypes = [_vp, ctypes.c_int, _vp]
+        L.ostrich_set_linear_solver.argtypes = [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                                ctypes.c_double]
         L.ostrich_set_adjoint_mode.restype = ctypes.c_int
         L.ostrich_step_list.argtypes = [_vp, _vp, _vp, ctypes.c_double, _vp, _vp, _vp, _vp, _vp, _vp, _vp,
                                         ctypes.c_int, _vp]
@@ -217,6 +221,8 @@ class Context:
         self.nb = scene.n_bodies
         if threads is not None:
             self.set_threads(threads)
+        if getattr(cfg, "linear_solver", LIN_DIRECT) != LIN_DIRECT:
+            self.set_linear_solver(cfg.linear_solver, cfg.precond, cfg.pcr_iters, cfg.pcr_iters_adj, cfg.pcr_rtol_adj)
 
     def _check(self, rc, what):
         if rc != OSTRICH_OK:
@@ -254,6 +260,13 @@ class Context:
         GMRES on the taped factor); krylov_iters: optional int32 device tensor [n_worlds]."""
         self._check(lib().ostrich_set_adjoint_mode(self._h, int(mode), _ptr(krylov_iters)), "ostrich_set_adjoint_mode")
         self.adj_mode = int(mode)
+
+    def set_linear_solver(self, solver, precond=PC_JACOBI, iters=16, adj_iters=256, adj_rtol=0.0):
+        """LIN_DIRECT (block-arrowhead factor, default) or LIN_PCR (matrix-free preconditioned
+        conjugate residual, `iters` per Newton step, preconditioner PC_JACOBI or PC_BLOCK)."""
+        self._check(lib().ostrich_set_linear_solver(self._h, int(solver), int(precond), int(iters), int(adj_iters),
+                                                    float(adj_rtol)), "ostrich_set_linear_solver")
+        self.linear_solver = int(solver)
 
     def ostrich_step_list(self, state_in, controls, h, state_out, worlds, tape_slots=None, impulses=None, ids=None,
                           status=None, iters=None, stream=None):

@@ -122,7 +122,7 @@ class SolverConfig:
     precond: int = 0          # PCR preconditioner: PC_JACOBI or PC_BLOCK
     pcr_iters: int = 16       # PCR iterations per Newton step (Sec. IV-B: 16)
     pcr_iters_adj: int = 256  # at most this many PCR iterations in the adjoint's solve
-    pcr_rtol_adj: float = 0.0  # adjoint PCR stops at |r| <= rtol |b|; 0: 1e-6 (FP32), 1e-12 (FP64)
+    pcr_rtol_adj: float = 0.0  # adjoint PCR stops at |r| <= rtol |b|; 0: 1e-10 (FP32), 1e-12 (FP64)
 
 
 @dataclasses.dataclass

@@ -60,6 +60,7 @@ def test_calls_on_a_null_context_return_einval(lib):
     assert lib.ostrich_adjoint(None, 0, None, 0.1, None, None, None) == OSTRICH_EINVAL
     assert lib.ostrich_adjoint_params(None, 0, None, 0.1, None, None, None, None, None, None, None) == OSTRICH_EINVAL
     assert lib.ostrich_set_adjoint_mode(None, 1, None) == OSTRICH_EINVAL
+    assert lib.ostrich_set_linear_solver(None, 1, 0, 16, 256, 0.0) == OSTRICH_EINVAL
     assert lib.ostrich_step(None, None, None, 0.1, None, None, None, None, None, -1, None) == OSTRICH_EINVAL
     assert lib.ostrich_tape_clear(None) == OSTRICH_EINVAL
 
@@ -80,3 +81,20 @@ def test_noalloc_refuses_heightmap_scenes(lib):
 def test_noalloc_refuses_worlds_beyond_its_array(lib):
     # 9280 B of tape per robot-over-box world: 1807 fit the 16 MiB array, 1808 do not
     assert _noalloc(lib, S.robot_box_scene(), 1808) == OSTRICH_EINVAL
+
+
+@pytest.mark.parametrize("args", [(2, 0, 16, 256, 0.0), (1, 2, 16, 256, 0.0), (1, 0, 0, 256, 0.0),
+                                  (1, 0, 16, 0, 0.0), (1, 1, 16, 256, -1.0)])
+def test_linear_solver_rejects_invalid_settings(lib, args):
+    """ostrich_set_linear_solver: unknown solver or preconditioner, counts below 1 and a
+    negative tolerance are EINVAL; valid settings are accepted (host only, no device
+    work: the context has no tape)."""
+    rc, h = _create(lib, _robot(), tape_slots=0)
+    if rc != 0:
+        pytest.skip("context creation needs a device here")
+    try:
+        assert lib.ostrich_set_linear_solver(h, *args) == OSTRICH_EINVAL
+        assert lib.ostrich_set_linear_solver(h, 1, 1, 16, 256, 0.0) == 0
+        assert lib.ostrich_set_linear_solver(h, 0, 0, 1, 1, 1e-8) == 0
+    finally:
+        lib.ostrich_destroy(h)

@@ -101,22 +101,19 @@ template <class S> struct JGroup {
 template <class S>
 __device__ __forceinline__ void joint_group(const DevScene& sc, int j, const S* qmp, const S* up, const S* qmc,
                                             const S* uc, double h, JGroup<S>& o) {
-  S qpp[7], qpc[7], Rp[9], Rc[9];
+  S qpp[7], qpc[7];
   kin_body<S, S>(qmp, up, h, qpp);
   kin_body<S, S>(qmc, uc, h, qpc);
-  qmat(qpp + 3, Rp);
-  qmat(qpc + 3, Rc);
+  const QuatRot<S> rotp(qpp + 3), rotc(qpc + 3);
   const vec3<S> pp = v3(qpp[0], qpp[1], qpp[2]), pc = v3(qpc[0], qpc[1], qpc[2]);
   const vec3<S> wp = v3(up[3], up[4], up[5]), wc = v3(uc[3], uc[4], uc[5]);
-  JRows<S> jr;
-  joint_rows_geom<S>(sc, j, pp, Rp, pc, Rc, jr);
-  for (int k = 0; k < 5; ++k) {
-    o.lin_p[k] = jr.lin_p[k]; o.lin_c[k] = jr.lin_c[k]; o.c[k] = jr.c[k];
-    o.ang_p[k] = map_Et(jr.ang_p[k], wp, h);
-    o.ang_c[k] = map_Et(jr.ang_c[k], wc, h);
-  }
+  joint_rows_each<S>(sc, j, pp, rotp, pc, rotc, [&](int k, vec3<S> lp, vec3<S> ap, vec3<S> lc, vec3<S> ac, S c) {
+    o.lin_p[k] = lp; o.lin_c[k] = lc; o.c[k] = c;
+    o.ang_p[k] = map_Et(ap, wp, h);
+    o.ang_c[k] = map_Et(ac, wc, h);
+  });
   SRow<S> sr;
-  servo_row_geom<S>(sc, j, pp, Rp, pc, Rc, sr);
+  servo_row_geom<S>(sc, j, pp, rotp, pc, rotc, sr);
   o.sl_p = sr.lin_p; o.sl_c = sr.lin_c;
   o.sa_p = map_Et(sr.ang_p, wp, h);
   o.sa_c = map_Et(sr.ang_c, wc, h);
@@ -127,10 +124,8 @@ __device__ __forceinline__ void joint_group(const DevScene& sc, int j, const S* 
 // The joint coordinate at q- (in S), for a position servo's bias (x(q-) - target)/h.
 template <class S>
 __device__ __forceinline__ S joint_coord_qm(const DevScene& sc, int j, const S* qmp, const S* qmc) {
-  S Rp[9], Rc[9];
-  qmat(qmp + 3, Rp);
-  qmat(qmc + 3, Rc);
-  return joint_coord<S>(sc, j, v3(qmp[0], qmp[1], qmp[2]), Rp, v3(qmc[0], qmc[1], qmc[2]), Rc);
+  return joint_coord<S>(sc, j, v3(qmp[0], qmp[1], qmp[2]), QuatRot<S>(qmp + 3), v3(qmc[0], qmc[1], qmc[2]),
+                        QuatRot<S>(qmc + 3));
 }
 
 // ---------------------------------------------------------------------------
@@ -256,28 +251,38 @@ __device__ Real group_vjp_q(const DevScene& sc, const WS<Real>& w, const ExWS<Re
     return acc.d;
   }
   const int j = grp - sc.n_slots, bp = sc.jp[j], bc = sc.jc[j];
-  D qmp[7], qmc[7], up[6], uc[6];
+  D qmp[7], qmc[7], qpp[7], qpc[7];
   for (int c = 0; c < 7; ++c) {
     qmp[c] = D(w.qm[7 * bp + c], (bp == db && c == dc) ? Real(1) : Real(0));
     qmc[c] = D(w.qm[7 * bc + c], (bc == db && c == dc) ? Real(1) : Real(0));
   }
-  for (int c = 0; c < 6; ++c) { up[c] = D(w.uk[6 * bp + c]); uc[c] = D(w.uk[6 * bc + c]); }
-  JGroup<D> g;
-  joint_group<D>(sc, j, qmp, up, qmc, uc, h, g);
-  const vec3<D> wpl = lift<D>(v3(wu[6 * bp], wu[6 * bp + 1], wu[6 * bp + 2]));
-  const vec3<D> wpa = lift<D>(v3(wu[6 * bp + 3], wu[6 * bp + 4], wu[6 * bp + 5]));
-  const vec3<D> wcl = lift<D>(v3(wu[6 * bc], wu[6 * bc + 1], wu[6 * bc + 2]));
-  const vec3<D> wca = lift<D>(v3(wu[6 * bc + 3], wu[6 * bc + 4], wu[6 * bc + 5]));
+  // the joint's rows as joint_group forms them, each contracted as soon as it is formed
+  kin_body<D, Real>(qmp, w.uk + 6 * bp, h, qpp);
+  kin_body<D, Real>(qmc, w.uk + 6 * bc, h, qpc);
+  const QuatRot<D> rotp(qpp + 3), rotc(qpc + 3);
+  const vec3<D> pp = v3(qpp[0], qpp[1], qpp[2]), pc = v3(qpc[0], qpc[1], qpc[2]);
+  // u+ and the adjoint w_u are constants along q-: kept in the working precision
+  const vec3<Real> wp = v3(w.uk[6 * bp + 3], w.uk[6 * bp + 4], w.uk[6 * bp + 5]);
+  const vec3<Real> wc = v3(w.uk[6 * bc + 3], w.uk[6 * bc + 4], w.uk[6 * bc + 5]);
+  const vec3<Real> wpl = v3(wu[6 * bp], wu[6 * bp + 1], wu[6 * bp + 2]);
+  const vec3<Real> wpa = v3(wu[6 * bp + 3], wu[6 * bp + 4], wu[6 * bp + 5]);
+  const vec3<Real> wcl = v3(wu[6 * bc], wu[6 * bc + 1], wu[6 * bc + 2]);
+  const vec3<Real> wca = v3(wu[6 * bc + 3], wu[6 * bc + 4], wu[6 * bc + 5]);
   const int i0 = w.ints[1] + 5 * j;
   D acc(Real(0));
-  for (int k = 0; k < 5; ++k) {
-    const D Jw = dot3(g.lin_p[k], wpl) + dot3(g.ang_p[k], wpa) + dot3(g.lin_c[k], wcl) + dot3(g.ang_c[k], wca);
-    acc = acc + D(wl[i0 + k]) * g.c[k] / D(hR) - D(hR * w.lk[i0 + k]) * Jw;
-  }
+  joint_rows_each<D>(sc, j, pp, rotp, pc, rotc, [&](int k, vec3<D> lp, vec3<D> ap, vec3<D> lc, vec3<D> ac, D c) {
+    const D Jw = dotm(lp, wpl) + dotm(map_Et(ap, wp, h), wpa) + dotm(lc, wcl) + dotm(map_Et(ac, wc, h), wca);
+    acc = acc + D(wl[i0 + k]) * c / D(hR) - D(hR * w.lk[i0 + k]) * Jw;
+  });
   const int is = servo_row(sc, w, j);
   if (is >= 0) {
-    const D Jw = dot3(g.sl_p, wpl) + dot3(g.sa_p, wpa) + dot3(g.sl_c, wcl) + dot3(g.sa_c, wca);
-    acc = acc + D(wl[is]) * g.sv - D(hR * w.lk[is]) * Jw;
+    SRow<D> sr;
+    servo_row_geom<D>(sc, j, pp, rotp, pc, rotc, sr);
+    const vec3<D> sa_p = map_Et(sr.ang_p, wp, h), sa_c = map_Et(sr.ang_c, wc, h);
+    const D sv = dotm(sr.lin_p, v3(w.uk[6 * bp], w.uk[6 * bp + 1], w.uk[6 * bp + 2])) + dotm(sa_p, wp) +
+                 dotm(sr.lin_c, v3(w.uk[6 * bc], w.uk[6 * bc + 1], w.uk[6 * bc + 2])) + dotm(sa_c, wc);
+    const D Jw = dotm(sr.lin_p, wpl) + dotm(sa_p, wpa) + dotm(sr.lin_c, wcl) + dotm(sa_c, wca);
+    acc = acc + D(wl[is]) * sv - D(hR * w.lk[is]) * Jw;
     // a position target's bias (x(q-) - target)/h holds q- directly
     if (sc.smode[j] == SERVO_POSITION) acc = acc + D(wl[is]) * joint_coord_qm<D>(sc, j, qmp, qmc) / D(hR);
   }

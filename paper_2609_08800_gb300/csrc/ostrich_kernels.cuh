@@ -211,47 +211,94 @@ template <class S, class Real> __device__ __forceinline__ void slot_frame2(const
 // ---------------------------------------------------------------------------
 // joint geometry in any scalar type S, from body positions and rotation matrices
 // ---------------------------------------------------------------------------
+// Body-frame to world rotations for the joint helpers: a rotation matrix (the step's
+// R(q) in shared memory) or a quaternion normalised once (the adjoint's dual numbers, where
+// nine matrix entries per body would cost registers).
+template <class S> struct MatRot {
+  const S* R;
+  __device__ __forceinline__ vec3<S> operator()(vec3<S> v) const { return mat3<S>(R, v); }
+};
+template <class S> struct QuatRot {
+  S w;
+  vec3<S> qv;
+  __device__ __forceinline__ explicit QuatRot(const S* q) {
+    const S inv = S(1) / ssqrt(q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
+    w = q[0] * inv;
+    qv = v3(q[1] * inv, q[2] * inv, q[3] * inv);
+  }
+  // v + w t + qv x t, t = 2 qv x v (the rotation of qrot, with the normalisation done once)
+  __device__ __forceinline__ vec3<S> operator()(vec3<S> v) const {
+    vec3<S> t = cross3(qv, v);
+    t = v3(t.x + t.x, t.y + t.y, t.z + t.z);
+    const vec3<S> c = cross3(qv, t);
+    return v3(v.x + w * t.x + c.x, v.y + w * t.y + c.y, v.z + w * t.z + c.z);
+  }
+};
+
+template <class S> __device__ __forceinline__ vec3<S> cvec(const double* a) { return v3(S(a[0]), S(a[1]), S(a[2])); }
+
 // The five rows of joint j (Eq. (3)): Jacobian parts before the rotation-rate map E and the
-// constraint values.  Revolute: anchor rows (p_p + r_p) - (p_c + r_c) by component, then the
-// alignment rows perp_k,p . axis_c.  Prismatic: b_k . d (b_k = R_p perp_k, d = (p_c + r_c) -
-// (p_p + r_p)), the alignment rows, and the twist lock perp2_p . perp1_c.
+// constraint values, handed row by row (k = 0..4) to f(k, lin_p, ang_p, lin_c, ang_c, c) so
+// that a caller contracts or stores each row without holding all five (each intermediate
+// lives only as long as its rows need it).  rotp / rotc: the parent's / child's rotation.
+// Revolute: anchor rows (p_p + r_p) - (p_c + r_c) by component, then the alignment rows
+// perp_k,p . axis_c.  Prismatic: b_k . d (b_k = R_p perp_k, d = (p_c + r_c) - (p_p + r_p)),
+// the alignment rows, and the twist lock perp2_p . perp1_c.
+template <class S, class RP, class RC, class F>
+__device__ __forceinline__ void joint_rows_each(const DevScene& sc, int j, vec3<S> pp, const RP& rotp, vec3<S> pc,
+                                                const RC& rotc, F&& f) {
+  const vec3<S> z = v3(S(0.0), S(0.0), S(0.0));
+  if (sc.jtype[j] == JOINT_REVOLUTE) {
+    {
+      const vec3<S> rp = rotp(cvec<S>(sc.ap[j])), rc = rotc(cvec<S>(sc.ac[j]));
+      const vec3<S> d = (pc + rc) - (pp + rp);
+      const vec3<S> ex = v3(S(1.0), S(0.0), S(0.0)), ey = v3(S(0.0), S(1.0), S(0.0)), ez = v3(S(0.0), S(0.0), S(1.0));
+      f(0, ex, cross3(rp, ex), scale(ex, S(-1.0)), scale(cross3(rc, ex), S(-1.0)), S(0.0) - d.x);
+      f(1, ey, cross3(rp, ey), scale(ey, S(-1.0)), scale(cross3(rc, ey), S(-1.0)), S(0.0) - d.y);
+      f(2, ez, cross3(rp, ez), scale(ez, S(-1.0)), scale(cross3(rc, ez), S(-1.0)), S(0.0) - d.z);
+    }
+    const vec3<S> aw = rotc(cvec<S>(sc.axc[j]));
+    {
+      const vec3<S> b1 = rotp(cvec<S>(sc.p1[j]));
+      const vec3<S> a1 = cross3(b1, aw);
+      f(3, z, a1, z, scale(a1, S(-1.0)), dot3(b1, aw));
+    }
+    const vec3<S> b2 = rotp(cvec<S>(sc.p2[j]));
+    const vec3<S> a2 = cross3(b2, aw);
+    f(4, z, a2, z, scale(a2, S(-1.0)), dot3(b2, aw));
+  } else {
+    const vec3<S> b1 = rotp(cvec<S>(sc.p1[j])), b2 = rotp(cvec<S>(sc.p2[j]));
+    {
+      const vec3<S> rp = rotp(cvec<S>(sc.ap[j])), rc = rotc(cvec<S>(sc.ac[j]));
+      const vec3<S> d = (pc + rc) - (pp + rp);
+      const vec3<S> dr = d + rp;
+      f(0, scale(b1, S(-1.0)), cross3(b1, dr), b1, cross3(rc, b1), dot3(b1, d));
+      f(1, scale(b2, S(-1.0)), cross3(b2, dr), b2, cross3(rc, b2), dot3(b2, d));
+    }
+    {
+      const vec3<S> aw = rotc(cvec<S>(sc.axc[j]));
+      const vec3<S> a1 = cross3(b1, aw), a2 = cross3(b2, aw);
+      f(2, z, a1, z, scale(a1, S(-1.0)), dot3(b1, aw));
+      f(3, z, a2, z, scale(a2, S(-1.0)), dot3(b2, aw));
+    }
+    const vec3<S> e1 = rotc(cvec<S>(sc.p1[j]));
+    const vec3<S> a3 = cross3(b2, e1);
+    f(4, z, a3, z, scale(a3, S(-1.0)), dot3(b2, e1));
+  }
+}
+
+// The same five rows held in one structure (for callers that need them all at once)
 template <class S> struct JRows {
   vec3<S> lin_p[5], ang_p[5], lin_c[5], ang_c[5];
   S c[5];
 };
 
-template <class S>
-__device__ __forceinline__ void joint_rows_geom(const DevScene& sc, int j, vec3<S> pp, const S* Rp, vec3<S> pc,
-                                                const S* Rc, JRows<S>& o) {
-  const vec3<S> rp = mat3<S>(Rp, v3(S(sc.ap[j][0]), S(sc.ap[j][1]), S(sc.ap[j][2])));
-  const vec3<S> rc = mat3<S>(Rc, v3(S(sc.ac[j][0]), S(sc.ac[j][1]), S(sc.ac[j][2])));
-  const vec3<S> z = v3(S(0.0), S(0.0), S(0.0));
-  const bool rev = sc.jtype[j] == JOINT_REVOLUTE;
-  const vec3<S> d = (pc + rc) - (pp + rp);
-  for (int k = 0; k < 5; ++k) {
-    if (rev && k < 3) {
-      const vec3<S> e = v3(S(k == 0 ? 1.0 : 0.0), S(k == 1 ? 1.0 : 0.0), S(k == 2 ? 1.0 : 0.0));
-      o.lin_p[k] = e; o.ang_p[k] = cross3(rp, e);
-      o.lin_c[k] = scale(e, S(-1.0)); o.ang_c[k] = scale(cross3(rc, e), S(-1.0));
-      o.c[k] = k == 0 ? S(0.0) - d.x : (k == 1 ? S(0.0) - d.y : S(0.0) - d.z);
-    } else if (!rev && k < 2) {
-      const double* pk = k == 0 ? sc.p1[j] : sc.p2[j];
-      const vec3<S> b = mat3<S>(Rp, v3(S(pk[0]), S(pk[1]), S(pk[2])));
-      o.lin_p[k] = scale(b, S(-1.0)); o.ang_p[k] = cross3(b, d + rp);
-      o.lin_c[k] = b; o.ang_c[k] = cross3(rc, b);
-      o.c[k] = dot3(b, d);
-    } else {
-      const int q = rev ? k - 3 : k - 2;        // 0, 1: axis alignment; 2: twist lock
-      const double* pb = q == 0 ? sc.p1[j] : sc.p2[j];
-      const double* pa = q < 2 ? sc.axc[j] : sc.p1[j];
-      const vec3<S> bw = mat3<S>(Rp, v3(S(pb[0]), S(pb[1]), S(pb[2])));
-      const vec3<S> aw = mat3<S>(Rc, v3(S(pa[0]), S(pa[1]), S(pa[2])));
-      const vec3<S> ba = cross3(bw, aw);
-      o.lin_p[k] = z; o.lin_c[k] = z;
-      o.ang_p[k] = ba; o.ang_c[k] = scale(ba, S(-1.0));
-      o.c[k] = dot3(bw, aw);
-    }
-  }
+template <class S, class RP, class RC>
+__device__ __forceinline__ void joint_rows_geom(const DevScene& sc, int j, vec3<S> pp, const RP& rotp, vec3<S> pc,
+                                                const RC& rotc, JRows<S>& o) {
+  joint_rows_each<S>(sc, j, pp, rotp, pc, rotc, [&](int k, vec3<S> lp, vec3<S> ap, vec3<S> lc, vec3<S> ac, S c) {
+    o.lin_p[k] = lp; o.ang_p[k] = ap; o.lin_c[k] = lc; o.ang_c[k] = ac; o.c[k] = c;
+  });
 }
 
 // Servo row of joint j (Eq. (8)): Jacobian parts before E of the joint rate, the relative
@@ -259,16 +306,15 @@ __device__ __forceinline__ void joint_rows_geom(const DevScene& sc, int j, vec3<
 // (prismatic).
 template <class S> struct SRow { vec3<S> lin_p, ang_p, lin_c, ang_c; };
 
-template <class S>
-__device__ __forceinline__ void servo_row_geom(const DevScene& sc, int j, vec3<S> pp, const S* Rp, vec3<S> pc,
-                                               const S* Rc, SRow<S>& o) {
-  const vec3<S> a = mat3<S>(Rp, v3(S(sc.axp[j][0]), S(sc.axp[j][1]), S(sc.axp[j][2])));
+template <class S, class RP, class RC>
+__device__ __forceinline__ void servo_row_geom(const DevScene& sc, int j, vec3<S> pp, const RP& rotp, vec3<S> pc,
+                                               const RC& rotc, SRow<S>& o) {
+  const vec3<S> a = rotp(cvec<S>(sc.axp[j]));
   if (sc.jtype[j] == JOINT_REVOLUTE) {
     o.lin_p = v3(S(0.0), S(0.0), S(0.0)); o.lin_c = o.lin_p;
     o.ang_p = scale(a, S(-1.0)); o.ang_c = a;
   } else {
-    const vec3<S> rp = mat3<S>(Rp, v3(S(sc.ap[j][0]), S(sc.ap[j][1]), S(sc.ap[j][2])));
-    const vec3<S> rc = mat3<S>(Rc, v3(S(sc.ac[j][0]), S(sc.ac[j][1]), S(sc.ac[j][2])));
+    const vec3<S> rp = rotp(cvec<S>(sc.ap[j])), rc = rotc(cvec<S>(sc.ac[j]));
     const vec3<S> d = (pc + rc) - (pp + rp);
     o.lin_p = scale(a, S(-1.0)); o.ang_p = cross3(a, d + rp);
     o.lin_c = a; o.ang_c = cross3(rc, a);
@@ -284,16 +330,16 @@ template <class T> __device__ __forceinline__ dual<T> satan2(dual<T> y, dual<T> 
   return dual<T>(satan2(y.v, x.v), (x.v * y.d - y.v * x.d) / r2);
 }
 
-template <class S>
-__device__ __forceinline__ S joint_coord(const DevScene& sc, int j, vec3<S> pp, const S* Rp, vec3<S> pc, const S* Rc) {
-  const vec3<S> a = mat3<S>(Rp, v3(S(sc.axp[j][0]), S(sc.axp[j][1]), S(sc.axp[j][2])));
+template <class S, class RP, class RC>
+__device__ __forceinline__ S joint_coord(const DevScene& sc, int j, vec3<S> pp, const RP& rotp, vec3<S> pc,
+                                         const RC& rotc) {
+  const vec3<S> a = rotp(cvec<S>(sc.axp[j]));
   if (sc.jtype[j] == JOINT_REVOLUTE) {
-    const vec3<S> f = mat3<S>(Rp, v3(S(sc.p1[j][0]), S(sc.p1[j][1]), S(sc.p1[j][2])));
-    const vec3<S> e = mat3<S>(Rc, v3(S(sc.p1[j][0]), S(sc.p1[j][1]), S(sc.p1[j][2])));
+    const vec3<S> f = rotp(cvec<S>(sc.p1[j]));
+    const vec3<S> e = rotc(cvec<S>(sc.p1[j]));
     return satan2(dot3(e, cross3(a, f)), dot3(e, f));
   }
-  const vec3<S> rp = mat3<S>(Rp, v3(S(sc.ap[j][0]), S(sc.ap[j][1]), S(sc.ap[j][2])));
-  const vec3<S> rc = mat3<S>(Rc, v3(S(sc.ac[j][0]), S(sc.ac[j][1]), S(sc.ac[j][2])));
+  const vec3<S> rp = rotp(cvec<S>(sc.ap[j])), rc = rotc(cvec<S>(sc.ac[j]));
   return dot3(a, (pc + rc) - (pp + rp));
 }
 
@@ -404,8 +450,9 @@ __device__ void world_setup(const DevScene& sc, WS<Real>& w, Src<Real> qmv, Src<
   for (int k = tid; k < sc.n_servo; k += nth) {
     const int j = servo_joint(sc, k), bp = sc.jp[j], bc = sc.jc[j];
     if (sc.smode[j] == SERVO_POSITION) {
-      const Real x = joint_coord<Real>(sc, j, v3(w.qm[7 * bp], w.qm[7 * bp + 1], w.qm[7 * bp + 2]), w.R + 9 * bp,
-                                       v3(w.qm[7 * bc], w.qm[7 * bc + 1], w.qm[7 * bc + 2]), w.R + 9 * bc);
+      const Real x = joint_coord<Real>(sc, j, v3(w.qm[7 * bp], w.qm[7 * bp + 1], w.qm[7 * bp + 2]),
+                                       MatRot<Real>{w.R + 9 * bp},
+                                       v3(w.qm[7 * bc], w.qm[7 * bc + 1], w.qm[7 * bc + 2]), MatRot<Real>{w.R + 9 * bc});
       w.sbc[k] = (x - w.ubar[k]) / Real(h);
     } else {
       w.sbc[k] = -w.ubar[k];
@@ -591,19 +638,18 @@ __device__ Real evaluate(const DevScene& sc, WS<Real>& w, const Real* u, const R
       const int j = it - sc.n_slots;
       const int i0 = mc + 5 * j;
       const int bp = sc.jp[j], bc = sc.jc[j];
-      JRows<Real> jr;
-      joint_rows_geom<Real>(sc, j, v3(w.qp[7 * bp], w.qp[7 * bp + 1], w.qp[7 * bp + 2]), w.R + 9 * bp,
-                            v3(w.qp[7 * bc], w.qp[7 * bc + 1], w.qp[7 * bc + 2]), w.R + 9 * bc, jr);
       const vec3<Real> wp = v3(u[6 * bp + 3], u[6 * bp + 4], u[6 * bp + 5]);
       const vec3<Real> wc = v3(u[6 * bc + 3], u[6 * bc + 4], u[6 * bc + 5]);
-      for (int k = 0; k < 5; ++k) {
-        const vec3<Real> ap_ = map_Et(jr.ang_p[k], wp, h), ac_ = map_Et(jr.ang_c[k], wc, h);
+      joint_rows_each<Real>(sc, j, v3(w.qp[7 * bp], w.qp[7 * bp + 1], w.qp[7 * bp + 2]), MatRot<Real>{w.R + 9 * bp},
+                            v3(w.qp[7 * bc], w.qp[7 * bc + 1], w.qp[7 * bc + 2]), MatRot<Real>{w.R + 9 * bc},
+                            [&](int k, vec3<Real> lp, vec3<Real> ap, vec3<Real> lc, vec3<Real> ac, Real c) {
+        const vec3<Real> ap_ = map_Et(ap, wp, h), ac_ = map_Et(ac, wc, h);
         const int i = i0 + k;
         Real* Jr = w.J + 12 * i;
-        Jr[0] = jr.lin_p[k].x; Jr[1] = jr.lin_p[k].y; Jr[2] = jr.lin_p[k].z; Jr[3] = ap_.x; Jr[4] = ap_.y; Jr[5] = ap_.z;
-        Jr[6] = jr.lin_c[k].x; Jr[7] = jr.lin_c[k].y; Jr[8] = jr.lin_c[k].z; Jr[9] = ac_.x; Jr[10] = ac_.y; Jr[11] = ac_.z;
-        w.r2[i] = jr.c[k] / hR; w.rhat[i] = jr.c[k] / hR; w.C[i] = Real(0);
-      }
+        Jr[0] = lp.x; Jr[1] = lp.y; Jr[2] = lp.z; Jr[3] = ap_.x; Jr[4] = ap_.y; Jr[5] = ap_.z;
+        Jr[6] = lc.x; Jr[7] = lc.y; Jr[8] = lc.z; Jr[9] = ac_.x; Jr[10] = ac_.y; Jr[11] = ac_.z;
+        w.r2[i] = c / hR; w.rhat[i] = c / hR; w.C[i] = Real(0);
+      });
     } else {
       // k-th servo, Eq. (8): J_c u + alpha lambda_c + b_c
       const int k = it - sc.n_slots - sc.nj;
@@ -611,8 +657,8 @@ __device__ Real evaluate(const DevScene& sc, WS<Real>& w, const Real* u, const R
       const int i = mc + 5 * sc.nj + k;
       const int bp = sc.jp[j], bc = sc.jc[j];
       SRow<Real> sr;
-      servo_row_geom<Real>(sc, j, v3(w.qp[7 * bp], w.qp[7 * bp + 1], w.qp[7 * bp + 2]), w.R + 9 * bp,
-                           v3(w.qp[7 * bc], w.qp[7 * bc + 1], w.qp[7 * bc + 2]), w.R + 9 * bc, sr);
+      servo_row_geom<Real>(sc, j, v3(w.qp[7 * bp], w.qp[7 * bp + 1], w.qp[7 * bp + 2]), MatRot<Real>{w.R + 9 * bp},
+                           v3(w.qp[7 * bc], w.qp[7 * bc + 1], w.qp[7 * bc + 2]), MatRot<Real>{w.R + 9 * bc}, sr);
       const vec3<Real> wp = v3(u[6 * bp + 3], u[6 * bp + 4], u[6 * bp + 5]);
       const vec3<Real> wc = v3(u[6 * bc + 3], u[6 * bc + 4], u[6 * bc + 5]);
       const vec3<Real> ap_ = map_Et(sr.ang_p, wp, h), ac_ = map_Et(sr.ang_c, wc, h);

@@ -58,6 +58,8 @@ template <class S> __device__ __forceinline__ vec3<S> cross3(vec3<S> a, vec3<S> 
   return v3(a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x);
 }
 template <class S, class T> __device__ __forceinline__ vec3<S> lift(vec3<T> a) { return v3(S(a.x), S(a.y), S(a.z)); }
+// a . b with b of another scalar type (a dual vector against a constant one)
+template <class S, class T> __device__ __forceinline__ S dotm(vec3<S> a, vec3<T> b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
 
 // Rotate v by the normalised quaternion q/|q| = (w, x, y, z):  v + w t + qv x t, t = 2 qv x v.
 template <class S> __device__ __forceinline__ vec3<S> qrot(const S* q, vec3<S> v) {

@@ -267,7 +267,8 @@ void ostrich_destroy(ostrich_ctx* ctx);
  *
  * EINVAL if n_worlds times the scene's per-world tape record exceeds the array (the
  * record is ostrich_tape_bytes / n_worlds of an FP32 context for the same scene: 9280 B
- * for the four-wheel robot over a box, so at most 1807 worlds per call), for heightmap
+ * for the four-wheel robot over a box, so at most 1807 worlds per call; see
+ * ostrich_noalloc_capacity), for heightmap
  * scenes (env OSTRICH_ENV_HEIGHTMAP: the heights would need a device copy), or on the
  * same argument errors as ostrich_create / ostrich_step; ECUDA if a launch fails.
  * The first call on a device resolves the array's device address on that device (with
@@ -278,6 +279,14 @@ void ostrich_destroy(ostrich_ctx* ctx);
  * overlap on the GPU (different streams, or host threads) race on the array: order
  * them on one stream. */
 #define OSTRICH_NOALLOC_SCRATCH_BYTES (16u << 20)
+
+/* Capacity of ostrich_step_adjoint_noalloc for a scene: *max_worlds receives how many
+ * worlds one call accepts (the array divided by the scene's FP32 per-world tape record),
+ * *record_bytes (may be NULL) that record's size.  Host only, touches no device.  EINVAL
+ * for a scene the entry point refuses (heightmap, or a description ostrich_create would
+ * refuse) or a NULL max_worlds. */
+ostrich_status ostrich_noalloc_capacity(const ostrich_scene_desc* scene, const ostrich_solver_cfg* cfg,
+                                        int32_t* max_worlds, size_t* record_bytes);
 ostrich_status ostrich_step_adjoint_noalloc(const ostrich_scene_desc* scene, const ostrich_solver_cfg* cfg,
                                             int n_worlds, int ld, const float* state_in, const float* controls,
                                             double h, float* state_out, const float* dL_dstate_next,

@@ -79,3 +79,15 @@ extern "C" ostrich_status ostrich_step_adjoint_noalloc(const ostrich_scene_desc*
   if (ost::launch_adjoint<float>(s, b, 64, st) != cudaSuccess) return OSTRICH_ECUDA;
   return OSTRICH_OK;
 }
+
+extern "C" ostrich_status ostrich_noalloc_capacity(const ostrich_scene_desc* scene, const ostrich_solver_cfg* cfg,
+                                                   int32_t* max_worlds, size_t* record_bytes) {
+  if (!scene || !cfg || !max_worlds) return OSTRICH_EINVAL;
+  if (scene->env == OSTRICH_ENV_HEIGHTMAP) return OSTRICH_EINVAL;
+  ost::DevScene s;
+  if (ost::build_scene(scene, cfg, OSTRICH_F32, s) != OSTRICH_OK) return OSTRICH_EINVAL;
+  const size_t rec = (size_t)ost::tape_layout(s).total * sizeof(float);
+  *max_worlds = (int32_t)((size_t)OSTRICH_NOALLOC_SCRATCH_BYTES / rec);
+  if (record_bytes) *record_bytes = rec;
+  return OSTRICH_OK;
+}

@@ -90,6 +90,8 @@ def lib():
         L.ostrich_last_error.argtypes = [_vp]
         L.ostrich_last_error.restype = ctypes.c_char_p
         L.ostrich_destroy.argtypes = [_vp]
+        L.ostrich_noalloc_capacity.argtypes = [ctypes.POINTER(SceneDesc), ctypes.POINTER(SolverCfg),
+                                               ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_size_t)]
         L.ostrich_step_adjoint_noalloc.argtypes = [ctypes.POINTER(SceneDesc), ctypes.POINTER(SolverCfg), ctypes.c_int,
                                                    ctypes.c_int, _vp, _vp, ctypes.c_double, _vp, _vp, _vp, _vp, _vp]
         L.ostrich_probe_ffma.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, _vp, ctypes.POINTER(ctypes.c_size_t),
@@ -178,6 +180,16 @@ def ostrich_step_adjoint_noalloc(scene, cfg, n_worlds, state_in, controls, h, st
                                             _ptr(dL_dstate), _ptr(dL_dcontrols), _stream(stream))
     if rc != OSTRICH_OK:
         raise RuntimeError(f"ostrich_step_adjoint_noalloc failed with status {rc}")
+
+
+def noalloc_capacity(scene, cfg=None):
+    """(max worlds per ostrich_step_adjoint_noalloc call, per-world tape record in bytes)."""
+    d, c = scene_desc(scene), solver_cfg(cfg or S.SolverConfig())
+    mw, rb = ctypes.c_int32(), ctypes.c_size_t()
+    rc = lib().ostrich_noalloc_capacity(ctypes.byref(d), ctypes.byref(c), ctypes.byref(mw), ctypes.byref(rb))
+    if rc != OSTRICH_OK:
+        raise ValueError(f"ostrich_noalloc_capacity refused the scene (status {rc})")
+    return int(mw.value), int(rb.value)
 
 
 def probe_ffma(blocks_per_sm=2, iters=40000, reps=10, stream=None):

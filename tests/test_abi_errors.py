@@ -98,3 +98,14 @@ def test_linear_solver_rejects_invalid_settings(lib, args):
         assert lib.ostrich_set_linear_solver(h, 0, 0, 1, 1, 1e-8) == 0
     finally:
         lib.ostrich_destroy(h)
+
+
+def test_noalloc_capacity_of_the_robot_and_refusals(lib):
+    """The capacity helper: 9280 B per robot-over-box world, 1807 worlds in the 16 MiB
+    array; heightmap scenes refused (host only)."""
+    mw, rb = M.noalloc_capacity(S.robot_box_scene())
+    assert (mw, rb) == (1807, 9280)
+    assert mw * rb <= 16 << 20 < (mw + 1) * rb
+    with pytest.raises(ValueError):
+        M.noalloc_capacity(S.terrain_scene(n=16))
+    assert lib.ostrich_noalloc_capacity(None, None, None, None) == OSTRICH_EINVAL

@@ -976,6 +976,29 @@ template <class Real> __device__ void chol_inv_inplace4(Real* A, int n, Real* co
   if (k < n) chol_round<1>(A, n, k, colbuf);
 }
 
+// Two-accumulator dot products (even and odd terms apart, halving the dependent chain):
+// a contiguous one, and one down a column of a packed triangle (element (l, c), l = c0 ..
+// n-1, at tri(l, c), the offset growing by l + 1 per row).
+template <class Real> __device__ __forceinline__ Real dot2c(const Real* a, const Real* b, int n) {
+  Real s0 = Real(0), s1 = Real(0);
+  int l = 0;
+  for (; l + 1 < n; l += 2) { s0 += a[l] * b[l]; s1 += a[l + 1] * b[l + 1]; }
+  if (l < n) s0 += a[l] * b[l];
+  return s0 + s1;
+}
+template <class Real> __device__ __forceinline__ Real dot2col(const Real* T, int c, int c0, int n, const Real* b) {
+  Real s0 = Real(0), s1 = Real(0);
+  int l = c0, off = tri(c0, c);
+  for (; l + 1 < n; l += 2) {
+    s0 += T[off] * b[l];
+    off += l + 1;
+    s1 += T[off] * b[l + 1];
+    off += l + 2;
+  }
+  if (l < n) s0 += T[off] * b[l];
+  return s0 + s1;
+}
+
 // Block-arrowhead factorisation kept in inverse form for row-parallel solves:
 //   Li_g = L_g^-1 with L_g L_g^T = A_g (contact groups; stored in G, packed),
 //   F_g = E_g L_g^-T (coupled separator rows; stored in H),
@@ -1004,9 +1027,7 @@ template <class Real> __device__ void factor(const DevScene& sc, WS<Real>& w, do
     Real* Fb = w.H + g * cm * ldg;
     for (int e = tid; e < cnt; e += nth) {
       const int k = e / n, j = e - k * n;
-      Real acc = 0;
-      for (int l = 0; l <= j; ++l) acc += Eb[k * ldg + l] * Lb[tri(j, l)];
-      Fb[k * ldg + j] = acc;
+      Fb[k * ldg + j] = dot2c(Eb + k * ldg, Lb + tri(j, 0), j + 1);
     }
   }
   __syncthreads();
@@ -1020,9 +1041,7 @@ template <class Real> __device__ void factor(const DevScene& sc, WS<Real>& w, do
       const int k1 = e / nc, k2 = e - k1 * nc;
       if (k2 > k1) continue;
       const int a = sc.cpl_row[g][k1], b = sc.cpl_row[g][k2];
-      Real acc = 0;
-      for (int j = 0; j < n; ++j) acc += Fb[k1 * ldg + j] * Fb[k2 * ldg + j];
-      w.S[a >= b ? tri(a, b) : tri(b, a)] -= acc;
+      w.S[a >= b ? tri(a, b) : tri(b, a)] -= dot2c(Fb + k1 * ldg, Fb + k2 * ldg, n);
     }
     __syncthreads();
   }
@@ -1039,10 +1058,7 @@ template <class Real> __device__ void arrow_solve(const DevScene& sc, WS<Real>& 
   // y_g = Li_g b_g
   for (int r = tid; r < mc; r += nth) {
     const int g = w.rgrp[r], r0 = w.g0[g], i = r - r0;
-    const Real* Li = w.G + g * gstr + tri(i, 0);
-    Real acc = 0;
-    for (int l = 0; l <= i; ++l) acc += Li[l] * v[r0 + l];
-    y[r] = acc;
+    y[r] = dot2c(w.G + g * gstr + tri(i, 0), v + r0, i + 1);
   }
   __syncthreads();
   // b_s' = b_s - sum_g F_g y_g
@@ -1050,43 +1066,36 @@ template <class Real> __device__ void arrow_solve(const DevScene& sc, WS<Real>& 
     Real acc = v[mc + a];
     for (int pa = 0; pa < sc.sep_n[a]; ++pa) {
       const int g = sc.sep_g[a][pa];
-      const Real* f = w.H + g * cm * ldg + sc.sep_k[a][pa] * ldg;
-      for (int j = 0; j < w.gn[g]; ++j) acc -= f[j] * y[w.g0[g] + j];
+      acc -= dot2c(w.H + g * cm * ldg + sc.sep_k[a][pa] * ldg, y + w.g0[g], w.gn[g]);
     }
     z[a] = acc;
   }
   __syncthreads();
   // y_s = Lsi b_s'
-  for (int a = tid; a < ss; a += nth) {
-    const Real* La = w.S + tri(a, 0);
-    Real acc = 0;
-    for (int b = 0; b <= a; ++b) acc += La[b] * z[b];
-    y[mc + a] = acc;
-  }
+  for (int a = tid; a < ss; a += nth) y[mc + a] = dot2c(w.S + tri(a, 0), z, a + 1);
   __syncthreads();
   // x_s = Lsi^T y_s
-  for (int a = tid; a < ss; a += nth) {
-    Real acc = 0;
-    for (int b = a; b < ss; ++b) acc += w.S[tri(b, a)] * y[mc + b];
-    v[mc + a] = acc;
-  }
+  for (int a = tid; a < ss; a += nth) v[mc + a] = dot2col(w.S, a, a, ss, y + mc);
   __syncthreads();
   // r_g = y_g - F_g^T x_s
   for (int r = tid; r < mc; r += nth) {
     const int g = w.rgrp[r], i = r - w.g0[g];
     const Real* Fb = w.H + g * cm * ldg;
-    Real acc = y[r];
-    for (int k = 0; k < sc.cpl_n[g]; ++k) acc -= Fb[k * ldg + i] * v[mc + sc.cpl_row[g][k]];
-    z[r] = acc;
+    Real s0 = y[r], s1 = Real(0);
+    const int nc = sc.cpl_n[g];
+    int k = 0;
+    for (; k + 1 < nc; k += 2) {
+      s0 -= Fb[k * ldg + i] * v[mc + sc.cpl_row[g][k]];
+      s1 -= Fb[(k + 1) * ldg + i] * v[mc + sc.cpl_row[g][k + 1]];
+    }
+    if (k < nc) s0 -= Fb[k * ldg + i] * v[mc + sc.cpl_row[g][k]];
+    z[r] = s0 + s1;
   }
   __syncthreads();
   // x_g = Li_g^T r_g
   for (int r = tid; r < mc; r += nth) {
     const int g = w.rgrp[r], r0 = w.g0[g], i = r - r0, n = w.gn[g];
-    const Real* Lb = w.G + g * gstr;
-    Real acc = 0;
-    for (int l = i; l < n; ++l) acc += Lb[tri(l, i)] * z[r0 + l];
-    v[r] = acc;
+    v[r] = dot2col(w.G + g * gstr, i, i, n, z + r0);
   }
   __syncthreads();
 }

@@ -744,17 +744,28 @@ template <class Real> __device__ void assemble(const DevScene& sc, WS<Real>& w, 
     const int ti = w.meta[4 * r] & 15, si = w.meta[4 * r] >> 4;
     Real Yr[12];
     minv_row(sc, w, r, Yr);
-    for (int jj = r0; jj <= r; ++jj) {
-      const int j = jj - r0;
-      Real v = hR * rowdot(w.J + 12 * jj, 0, Yr, 0);
-      if (jj == r) v += w.C[r] + delta;
-      if (ti == ROW_FRIC && (w.meta[4 * jj] & 15) == ROW_FRIC && w.ref[r] == w.ref[jj]) {
-        const Real* rd = w.srad + 3 * w.ref[r];
-        const int sj = w.meta[4 * jj] >> 4;
-        v += (si == 1 && sj == 1) ? rd[0] : ((si == 2 && sj == 2) ? rd[2] : rd[1]);
-      }
-      Gb[tri(i, j)] = v;
+    // row i of the group block: h J M^-1 J^T for every column, then the diagonal and the
+    // radial terms of the row's own contact (friction rows of one slot are adjacent)
+    Real* Gi = Gb + tri(i, 0);
+    int jj = r0;
+    for (; jj + 1 <= r; jj += 2) {
+      const Real v0 = hR * rowdot(w.J + 12 * jj, 0, Yr, 0);
+      const Real v1 = hR * rowdot(w.J + 12 * (jj + 1), 0, Yr, 0);
+      Gi[jj - r0] = v0;
+      Gi[jj + 1 - r0] = v1;
     }
+    if (jj <= r) Gi[jj - r0] = hR * rowdot(w.J + 12 * jj, 0, Yr, 0);
+    Real dg = Gi[i] + (w.C[r] + delta);
+    if (ti == ROW_FRIC) {
+      const Real* rd = w.srad + 3 * w.ref[r];
+      if (si == 1) {
+        dg += rd[0];
+      } else {
+        dg += rd[2];
+        Gi[i - 1] += rd[1];
+      }
+    }
+    Gi[i] = dg;
     Real* Eb = w.E + g * sc.cmax * ldg;
     for (int k = 0; k < sc.cpl_n[g]; ++k) {
       const int row = mc + sc.cpl_row[g][k];

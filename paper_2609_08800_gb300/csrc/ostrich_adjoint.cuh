@@ -61,8 +61,9 @@ __device__ __forceinline__ void contact_group(const DevScene& sc, const WS<Real>
   const vec3<S> wk = v3(u6[3], u6[4], u6[5]);
   const vec3<S> ul = v3(u6[0], u6[1], u6[2]);
   o.dir[0] = n; o.dir[1] = t1; o.dir[2] = t2;
+  const MapE<S> Ek(wk, h);
   for (int k = 0; k < 3; ++k) {
-    o.ang[k] = map_Et(cross3(lev, o.dir[k]), wk, h);
+    o.ang[k] = Ek(cross3(lev, o.dir[k]));
     o.vel[k] = dot3(o.dir[k], ul) + dot3(o.ang[k], wk);
   }
   o.cn = dot3(n, x) - d;
@@ -107,16 +108,17 @@ __device__ __forceinline__ void joint_group(const DevScene& sc, int j, const S* 
   const QuatRot<S> rotp(qpp + 3), rotc(qpc + 3);
   const vec3<S> pp = v3(qpp[0], qpp[1], qpp[2]), pc = v3(qpc[0], qpc[1], qpc[2]);
   const vec3<S> wp = v3(up[3], up[4], up[5]), wc = v3(uc[3], uc[4], uc[5]);
+  const MapE<S> Ep(wp, h), Ec(wc, h);
   joint_rows_each<S>(sc, j, pp, rotp, pc, rotc, [&](int k, vec3<S> lp, vec3<S> ap, vec3<S> lc, vec3<S> ac, S c) {
     o.lin_p[k] = lp; o.lin_c[k] = lc; o.c[k] = c;
-    o.ang_p[k] = map_Et(ap, wp, h);
-    o.ang_c[k] = map_Et(ac, wc, h);
+    o.ang_p[k] = Ep(ap);
+    o.ang_c[k] = Ec(ac);
   });
   SRow<S> sr;
   servo_row_geom<S>(sc, j, pp, rotp, pc, rotc, sr);
   o.sl_p = sr.lin_p; o.sl_c = sr.lin_c;
-  o.sa_p = map_Et(sr.ang_p, wp, h);
-  o.sa_c = map_Et(sr.ang_c, wc, h);
+  o.sa_p = Ep(sr.ang_p);
+  o.sa_c = Ec(sr.ang_c);
   o.sv = dot3(o.sl_p, v3(up[0], up[1], up[2])) + dot3(o.sa_p, wp) + dot3(o.sl_c, v3(uc[0], uc[1], uc[2])) +
          dot3(o.sa_c, wc);
 }
@@ -270,15 +272,16 @@ __device__ Real group_vjp_q(const DevScene& sc, const WS<Real>& w, const ExWS<Re
   const vec3<Real> wca = v3(wu[6 * bc + 3], wu[6 * bc + 4], wu[6 * bc + 5]);
   const int i0 = w.ints[1] + 5 * j;
   D acc(Real(0));
+  const MapE<Real> Ep(wp, h), Ec(wc, h);
   joint_rows_each<D>(sc, j, pp, rotp, pc, rotc, [&](int k, vec3<D> lp, vec3<D> ap, vec3<D> lc, vec3<D> ac, D c) {
-    const D Jw = dotm(lp, wpl) + dotm(map_Et(ap, wp, h), wpa) + dotm(lc, wcl) + dotm(map_Et(ac, wc, h), wca);
+    const D Jw = dotm(lp, wpl) + dotm(Ep(ap), wpa) + dotm(lc, wcl) + dotm(Ec(ac), wca);
     acc = acc + D(wl[i0 + k]) * c / D(hR) - D(hR * w.lk[i0 + k]) * Jw;
   });
   const int is = servo_row(sc, w, j);
   if (is >= 0) {
     SRow<D> sr;
     servo_row_geom<D>(sc, j, pp, rotp, pc, rotc, sr);
-    const vec3<D> sa_p = map_Et(sr.ang_p, wp, h), sa_c = map_Et(sr.ang_c, wc, h);
+    const vec3<D> sa_p = Ep(sr.ang_p), sa_c = Ec(sr.ang_c);
     const D sv = dotm(sr.lin_p, v3(w.uk[6 * bp], w.uk[6 * bp + 1], w.uk[6 * bp + 2])) + dotm(sa_p, wp) +
                  dotm(sr.lin_c, v3(w.uk[6 * bc], w.uk[6 * bc + 1], w.uk[6 * bc + 2])) + dotm(sa_c, wc);
     const D Jw = dotm(sr.lin_p, wpl) + dotm(sa_p, wpa) + dotm(sr.lin_c, wcl) + dotm(sa_c, wca);

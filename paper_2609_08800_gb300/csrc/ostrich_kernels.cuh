@@ -582,8 +582,9 @@ __device__ Real evaluate(const DevScene& sc, WS<Real>& w, const Real* u, const R
       vec3<Real> wk = v3(u[6 * b + 3], u[6 * b + 4], u[6 * b + 5]);
       vec3<Real> dirs[3] = {n, t1, t2};
       Real vel[3];
+      const MapE<Real> Ek(wk, h);
       for (int k = 0; k < 3; ++k) {
-        vec3<Real> ang = map_Et(cross3(lev, dirs[k]), wk, h);
+        vec3<Real> ang = Ek(cross3(lev, dirs[k]));
         Real* Jr = w.J + 12 * (i + k);
         Jr[0] = dirs[k].x; Jr[1] = dirs[k].y; Jr[2] = dirs[k].z; Jr[3] = ang.x; Jr[4] = ang.y; Jr[5] = ang.z;
         for (int q = 6; q < 12; ++q) Jr[q] = 0;
@@ -640,10 +641,11 @@ __device__ Real evaluate(const DevScene& sc, WS<Real>& w, const Real* u, const R
       const int bp = sc.jp[j], bc = sc.jc[j];
       const vec3<Real> wp = v3(u[6 * bp + 3], u[6 * bp + 4], u[6 * bp + 5]);
       const vec3<Real> wc = v3(u[6 * bc + 3], u[6 * bc + 4], u[6 * bc + 5]);
+      const MapE<Real> Ep(wp, h), Ec(wc, h);
       joint_rows_each<Real>(sc, j, v3(w.qp[7 * bp], w.qp[7 * bp + 1], w.qp[7 * bp + 2]), MatRot<Real>{w.R + 9 * bp},
                             v3(w.qp[7 * bc], w.qp[7 * bc + 1], w.qp[7 * bc + 2]), MatRot<Real>{w.R + 9 * bc},
                             [&](int k, vec3<Real> lp, vec3<Real> ap, vec3<Real> lc, vec3<Real> ac, Real c) {
-        const vec3<Real> ap_ = map_Et(ap, wp, h), ac_ = map_Et(ac, wc, h);
+        const vec3<Real> ap_ = Ep(ap), ac_ = Ec(ac);
         const int i = i0 + k;
         Real* Jr = w.J + 12 * i;
         Jr[0] = lp.x; Jr[1] = lp.y; Jr[2] = lp.z; Jr[3] = ap_.x; Jr[4] = ap_.y; Jr[5] = ap_.z;

@@ -107,12 +107,23 @@ template <class S, class U> __device__ __forceinline__ void kin_body(const S* qm
 
 // Angular part of a row Jacobian mapped through the rotation-rate map of Eq. (1):
 // E^T a with E = (I + h/2 [wk]x) / (1 + (h/2)^2 |wk|^2).
+// The same map with its scalar 1 / (1 + (h/2)^2 |wk|^2) formed once, for the rows of one
+// body that share wk (the quotient is the costly part).
+template <class T> struct MapE {
+  vec3<T> wk;
+  T hh, inv;
+  __device__ __forceinline__ MapE(vec3<T> w, double h) : wk(w) {
+    hh = T(0.5 * h);
+    const T den = T(1) + hh * hh * (wk.x * wk.x + wk.y * wk.y + wk.z * wk.z);
+    inv = T(1) / den;
+  }
+  template <class S> __device__ __forceinline__ vec3<S> operator()(vec3<S> a) const {
+    const vec3<S> c = cross3(a, lift<S>(wk));
+    return v3((a.x + c.x * hh) * inv, (a.y + c.y * hh) * inv, (a.z + c.z * hh) * inv);
+  }
+};
 template <class S, class T> __device__ __forceinline__ vec3<S> map_Et(vec3<S> a, vec3<T> wk, double h) {
-  T hh = T(0.5 * h);
-  T den = T(1) + hh * hh * (wk.x * wk.x + wk.y * wk.y + wk.z * wk.z);
-  T inv = T(1) / den;
-  vec3<S> c = cross3(a, lift<S>(wk));
-  return v3((a.x + c.x * hh) * inv, (a.y + c.y * hh) * inv, (a.z + c.z * hh) * inv);
+  return MapE<T>(wk, h)(a);
 }
 
 // ---------------------------------------------------------------------------

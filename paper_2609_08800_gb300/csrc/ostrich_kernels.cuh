@@ -1517,7 +1517,17 @@ __device__ __forceinline__ void step_world(const DevScene& sc, WS<Real>& w, cons
   int best_k = -1, k = 0, conv = 0;
   const Real tol2 = Real(sc.tol) * Real(sc.tol);
   const int n_alpha = sc.ls ? 4 : 1;
-  for (k = 0; k < sc.budget; ++k) {
+  // A NaN merit at the warm start (a non-finite input, or an input that has blown up)
+  // makes every Newton step NaN: the iterate is set to NaN at once instead of after the
+  // whole budget of NaN iterations, and the step returns it with status bits 1 and 2.
+  const bool nan0 = !(merit == merit);
+  if (nan0) {
+    const Real qnan = Real(NAN);
+    for (int i = tid; i < 6 * nb; i += nth) w.uk[i] = qnan;
+    for (int i = tid; i < m; i += nth) w.lk[i] = qnan;
+    __syncthreads();
+  }
+  for (k = 0; k < sc.budget && !nan0; ++k) {
     if (k >= sc.kmin && merit < best) {
       best = merit; best_k = k;
       for (int i = tid; i < 6 * nb; i += nth) w.ub[i] = w.uk[i];

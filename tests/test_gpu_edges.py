@@ -100,10 +100,20 @@ def test_non_finite_world_is_flagged_and_isolated(M):
     cfg = S.SolverConfig()
     out, status, _, _ = _step(M, sc, cfg, bad, ub, dtype="f32")
     ref, status_ref, _, _ = _step(M, sc, cfg, st, ub, dtype="f32")
-    assert int(status[5]) & 2
+    assert int(status[5]) & 3 == 3                   # not converged, non-finite
+    assert not torch.isfinite(out[7 * sc.n_bodies:13 * sc.n_bodies, 5]).any()
     others = [w for w in range(W) if w != 5]
     assert torch.equal(out[:, others], ref[:, others])
     assert torch.equal(status[others], status_ref[others])
+    # the NaN warm start ends the step at once: no Newton iterations, a NaN iterate
+    ctx = M.Context(sc, cfg, W, dtype="f32", tape_slots=0)
+    it = torch.zeros(W, dtype=torch.int32, device="cuda")
+    s_in = torch.tensor(bad, dtype=torch.float32, device="cuda")
+    ctx.ostrich_step(s_in, torch.tensor(ub, dtype=torch.float32, device="cuda"), H, torch.empty_like(s_in),
+                     None, None, None, it)
+    torch.cuda.synchronize()
+    assert int(it[5]) & 0xFFFF == 0
+    ctx.close()
 
 
 def test_list_skips_out_of_range_entries(M):

@@ -4,7 +4,7 @@ The CUDA path solves J_F^T w = [-g; 0] with the full Jacobian of the residual in
 (u+, lambda+) by GMRES preconditioned with the taped paper-mode factor; the oracle forms
 the same Jacobian densely with dual numbers and solves it by LU.  Both are taken at the
 CUDA path's returned iterate (oracle_adjoint_at, mode exact).  Tolerances: FP64 1e-6 and
-FP32 1e-3 of the largest entry (the benchmark spec's adjoint tolerance); the Krylov solve
+FP32 1e-3 of the largest entry (the FP32 adjoint tolerance of the parity tests); the Krylov solve
 must converge in every world.  The implicit-function theorem holds at a root of the
 residual: away from one the Jacobian depends on how the rows are scaled (the oracle
 differentiates its merit-weighted rows, the CUDA path the Newton rows), so the worlds

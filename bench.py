@@ -316,7 +316,7 @@ def run_ours(args, rank, world_size, local_rank):
 
 
 def run_optimisation(args, torch, rank, world_size):
-    """Config 3 as stated: the robot over the box obstacle, args.worlds worlds per GPU, FP32,
+    """The optimisation workload: the robot over the box obstacle, args.worlds worlds per GPU, FP32,
     8-knot wheel-velocity splines per world (seeded), horizon T = 100 at h = 0.1, rollout
     through the autograd.Function with checkpoints every 10 steps (the backward recomputes
     each segment into the tape, then sweeps the adjoint back through it), loss = squared
@@ -672,7 +672,7 @@ def run_terrain(args, torch):
 
 
 def run_serving(args, torch):
-    """Config 5: a seeded Poisson stream (mean args.serve_rate req/s over args.serve_seconds of
+    """The serving workload: a seeded Poisson stream (mean args.serve_rate req/s over args.serve_seconds of
     arrivals; 1-512 worlds log-uniform; horizon 20-200 steps; box-drop, robot-over-box and
     mesh-terrain scenes; half forward-only, half forward+adjoint) served by continuous
     batching, then the same stream by a FIFO queue of batched requests and by the plain
@@ -822,7 +822,7 @@ def dist_max(x):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20, help="timed optimisation iterations (config 3: 20)")
+    ap.add_argument("--steps", type=int, default=20, help="timed optimisation iterations (Adam iterations on the spline knots)")
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--worlds", type=int, default=8192)

@@ -14,7 +14,7 @@ the bound of its class (bounds from a 1024-world measurement, in brackets):
 
   contact index sets      all worlds, bit-exact;
   A both converged        state within 1e-4 of max(|x|, 1), impulses within 1e-3 of the
-                          step's largest impulse (north-star tolerances) [1e-5, 3.8e-4];
+                          step's largest impulse (the parity tolerances) [1e-5, 3.8e-4];
   B FP32 budget, oracle   the FP32 stall: the exact residual (the oracle's residual
     converged             function at the CUDA iterate) at most 1e-3 m/s, 10 x tol
                           [5.9e-4]; state within 1e-4 of the oracle's solution [8.6e-6];

@@ -12,7 +12,7 @@ compared are those whose returned iterate is a solution -- converged in FP64, an
 residual (the oracle's residual function at the CUDA iterate) of at most 3e-4 m/s in
 FP32, the FP32 floor the other parity tests use.
 
-Pins of the exact mode beyond the oracle: the box drop of config 1 gives dx_T/dv0 = h
+Pins of the exact mode beyond the oracle: the 20-step box drop (v0 from seed 0) gives dx_T/dv0 = h
 through a 20-step rollout (the paper's frozen-W adjoint gives 0.69 h), and dL/dmu of a
 sliding box is -g h.
 """
@@ -130,8 +130,8 @@ def test_exact_adjoint_box_fp64(M):
     _exact_vs_oracle(M, sc, cfg, st, np.zeros((0, W)), "f64", 1e-6, seed=2)
 
 
-def test_config1_rollout_gradient_is_h(M):
-    """Config 1: box 0.4 x 0.4 x 0.2 m, 10 kg, dropped from 0.05 m with v0 from seed 0,
+def test_box_drop_rollout_gradient_is_h(M):
+    """The box-drop rollout: box 0.4 x 0.4 x 0.2 m, 10 kg, dropped from 0.05 m with v0 from seed 0,
     FP64, T = 20, Newton tol 1e-10; loss x_T.  The exact adjoint swept back through the
     rollout gives dx_T/dv0 = h (the box slides h max(0, v0 - 0.3848) and stops in step
     2); the paper's frozen-W adjoint gives the landing step's sliding ratio times h."""
@@ -152,7 +152,7 @@ def test_config1_rollout_gradient_is_h(M):
             g, _ = ctx.adjoint(t, g, H)
         grads[mode] = float(g[7, 0])
         ctx.close()
-    print(f"config 1 dx_T/dv0: exact {grads[M.ADJ_EXACT]:.9f}, paper {grads[M.ADJ_PAPER]:.6f}")
+    print(f"box drop dx_T/dv0: exact {grads[M.ADJ_EXACT]:.9f}, paper {grads[M.ADJ_PAPER]:.6f}")
     assert grads[M.ADJ_EXACT] == pytest.approx(H, abs=1e-6)
     assert grads[M.ADJ_PAPER] == pytest.approx(0.0686173, abs=1e-5)
 

@@ -212,7 +212,7 @@ def _terrain_states(sc, W, seed):
 
 @pytest.mark.parametrize("seed", [0, 1])
 def test_terrain_fp32_matches_oracle(ostrich, seed):
-    """Config-4 scene: mesh terrain, FP32, truncated pull-back adjoint."""
+    """The mesh-terrain scene: FP32, truncated pull-back adjoint."""
     sc = S.terrain_scene()
     W = 48
     st = _terrain_states(sc, W, seed)

@@ -744,8 +744,8 @@ def test_paper_adjoint_on_sliding_box_closed_form(v):
     assert re["dstate"][7] == pytest.approx(1.0, abs=1e-9)
 
 
-def test_paper_adjoint_config1_bias():
-    """Config 1 (box drop, v0 from seed 0, T = 20): the exact gradient dx_T/dv0 is h; the
+def test_paper_adjoint_box_drop_bias():
+    """The box-drop rollout (v0 from seed 0, T = 20): the exact gradient dx_T/dv0 is h; the
     paper's frozen-W adjoint gives h times the landing step's sliding ratio (the box stops
     in step 2, where sticking makes both modes agree), a bias of about -31 %."""
     sc, st = S.box_drop_inputs(0)
@@ -764,7 +764,7 @@ def test_paper_adjoint_config1_bias():
     r1 = orc.step(states[0], np.zeros(1), h)
     lam = r1["state"][sc.lam_index:].reshape(-1, 3)
     ratio = _paper_sliding_ratio(sc, h, r1["state"][7], lam[:, 0], r1["ids"] >= 0)
-    print(f"config-1 dx_T/dv0: exact {grads[O.ADJ_EXACT]:.6f}, paper {grads[O.ADJ_PAPER]:.6f} "
+    print(f"box drop dx_T/dv0: exact {grads[O.ADJ_EXACT]:.6f}, paper {grads[O.ADJ_PAPER]:.6f} "
           f"(bias {grads[O.ADJ_PAPER] / h - 1:+.4f})")
     assert grads[O.ADJ_EXACT] == pytest.approx(h, abs=1e-9)
     assert grads[O.ADJ_PAPER] == pytest.approx(h * ratio, rel=1e-5)
@@ -877,7 +877,7 @@ def test_mu_gradient_sliding_box_closed_form(v):
 
 
 def test_mu_gradient_landing_step_closed_form():
-    """Config 1's landing step: the box lands (u_z+ = -0.5 m/s) while sliding, the friction
+    """The box drop's landing step: the box lands (u_z+ = -0.5 m/s) while sliding, the friction
     impulse is mu m (g h - 0.5), so dv_x+/dmu = -(g h - 0.5)."""
     gold = json.load(open(os.path.join(GOLD, "box_drop_closed_form.json")))
     sc, st = S.box_drop_inputs(0)

@@ -267,7 +267,7 @@ def run_ours(args, rank, world_size, local_rank):
                            "T recomputed steps and T adjoint steps; world-steps = W x T per iteration",
                    "newton_budget": cfg.budget, "tol": FP32_TOL, "threads_per_world": opt["threads_per_world"],
                    "parallelism": f"replicas{world_size}",
-                   "l2": "trajectory 0.61 GB and tape of one segment 0.76 GB per iteration > 129 MB L2 (no flush needed)"},
+                   "l2": "trajectory 0.61 GB and tape of one segment 0.85 GB per iteration > 129 MB L2 (no flush needed)"},
         "gpu_launches": opt["gpu_launches_per_iteration"] * opt["iterations"],
         "e2e": opt["e2e"],
         "optimisation": {k: opt[k] for k in ("loss_first_warmup", "loss_first_timed", "loss_last_timed",

@@ -266,8 +266,8 @@ void ostrich_destroy(ostrich_ctx* ctx);
  * needed and nothing is allocated, freed or kept.
  *
  * EINVAL if n_worlds times the scene's per-world tape record exceeds the array (the
- * record is ostrich_tape_bytes / n_worlds of an FP32 context for the same scene: 9280 B
- * for the four-wheel robot over a box, so at most 1807 worlds per call; see
+ * record is ostrich_tape_bytes / n_worlds of an FP32 context for the same scene: 10432 B
+ * for the four-wheel robot over a box, so at most 1608 worlds per call; see
  * ostrich_noalloc_capacity), for heightmap
  * scenes (env OSTRICH_ENV_HEIGHTMAP: the heights would need a device copy), or on the
  * same argument errors as ostrich_create / ostrich_step; ECUDA if a launch fails.

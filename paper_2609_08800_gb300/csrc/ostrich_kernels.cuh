@@ -362,9 +362,19 @@ __device__ __forceinline__ int servo_joint(const DevScene& sc, int k) {
 // arrays state, 1 for a tape record)
 template <class Real> struct Src { const Real* p; size_t stride; };
 
+// Integers in a tape of Real elements, bit for bit: the bits of a float, or the value of a
+// double (exact for every int).
+__device__ __forceinline__ float tape_from_int(int v, float) { return __int_as_float(v); }
+__device__ __forceinline__ double tape_from_int(int v, double) { return (double)v; }
+__device__ __forceinline__ int tape_to_int(float v) { return __float_as_int(v); }
+__device__ __forceinline__ int tape_to_int(double v) { return (int)v; }
+
+// ct_out: when not null, the contact slot table of this step is recorded there (a tape
+// record's slot table); ct_in: when not null, the table is read from there instead of
+// running the activation (the adjoint, at the taped step: the same set by construction).
 template <class Real>
 __device__ void world_setup(const DevScene& sc, WS<Real>& w, Src<Real> qmv, Src<Real> umv, Src<Real> ubarv,
-                            double h) {
+                            double h, Real* ct_out = nullptr, const Real* ct_in = nullptr) {
   const int tid = threadIdx.x, nth = blockDim.x;
   const int nb = sc.nb;
   for (int i = tid; i < 7 * nb; i += nth) w.qm[i] = qmv.p[i * qmv.stride];
@@ -383,10 +393,26 @@ __device__ void world_setup(const DevScene& sc, WS<Real>& w, Src<Real> qmv, Src<
     w.sn[3 * sl] = n.x; w.sn[3 * sl + 1] = n.y; w.sn[3 * sl + 2] = n.z; w.sd[sl] = d;
     w.st1[3 * sl] = t1.x; w.st1[3 * sl + 1] = t1.y; w.st1[3 * sl + 2] = t1.z;
     w.st2[3 * sl] = t2.x; w.st2[3 * sl + 1] = t2.y; w.st2[3 * sl + 2] = t2.z;
+    if (ct_out) {
+      Real* c = ct_out + CT_PER_SLOT * sl;
+      c[0] = tape_from_int(a.active, Real(0)); c[1] = tape_from_int(a.id, Real(0)); c[2] = tape_from_int(a.ftype, Real(0));
+      c[3] = Real(a.n[0]); c[4] = Real(a.n[1]); c[5] = Real(a.n[2]); c[6] = Real(a.d);
+      c[7] = Real(a.ex); c[8] = Real(a.ez);
+    }
   };
   if (tid == 0) w.ints[7] = 0;
   __syncthreads();
-  if (sc.env == ENV_HEIGHTMAP) {
+  if (ct_in) {
+    for (int sl = tid; sl < sc.n_slots; sl += nth) {
+      const Real* c = ct_in + CT_PER_SLOT * sl;
+      SlotAct a;
+      a.active = tape_to_int(c[0]); a.id = tape_to_int(c[1]); a.ftype = tape_to_int(c[2]);
+      a.n[0] = (float)c[3]; a.n[1] = (float)c[4]; a.n[2] = (float)c[5]; a.d = (float)c[6];
+      a.ex = (float)c[7]; a.ez = (float)c[8];
+      const int b = sc.slot_body[sl];
+      store_slot(sl, b, sl - sc.slot_base[b], a);
+    }
+  } else if (sc.env == ENV_HEIGHTMAP) {
     // one thread per wheel rim: the rim's candidate faces fill its nf slots in order
     for (int e = tid; e < 2 * nb; e += nth) {
       const int b = e >> 1, rim = e & 1;
@@ -1503,7 +1529,7 @@ __device__ __forceinline__ void step_world(const DevScene& sc, WS<Real>& w, cons
   // this world's inputs (structure of arrays, world index fastest)
   Src<Real> sq = {sin + world, (size_t)ld}, su = {sin + (size_t)7 * nb * ld + world, (size_t)ld};
   Src<Real> sb = {ctl ? ctl + world : sin, ctl ? (size_t)ld : (size_t)0};
-  world_setup<Real>(sc, w, sq, su, sb, h);
+  world_setup<Real>(sc, w, sq, su, sb, h, tpw ? tpw + tl.off_ct : nullptr);
   const int m = w.ints[0];
   // warm start: lambda from the previous step on the active rows
   for (int i = tid; i < m; i += nth) w.lk[i] = sin[(size_t)(13 * nb + w.meta[4 * i + 3]) * ld + world];
@@ -1761,7 +1787,7 @@ __global__ void __launch_bounds__(128, 3) adjoint_kernel(const DevScene scp, con
   const TapeLayout tl = tape_layout(sc);
   const Real* tp = reinterpret_cast<const Real*>(a.tape) + ((size_t)slot * a.n_worlds + world) * tl.total;
   Src<Real> sq = {tp + tl.off_qm, 1}, su = {tp + tl.off_um, 1}, sb = {tp + tl.off_ubar, 1};
-  world_setup<Real>(sc, w, sq, su, sb, h);
+  world_setup<Real>(sc, w, sq, su, sb, h, (Real*)nullptr, tp + tl.off_ct);   // the step's contact set
   const int m = w.ints[0], mc = w.ints[1];
   for (int i = tid; i < 6 * nb; i += nth) w.uk[i] = tp[tl.off_u + i];
   for (int i = tid; i < m; i += nth) w.lk[i] = tp[tl.off_lam + w.meta[4 * i + 3]];

@@ -133,12 +133,13 @@ struct AdjArgs {
   int32_t* krylov = nullptr;    // optional: per world Krylov iterations (GMRES, or the PCR solve) | 1 << 16 if not converged
 };
 
-// Tape record of one world for one step: inputs, returned iterate and the Schur factor
-// (block-arrowhead, in inverse form).
-// All counts in Real elements.
+// Tape record of one world for one step: inputs, the contact slot table the step's
+// activation produced, returned iterate and the Schur factor (block-arrowhead, in inverse
+// form).  All counts in Real elements.
 struct TapeLayout {
-  int off_qm, off_um, off_ubar, off_u, off_lam, off_G, off_H, off_S, total;
+  int off_qm, off_um, off_ubar, off_ct, off_u, off_lam, off_G, off_H, off_S, total;
 };
+constexpr int CT_PER_SLOT = 9;   // active, id, feature type (bit-exact), normal (3), offset, edge (2)
 
 inline __host__ __device__ TapeLayout tape_layout(const DevScene& s) {
   TapeLayout t;
@@ -146,6 +147,7 @@ inline __host__ __device__ TapeLayout tape_layout(const DevScene& s) {
   t.off_qm = o; o += 7 * s.nb;
   t.off_um = o; o += 6 * s.nb;
   t.off_ubar = o; o += s.n_servo > 0 ? s.n_servo : 1;
+  t.off_ct = o; o += CT_PER_SLOT * s.n_slots;        // the step's contact slot table
   t.off_u = o; o += 6 * s.nb;
   t.off_lam = o; o += s.m_max;
   t.off_G = o; o += s.n_groups * tri_size(s.pg);    // inverse Cholesky factors L_g^-1 of the groups (packed)

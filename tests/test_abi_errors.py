@@ -79,8 +79,8 @@ def test_noalloc_refuses_heightmap_scenes(lib):
 
 
 def test_noalloc_refuses_worlds_beyond_its_array(lib):
-    # 9280 B of tape per robot-over-box world: 1807 fit the 16 MiB array, 1808 do not
-    assert _noalloc(lib, S.robot_box_scene(), 1808) == OSTRICH_EINVAL
+    # 10432 B of tape per robot-over-box world: 1608 fit the 16 MiB array, 1609 do not
+    assert _noalloc(lib, S.robot_box_scene(), 1609) == OSTRICH_EINVAL
 
 
 @pytest.mark.parametrize("args", [(2, 0, 16, 256, 0.0), (1, 2, 16, 256, 0.0), (1, 0, 0, 256, 0.0),
@@ -101,10 +101,10 @@ def test_linear_solver_rejects_invalid_settings(lib, args):
 
 
 def test_noalloc_capacity_of_the_robot_and_refusals(lib):
-    """The capacity helper: 9280 B per robot-over-box world, 1807 worlds in the 16 MiB
+    """The capacity helper: 10432 B per robot-over-box world, 1608 worlds in the 16 MiB
     array; heightmap scenes refused (host only)."""
     mw, rb = M.noalloc_capacity(S.robot_box_scene())
-    assert (mw, rb) == (1807, 9280)
+    assert (mw, rb) == (1608, 10432)
     assert mw * rb <= 16 << 20 < (mw + 1) * rb
     with pytest.raises(ValueError):
         M.noalloc_capacity(S.terrain_scene(n=16))

@@ -53,7 +53,7 @@ def test_noalloc_rejects_sizes_beyond_the_array():
         pytest.skip("no GPU")
     from paper_2609_08800_gb300 import ostrich as M
     sc = S.robot_box_scene()
-    W = 2048                        # 2048 x 9280 B > 16 MiB (at most 1807 robot worlds)
+    W = 2048                        # 2048 x 10432 B > 16 MiB (at most 1608 robot worlds)
     st = torch.zeros(sc.n_state, W, dtype=torch.float32, device="cuda")
     ub = torch.zeros(sc.n_servos, W, dtype=torch.float32, device="cuda")
     with pytest.raises(RuntimeError, match="status 1"):

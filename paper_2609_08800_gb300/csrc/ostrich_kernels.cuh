@@ -484,46 +484,79 @@ __device__ void world_setup(const DevScene& sc, WS<Real>& w, Src<Real> qmv, Src<
       w.sbc[k] = -w.ubar[k];
     }
   }
-  // row compaction (one thread, fixed order): groups of contact rows, then separator
-  if (tid == 0) {
-    int m = 0;
-    for (int g = 0; g < sc.n_groups; ++g) {
-      int b = sc.group_body[g];
-      w.g0[g] = m;
-      for (int sl = sc.slot_base[b]; sl < sc.slot_base[b] + sc.slot_count[b]; ++sl) {
-        if (!w.sact[sl]) { w.srow[sl] = -1; continue; }
-        w.srow[sl] = m;
-        int lam = 5 * sc.nj + sc.n_servo + 3 * sl;
-        for (int k = 0; k < 3; ++k) {
-          int t = k == 0 ? ROW_NORMAL : ROW_FRIC;
-          w.meta[4 * m] = t | (k << 4); w.meta[4 * m + 1] = b; w.meta[4 * m + 2] = -1; w.meta[4 * m + 3] = lam + k;
-          w.ref[m] = sl;
-          w.rgrp[m] = g;
-          ++m;
-        }
+  // row compaction, fixed order: the contact rows of the active slots in slot order (so
+  // grouped by body), then the separator rows.  A slot's first row is 3 x the number of
+  // active slots before it: warp ballots over the slot table (at most 64 slots) give the
+  // prefix counts, and each lane writes its own slot's rows.
+  if (tid < 32) {
+    const int lane = tid, ns = sc.n_slots;
+    const unsigned m0 = __ballot_sync(0xffffffffu, lane < ns && w.sact[lane]);
+    const unsigned m1 = __ballot_sync(0xffffffffu, 32 + lane < ns && w.sact[32 + lane]);
+    const int c0 = __popc(m0);
+    for (int c = 0; c < 2; ++c) {
+      const int sl = 32 * c + lane;
+      if (sl >= ns) continue;
+      const unsigned mk = c == 0 ? m0 : m1;
+      if (!((mk >> lane) & 1u)) { w.srow[sl] = -1; continue; }
+      const int r0 = 3 * ((c == 0 ? 0 : c0) + __popc(mk & ((1u << lane) - 1u)));
+      const int bb = sc.slot_body[sl];
+      w.srow[sl] = r0;
+      const int lam = 5 * sc.nj + sc.n_servo + 3 * sl;
+      int gb = 0;
+      while (sc.group_body[gb] != bb) ++gb;
+      for (int k = 0; k < 3; ++k) {
+        const int r = r0 + k;
+        w.meta[4 * r] = (k == 0 ? ROW_NORMAL : ROW_FRIC) | (k << 4); w.meta[4 * r + 1] = bb; w.meta[4 * r + 2] = -1;
+        w.meta[4 * r + 3] = lam + k;
+        w.ref[r] = sl;
+        w.rgrp[r] = gb;
       }
-      w.gn[g] = m - w.g0[g];
     }
-    int mc = m;
-    for (int j = 0; j < sc.nj; ++j)
-      for (int k = 0; k < 5; ++k) {
-        w.meta[4 * m] = ROW_JOINT | (k << 4); w.meta[4 * m + 1] = sc.jp[j]; w.meta[4 * m + 2] = sc.jc[j];
-        w.meta[4 * m + 3] = 5 * j + k; w.ref[m] = j; ++m;
+    // groups: first row and row count of each body's slots
+    for (int g = lane; g < sc.n_groups; g += 32) {
+      const int bb = sc.group_body[g], lo = sc.slot_base[bb], hi = lo + sc.slot_count[bb];
+      auto before = [&](int x) {   // active slots with index < x
+        const unsigned lo0 = x >= 32 ? m0 : (m0 & ((1u << x) - 1u));
+        const unsigned lo1 = x <= 32 ? 0u : (x >= 64 ? m1 : (m1 & ((1u << (x - 32)) - 1u)));
+        return __popc(lo0) + __popc(lo1);
+      };
+      w.g0[g] = 3 * before(lo);
+      w.gn[g] = 3 * (before(hi) - before(lo));
+    }
+    if (lane == 0) {
+      const int mc = 3 * (c0 + __popc(m1));
+      w.ints[1] = mc;
+      w.ints[0] = mc + sc.ss;
+    }
+  }
+  __syncthreads();
+  {
+    const int mc = w.ints[1];
+    // separator rows: five per joint, then one per servo
+    for (int a = tid; a < sc.ss; a += nth) {
+      const int r = mc + a;
+      if (a < 5 * sc.nj) {
+        const int j = a / 5, k = a - 5 * j;
+        w.meta[4 * r] = ROW_JOINT | (k << 4); w.meta[4 * r + 1] = sc.jp[j]; w.meta[4 * r + 2] = sc.jc[j];
+        w.meta[4 * r + 3] = 5 * j + k; w.ref[r] = j;
+      } else {
+        const int j = servo_joint(sc, a - 5 * sc.nj);
+        w.meta[4 * r] = ROW_SERVO; w.meta[4 * r + 1] = sc.jp[j]; w.meta[4 * r + 2] = sc.jc[j];
+        w.meta[4 * r + 3] = 5 * sc.nj + sc.servo_of[j]; w.ref[r] = j;
       }
-    for (int j = 0; j < sc.nj; ++j) {
-      if (sc.servo_of[j] < 0) continue;
-      w.meta[4 * m] = ROW_SERVO; w.meta[4 * m + 1] = sc.jp[j]; w.meta[4 * m + 2] = sc.jc[j];
-      w.meta[4 * m + 3] = 5 * sc.nj + sc.servo_of[j]; w.ref[m] = j; ++m;
     }
-    w.ints[0] = m; w.ints[1] = mc;
-    // per-body lists: its group and the separator rows that touch it
-    for (int b = 0; b < nb; ++b) { w.bgrp[b] = -1; w.bsepn[b] = 0; }
-    for (int g = 0; g < sc.n_groups; ++g) w.bgrp[sc.group_body[g]] = g;
-    int ssd = sc.ss > 0 ? sc.ss : 1;
-    for (int i = mc; i < m; ++i) {
-      int b0 = w.meta[4 * i + 1], b1 = w.meta[4 * i + 2];
-      w.bsep[b0 * ssd + w.bsepn[b0]++] = i;
-      if (b1 >= 0) w.bsep[b1 * ssd + w.bsepn[b1]++] = i;
+    // per-body lists: its group and the separator rows that touch it, in row order
+    const int ssd = sc.ss > 0 ? sc.ss : 1;
+    for (int bb = tid; bb < nb; bb += nth) {
+      int gb = -1;
+      for (int g = 0; g < sc.n_groups; ++g) if (sc.group_body[g] == bb) gb = g;
+      w.bgrp[bb] = gb;
+      int cnt = 0;
+      for (int a2 = 0; a2 < sc.ss; ++a2) {
+        const int j = a2 < 5 * sc.nj ? a2 / 5 : servo_joint(sc, a2 - 5 * sc.nj);
+        if (sc.jp[j] == bb || sc.jc[j] == bb) w.bsep[bb * ssd + cnt++] = mc + a2;
+      }
+      w.bsepn[bb] = cnt;
     }
   }
   __syncthreads();

@@ -146,8 +146,10 @@ ostrich_status ostrich_step(ostrich_ctx* ctx, const void* state_in, const void* 
 
 /* Adjoint of the step recorded in tape_slot (Sec. III-D): dL/dstate_next (state
  * layout; lambda entries ignored) -> dL/dstate (lambda entries zero) and
- * dL/dcontrols (may be NULL).  h must equal the recorded step's.  ETAPE if the slot
- * holds no step. */
+ * dL/dcontrols (may be NULL).  The slot holds the step's inputs, its contact set (the
+ * adjoint uses the same set, it does not run the activation again), the returned
+ * iterate and, under the direct solver, the Schur factor at that iterate.  h must equal
+ * the recorded step's.  ETAPE if the slot holds no step. */
 ostrich_status ostrich_adjoint(ostrich_ctx* ctx, int tape_slot, const void* dL_dstate_next, double h,
                                void* dL_dstate, void* dL_dcontrols, void* stream);
 
@@ -192,7 +194,7 @@ ostrich_status ostrich_set_adjoint_mode(ostrich_ctx* ctx, int mode, int32_t* kry
  *     (never assembled) and one application of the preconditioner, precond =
  *     OSTRICH_PC_JACOBI (the inverse diagonal of A) or OSTRICH_PC_BLOCK (the inverse of each
  *     contact group's diagonal block and of the joint/servo block, by in-place Cholesky).
- *     Nothing but the iterate is taped; the paper-mode adjoint forms the same operator and
+ *     No factor is taped; the paper-mode adjoint forms the same operator and
  *     preconditioner at the taped iterate and solves with PCR, restarted on the true
  *     residual (formed with compensated sums) until |r| <= adj_rtol |rhs|, until a restart
  *     no longer changes the solution at working precision, or after adj_iters PCR iterations

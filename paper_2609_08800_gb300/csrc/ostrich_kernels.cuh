@@ -1804,6 +1804,7 @@ __global__ void __launch_bounds__(128, 3) adjoint_kernel(const DevScene scp, con
   extern __shared__ __align__(16) char smem[];
   __shared__ __align__(16) DevScene ssc;
   __shared__ int bgl[NB_CAP * GROUPS_PER_BODY], bgn[NB_CAP], item0[NB_CAP + 1];
+  __shared__ int ncon[NB_CAP], jpre[NB_CAP + 1], cpre[NB_CAP + 1];
   scene_to_shared(scp, ssc);
   const DevScene& sc = ssc;
   WS<Real> w = ws_carve<Real>(smem, sc);
@@ -1831,6 +1832,16 @@ __global__ void __launch_bounds__(128, 3) adjoint_kernel(const DevScene scp, con
     int acc = 0;
     for (int b = 0; b < nb; ++b) { item0[b] = acc; acc += 7 * (bgn[b] + 1); }
     item0[nb] = acc;
+    // work order of the pull-back items by cost: joint groups, contact groups, body terms
+    int aj = 0, ac = 0;
+    for (int b = 0; b < nb; ++b) {
+      int nc = 0;
+      while (nc < bgn[b] && bgl[b * GROUPS_PER_BODY + nc] < sc.n_slots) ++nc;
+      ncon[b] = nc;
+      jpre[b] = aj; aj += 7 * (bgn[b] - nc);
+      cpre[b] = ac; ac += 7 * nc;
+    }
+    jpre[nb] = aj; cpre[nb] = ac;
   }
   if (sc.lin == LIN_DIRECT) {
     // factor from the tape
@@ -2021,13 +2032,32 @@ __global__ void __launch_bounds__(128, 3) adjoint_kernel(const DevScene scp, con
   const bool trunc = MODE == ADJ_PAPER && sc.pullback == 1;
   Real* item = w.G;     // the factor (G, E, H, S, one carved run) is no longer needed;
                         // sum_b 7 (groups_b + 1) <= 14 m_max items
-  const int n_items = item0[nb];
+  // taken in cost order (every joint item, then every contact item, then the body terms)
+  // so that the threads' loads even out; each item is stored at its place in the per-body
+  // layout, which fixes the order of the sums below
+  const int n_items = item0[nb], nj_items = jpre[nb], nc_items = cpre[nb];
   for (int e = tid; e < n_items; e += nth) {
-    int b = 0;
-    while (e >= item0[b + 1]) ++b;
-    const int r = e - item0[b], c = r / (bgn[b] + 1), k = r - c * (bgn[b] + 1);
-    item[e] = k == 0 ? body_vjp(sc, w, b, c, gq, wu, h)
-                     : group_vjp_q<Real, MODE>(sc, w, ex, bgl[b * GROUPS_PER_BODY + k - 1], b, c, wl, wu, trunc, h);
+    int b = 0, c, k;
+    if (e < nj_items) {
+      while (e >= jpre[b + 1]) ++b;
+      const int nj = bgn[b] - ncon[b], r = e - jpre[b];
+      c = r / nj;
+      k = 1 + ncon[b] + (r - c * nj);
+    } else if (e < nj_items + nc_items) {
+      const int e2 = e - nj_items;
+      while (e2 >= cpre[b + 1]) ++b;
+      const int nc = ncon[b], r = e2 - cpre[b];
+      c = r / nc;
+      k = 1 + (r - c * nc);
+    } else {
+      const int e3 = e - nj_items - nc_items;
+      b = e3 / 7;
+      c = e3 - 7 * b;
+      k = 0;
+    }
+    item[item0[b] + c * (bgn[b] + 1) + k] =
+        k == 0 ? body_vjp(sc, w, b, c, gq, wu, h)
+               : group_vjp_q<Real, MODE>(sc, w, ex, bgl[b * GROUPS_PER_BODY + k - 1], b, c, wl, wu, trunc, h);
   }
   __syncthreads();
   for (int e = tid; e < nb * 7; e += nth) {

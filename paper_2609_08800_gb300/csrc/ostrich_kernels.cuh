@@ -362,6 +362,16 @@ __device__ __forceinline__ int servo_joint(const DevScene& sc, int k) {
 // arrays state, 1 for a tape record)
 template <class Real> struct Src { const Real* p; size_t stride; };
 
+// Asynchronous global -> shared copy of one element (cp.async, cached in L1), committed
+// as a group and awaited before use, so that the copies proceed while the CTA computes.
+template <class Real> __device__ __forceinline__ void cp_async_elem(Real* smem_dst, const Real* gsrc) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem_dst);
+  if (sizeof(Real) == 8) asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gsrc) : "memory");
+  else asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
 // Integers in a tape of Real elements, bit for bit: the bits of a float, or the value of a
 // double (exact for every int).
 __device__ __forceinline__ float tape_from_int(int v, float) { return __int_as_float(v); }
@@ -1820,6 +1830,14 @@ __global__ void __launch_bounds__(128, 3) adjoint_kernel(const DevScene scp, con
   const Real hR = Real(h);
   const TapeLayout tl = tape_layout(sc);
   const Real* tp = reinterpret_cast<const Real*>(a.tape) + ((size_t)slot * a.n_worlds + world) * tl.total;
+  if (sc.lin == LIN_DIRECT) {
+    // the taped factor, copied to shared memory in the background of the setup and the
+    // evaluation (neither touches G, H or S); awaited before the solve
+    for (int i = tid; i < sc.n_groups * tri_size(sc.pg); i += nth) cp_async_elem(w.G + i, tp + tl.off_G + i);
+    for (int i = tid; i < sc.n_groups * sc.cmax * sc.ldg; i += nth) cp_async_elem(w.H + i, tp + tl.off_H + i);
+    for (int i = tid; i < tri_size(sc.ss); i += nth) cp_async_elem(w.S + i, tp + tl.off_S + i);
+    cp_async_commit();
+  }
   Src<Real> sq = {tp + tl.off_qm, 1}, su = {tp + tl.off_um, 1}, sb = {tp + tl.off_ubar, 1};
   world_setup<Real>(sc, w, sq, su, sb, h, (Real*)nullptr, tp + tl.off_ct);   // the step's contact set
   const int m = w.ints[0], mc = w.ints[1];
@@ -1844,10 +1862,8 @@ __global__ void __launch_bounds__(128, 3) adjoint_kernel(const DevScene scp, con
     jpre[nb] = aj; cpre[nb] = ac;
   }
   if (sc.lin == LIN_DIRECT) {
-    // factor from the tape
-    for (int i = tid; i < sc.n_groups * tri_size(sc.pg); i += nth) w.G[i] = tp[tl.off_G + i];
-    for (int i = tid; i < sc.n_groups * sc.cmax * sc.ldg; i += nth) w.H[i] = tp[tl.off_H + i];
-    for (int i = tid; i < tri_size(sc.ss); i += nth) w.S[i] = tp[tl.off_S + i];
+    cp_async_wait_all();     // this thread's copies of the taped factor; the barrier below
+                             // (before the solve) makes every thread's visible
   } else if (MODE == ADJ_EXACT) {
     // PCR mode tapes no factor: the exact mode's GMRES preconditioner is the direct factor,
     // formed here at the taped iterate

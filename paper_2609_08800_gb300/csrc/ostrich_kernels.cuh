@@ -159,6 +159,23 @@ template <class Real> __device__ Real block_max(WS<Real>& w, Real v) {
   return mx;
 }
 
+// two block maxima at once (every thread gets both), through w.red[40..] and w.red[56..]
+template <class Real> __device__ void block_max2(WS<Real>& w, Real& a, Real& b) {
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = (blockDim.x + 31) >> 5;
+  for (int o = 16; o > 0; o >>= 1) {
+    a = fmax(a, __shfl_xor_sync(0xffffffffu, a, o));
+    b = fmax(b, __shfl_xor_sync(0xffffffffu, b, o));
+  }
+  __syncthreads();
+  if (lane == 0) { w.red[40 + wid] = a; w.red[56 + wid] = b; }
+  __syncthreads();
+  Real ma = w.red[40], mb = w.red[56];
+  for (int i = 1; i < nw; ++i) { ma = fmax(ma, w.red[40 + i]); mb = fmax(mb, w.red[56 + i]); }
+  __syncthreads();
+  a = ma;
+  b = mb;
+}
+
 // ---------------------------------------------------------------------------
 // geometry helpers in any scalar type S
 // ---------------------------------------------------------------------------
@@ -623,8 +640,10 @@ template <class Real> __device__ __forceinline__ void minv_row(const DevScene& s
 // ---------------------------------------------------------------------------
 // one residual / Jacobian evaluation at iterate (u, lam); returns the merit
 // ---------------------------------------------------------------------------
+// dyn = false (the adjoint): the rows, their compliance and delta only; the dynamics
+// residual and the merit are not formed (the returned merit is 0).
 template <class Real>
-__device__ Real evaluate(const DevScene& sc, WS<Real>& w, const Real* u, const Real* lam, double h) {
+__device__ Real evaluate(const DevScene& sc, WS<Real>& w, const Real* u, const Real* lam, double h, bool dyn = true) {
   const int tid = threadIdx.x, nth = blockDim.x;
   const int nb = sc.nb, m = w.ints[0], mc = w.ints[1];
   const Real hR = Real(h);
@@ -744,44 +763,47 @@ __device__ Real evaluate(const DevScene& sc, WS<Real>& w, const Real* u, const R
     }
   }
   __syncthreads();
-  // Eq. (10): r_dyn = M (u - u-) - h f - h J^T lambda, per body; merit part |M^-1 r_dyn|^2.
-  // The inertia and constraint terms nearly cancel at convergence, so the sum is
-  // accumulated with exact products and exact partial sums (acc2).
-  const int ssd = sc.ss > 0 ? sc.ss : 1;
-  for (int task = tid; task < 6 * nb; task += nth) {
-    const int b = task / 6, k = task - 6 * (task / 6);
-    acc2<Real> rd;
-    int g = w.bgrp[b];
-    if (g >= 0)
-      for (int i = w.g0[g]; i < w.g0[g] + w.gn[g]; ++i) rd.add_prod(w.J[12 * i + k], -hR * lam[i]);
-    for (int t = 0; t < w.bsepn[b]; ++t) {
-      int i = w.bsep[b * ssd + t];
-      int side = w.meta[4 * i + 1] == b ? 0 : 6;
-      rd.add_prod(w.J[12 * i + side + k], -hR * lam[i]);
-    }
-    if (k < 3) {
-      const Real m_ = Real(sc.mass[b]);
-      rd.add_prod(m_, u[6 * b + k]);
-      rd.add_prod(-m_, w.um[6 * b + k]);
-    } else {
-      for (int c = 0; c < 3; ++c) {
-        rd.add_prod(w.Iw[9 * b + 3 * (k - 3) + c], u[6 * b + 3 + c]);
-        rd.add_prod(-w.Iw[9 * b + 3 * (k - 3) + c], w.um[6 * b + 3 + c]);
+  if (dyn) {
+    // Eq. (10): r_dyn = M (u - u-) - h f - h J^T lambda, per body; merit part |M^-1 r_dyn|^2.
+    // The inertia and constraint terms nearly cancel at convergence, so the sum is
+    // accumulated with exact products and exact partial sums (acc2).
+    const int ssd = sc.ss > 0 ? sc.ss : 1;
+    for (int task = tid; task < 6 * nb; task += nth) {
+      const int b = task / 6, k = task - 6 * (task / 6);
+      acc2<Real> rd;
+      int g = w.bgrp[b];
+      if (g >= 0)
+        for (int i = w.g0[g]; i < w.g0[g] + w.gn[g]; ++i) rd.add_prod(w.J[12 * i + k], -hR * lam[i]);
+      for (int t = 0; t < w.bsepn[b]; ++t) {
+        int i = w.bsep[b * ssd + t];
+        int side = w.meta[4 * i + 1] == b ? 0 : 6;
+        rd.add_prod(w.J[12 * i + side + k], -hR * lam[i]);
       }
+      if (k < 3) {
+        const Real m_ = Real(sc.mass[b]);
+        rd.add_prod(m_, u[6 * b + k]);
+        rd.add_prod(-m_, w.um[6 * b + k]);
+      } else {
+        for (int c = 0; c < 3; ++c) {
+          rd.add_prod(w.Iw[9 * b + 3 * (k - 3) + c], u[6 * b + 3 + c]);
+          rd.add_prod(-w.Iw[9 * b + 3 * (k - 3) + c], w.um[6 * b + 3 + c]);
+        }
+      }
+      rd.add_prod(-hR, w.f[6 * b + k]);
+      w.rdyn[6 * b + k] = rd.value();
     }
-    rd.add_prod(-hR, w.f[6 * b + k]);
-    w.rdyn[6 * b + k] = rd.value();
+    __syncthreads();
   }
-  __syncthreads();
   Real part = Real(0);
-  for (int b = tid; b < nb; b += nth) {
+  for (int b = tid; b < nb && dyn; b += nth) {
     const Real* rv = w.rdyn + 6 * b;
     Real mi = Real(1) / Real(sc.mass[b]);
     vec3<Real> iw = mat3<Real>(w.Iwi + 9 * b, v3(rv[3], rv[4], rv[5]));
     Real mr[6] = {rv[0] * mi, rv[1] * mi, rv[2] * mi, iw.x, iw.y, iw.z};
     for (int k = 0; k < 6; ++k) { w.mr[6 * b + k] = mr[k]; part += mr[k] * mr[k]; }
   }
-  for (int i = tid; i < m; i += nth) part += w.r2[i] * w.r2[i];
+  if (dyn)
+    for (int i = tid; i < m; i += nth) part += w.r2[i] * w.r2[i];
   // with the merit: delta = delta_rel * mean diag(h J M^-1 J^T) of these rows, for the
   // assembly at this iterate (scal[2])
   Real dpart = 0;
@@ -1279,8 +1301,7 @@ __device__ void schur_solve(const DevScene& sc, WS<Real>& w, const Real* b, Real
     __syncthreads();
     // optional early stop once the correction no longer changes x at working precision
     if (stop_rel > Real(0)) {
-      cmax = block_max(w, cmax);
-      xmax = block_max(w, xmax);
+      block_max2(w, cmax, xmax);
       if (cmax <= stop_rel * xmax) break;
     }
   }
@@ -1844,7 +1865,7 @@ __global__ void __launch_bounds__(128, 3) adjoint_kernel(const DevScene scp, con
   for (int i = tid; i < 6 * nb; i += nth) w.uk[i] = tp[tl.off_u + i];
   for (int i = tid; i < m; i += nth) w.lk[i] = tp[tl.off_lam + w.meta[4 * i + 3]];
   __syncthreads();
-  evaluate(sc, w, w.uk, w.lk, h);      // J (with E at u*), poses at q+
+  evaluate(sc, w, w.uk, w.lk, h, false);   // J (with E at u*), C, delta, poses at q+
   if (tid == 0) {
     body_groups(sc, w, bgl, bgn);
     int acc = 0;

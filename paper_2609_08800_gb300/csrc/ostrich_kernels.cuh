@@ -1679,18 +1679,22 @@ __device__ __forceinline__ void step_world(const DevScene& sc, WS<Real>& w, cons
     __syncthreads();
   }
   uint32_t status = 0;
+  // the workspace holds the evaluation of (uk, lk) -- the last one the loop made -- unless
+  // the best iterate is restored (or the iterate was set to NaN)
+  bool evald = !nan0;
   if (!conv) {
     if (k >= sc.kmin && merit < best) { best = merit; best_k = k; }
     else if (best_k >= 0) {
       for (int i = tid; i < 6 * nb; i += nth) w.uk[i] = w.ub[i];
       for (int i = tid; i < m; i += nth) w.lk[i] = w.lb[i];
       merit = best;
+      evald = false;
     }
     status |= 1u;
   }
   __syncthreads();
   // the returned iterate: its Jacobian, compliance and Schur factor go to the tape
-  Real mret = evaluate(sc, w, w.uk, w.lk, h);
+  const Real mret = evald ? merit : evaluate(sc, w, w.uk, w.lk, h);
   if (!(mret == mret) || !(fabs((double)mret) < 1e300)) status |= 2u;
   status |= (uint32_t)w.ints[7];
   if (tpw) {

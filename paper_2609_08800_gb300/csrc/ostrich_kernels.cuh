@@ -1642,11 +1642,14 @@ __device__ __forceinline__ void step_world(const DevScene& sc, WS<Real>& w, cons
       for (int q = 0; q < 6; ++q) jm.add_prod(Ji[q], w.mr[6 * b0 + q]);
       if (b1 >= 0) for (int q = 0; q < 6; ++q) jm.add_prod(Ji[6 + q], w.mr[6 * b1 + q]);
       jm.add(-w.rhat[i]);
-      w.rhs[i] = jm.value();
+      // unrefined direct solve: the right-hand side goes straight to dl, solved in place
+      if (sc.lin == LIN_DIRECT && sc.refine == 0) w.dl[i] = jm.value();
+      else w.rhs[i] = jm.value();
     }
     __syncthreads();
     if (sc.lin == LIN_DIRECT) {
-      schur_solve(sc, w, w.rhs, w.dl, w.du, w.lt, h, sc.refine);
+      if (sc.refine == 0) arrow_solve(sc, w, w.dl);
+      else schur_solve(sc, w, w.rhs, w.dl, w.du, w.lt, h, sc.refine);
     } else {
       int pconv;
       pcr_solve<Real, false>(sc, w, w.rhs, w.dl, sc.pcr_iters, Real(0), w.du, h, &pconv);

@@ -20,7 +20,8 @@ Prints one JSON line.  Extra keys:
   plain_form     the same kernels launched once per world per step (W = 1)
   serving        the Poisson request stream: continuous batching, FIFO queue, plain form
   cpu_baseline   the FP64 oracle on the host cores, on a bounded sample
-`--impl reference` times the FP64 oracle instead (the reference arm).
+`--impl reference` times the FP64 oracle instead (the reference arm): each step one Adam
+iteration of the same optimisation workload on a sample of worlds, split over the host cores.
 """
 from __future__ import annotations
 
@@ -261,13 +262,10 @@ def run_ours(args, rank, world_size, local_rank):
         "metric": METRIC, "value": opt["value"], "unit": UNIT, "n_gpus": world_size, "steps": opt["iterations"],
         "warmup": args.warmup, "ms_per_step": opt["ms_per_iteration"], "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": f"robot_over_box_{W}_worlds_fp32_adam_T{OPT_T}_ckpt{CHUNK}",
-                   "worlds_per_gpu": W, "horizon_steps": OPT_T, "h": H, "checkpoint_every": CHUNK,
-                   "step": "one Adam iteration (lr 0.3) on 8-knot wheel splines: T forward steps, the backward's "
-                           "T recomputed steps and T adjoint steps; world-steps = W x T per iteration",
-                   "newton_budget": cfg.budget, "tol": FP32_TOL, "threads_per_world": opt["threads_per_world"],
-                   "parallelism": f"replicas{world_size}",
-                   "l2": "trajectory 0.61 GB and tape of one segment 0.85 GB per iteration > 129 MB L2 (no flush needed)"},
+        "config": dict(opt_config(W), newton_budget=cfg.budget, threads_per_world=opt["threads_per_world"],
+                       parallelism=f"replicas{world_size}",
+                       l2="trajectory 0.61 GB and tape of one segment 0.85 GB per iteration > 129 MB L2 "
+                          "(no flush needed)"),
         "gpu_launches": opt["gpu_launches_per_iteration"] * opt["iterations"],
         "e2e": opt["e2e"],
         "optimisation": {k: opt[k] for k in ("loss_first_warmup", "loss_first_timed", "loss_last_timed",
@@ -730,19 +728,28 @@ def run_serving(args, torch):
     return out
 
 
-def _oracle_chunk_worlds(states, controls, g, orc):
-    """Forward CHUNK steps then CHUNK adjoints of each world on the oracle; world-steps run."""
-    n = 0
-    for w in range(states.shape[1]):
-        s = states[:, w].astype(np.float32).astype(np.float64)
-        traj = [s]
-        for t in range(CHUNK):
-            traj.append(orc.step(traj[-1], controls[t, :, w].astype(np.float64), H)["state"])
-        gg = g[:, w].copy()
-        for t in reversed(range(CHUNK)):
-            gg = orc.step_adjoint(traj[t], controls[t, :, w].astype(np.float64), H, gg)["dstate"]
-        n += CHUNK
-    return n
+def _oracle_opt_world(s0, knots, B, orc):
+    """One world of the optimisation workload on the oracle: the T-step rollout under the
+    spline controls B @ knots^T, the loss |p_xy(T) - (3, 0)|^2 of the chassis, then the
+    backward sweep (every step re-solved by the oracle's adjoint call, as the checkpointed
+    backward recomputes its segments) and the knot gradient B^T dL/dcontrols.  A world
+    whose rollout diverged gets no gradient.  Returns (loss, dL/dknots [wheels, K])."""
+    T = B.shape[0]
+    ctl = B @ knots.T                                  # [T, wheels]
+    traj = [np.asarray(s0, dtype=np.float64)]
+    for t in range(T):
+        traj.append(orc.step(traj[-1], ctl[t], H)["state"])
+    sT = traj[T]
+    loss = (sT[0] - 3.0) ** 2 + sT[1] ** 2
+    if not np.isfinite(loss):
+        return float(loss), np.zeros_like(knots)
+    g = np.zeros_like(sT)
+    g[0], g[1] = 2.0 * (sT[0] - 3.0), 2.0 * sT[1]
+    du = np.zeros_like(ctl)
+    for t in reversed(range(T)):
+        r = orc.step_adjoint(traj[t], ctl[t], H, g)
+        g, du[t] = r["dstate"], r["dubar"]
+    return float(loss), np.nan_to_num((B.T @ du).T, nan=0.0, posinf=0.0, neginf=0.0)
 
 
 _WORKER_ORACLE = None
@@ -755,37 +762,80 @@ def _worker_init():
 
 
 def _worker_run(job):
-    states, controls, g = job
-    return _oracle_chunk_worlds(states, controls, g, _WORKER_ORACLE)
+    states, knots = job
+    B = SP.basis(OPT_T, knots.shape[2], H)
+    return [_oracle_opt_world(states[:, w], knots[w], B, _WORKER_ORACLE) for w in range(states.shape[1])]
 
 
-def run_cpu_baseline(args, impl_line=False, procs=1):
-    """FP64 oracle on the host: forward + adjoint of a bounded sample of the workload,
-    in this process (procs = 1) or split over `procs` spawned processes (one oracle each,
-    args.cpu_worlds worlds per process; pool start-up outside the timing)."""
-    from oracle import oracle as O
-    W = args.cpu_worlds * procs
-    scene, states, controls, g = make_inputs(max(W, 1), seed=0)
-    if procs <= 1:
-        orc = O.Oracle(scene, S.SolverConfig(tol=FP32_TOL))
+class OracleOptSample:
+    """The optimisation workload (robot over the box, 8-knot wheel splines, T = 100,
+    h = 0.1, Newton budget 16, tol 1e-4, Adam with lr 0.3 on the knots) on a sample of
+    worlds, on the FP64 oracle: in this process (procs = 1) or split over `procs` spawned
+    processes, one oracle each (pool start-up and a one-world warm call outside the
+    timing).  One call of `iteration` is one Adam iteration over the sample."""
+
+    def __init__(self, n_worlds, procs=1):
+        scene = S.robot_box_scene()
+        self.n, self.procs = n_worlds, max(1, procs)
+        self.states = S.robot_box_states(scene, n_worlds, seed=0).astype(np.float32).astype(np.float64)
+        self.knots = S.spline_knots(n_worlds, n_wheels=4, n_knots=8, seed=0).astype(np.float32).astype(np.float64)
+        self.m1, self.m2, self.t = np.zeros_like(self.knots), np.zeros_like(self.knots), 0
+        self.pool, self.orc = None, None
+        if self.procs > 1:
+            import multiprocessing as mp
+            self.pool = mp.get_context("spawn").Pool(self.procs, initializer=_worker_init)
+            self.pool.map(_worker_run, [(self.states[:, :1], self.knots[:1, :, :])] * self.procs)
+        else:
+            from oracle import oracle as O
+            self.orc = O.Oracle(scene, S.SolverConfig(tol=FP32_TOL))
+            B = SP.basis(OPT_T, self.knots.shape[2], H)
+            self.orc.step(self.states[:, 0], B[0] @ self.knots[0].T, H)
+
+    def iteration(self):
+        """One Adam iteration over the sample; returns (world-steps, seconds)."""
         t0 = time.perf_counter()
-        n = _oracle_chunk_worlds(states[:, :W], controls[:, :, :W], g[:, :W], orc)
-        dt = time.perf_counter() - t0
-        how = "single thread"
-    else:
-        import multiprocessing as mp
-        per = args.cpu_worlds
-        jobs = [(states[:, k * per:(k + 1) * per], controls[:, :, k * per:(k + 1) * per], g[:, k * per:(k + 1) * per])
-                for k in range(procs)]
-        with mp.get_context("spawn").Pool(procs, initializer=_worker_init) as pool:
-            pool.map(_worker_run, [(j[0][:, :1], j[1][:, :, :1], j[2][:, :1]) for j in jobs])    # warm: load, first call
-            t0 = time.perf_counter()
-            n = sum(pool.map(_worker_run, jobs))
-            dt = time.perf_counter() - t0
-        how = f"{procs} processes, one oracle each"
-    return {"value": n / dt, "unit": UNIT, "cores": procs, "kind": "oracle",
-            "sample": f"{W} worlds x {CHUNK}-step chunk, forward + adjoint (the adjoint call re-solves the step), "
-                      f"{how}, {dt:.1f} s"}
+        if self.pool is not None:
+            bounds = np.linspace(0, self.n, self.procs + 1).astype(int)
+            jobs = [(self.states[:, a:b], self.knots[a:b]) for a, b in zip(bounds[:-1], bounds[1:])]
+            res = [r for part in self.pool.map(_worker_run, jobs) for r in part]
+        else:
+            B = SP.basis(OPT_T, self.knots.shape[2], H)
+            res = [_oracle_opt_world(self.states[:, w], self.knots[w], B, self.orc) for w in range(self.n)]
+        grad = np.stack([r[1] for r in res])
+        # Adam (lr 0.3, betas 0.9 / 0.999, eps 1e-8), as torch.optim.Adam
+        self.t += 1
+        self.m1 = 0.9 * self.m1 + 0.1 * grad
+        self.m2 = 0.999 * self.m2 + 0.001 * grad * grad
+        mh, vh = self.m1 / (1.0 - 0.9 ** self.t), self.m2 / (1.0 - 0.999 ** self.t)
+        self.knots = self.knots - 0.3 * mh / (np.sqrt(vh) + 1e-8)
+        return self.n * OPT_T, time.perf_counter() - t0
+
+    def describe(self, dt):
+        how = f"{self.procs} processes, one oracle each" if self.pool is not None else "single thread"
+        return (f"{self.n} worlds x one Adam iteration over T = {OPT_T} (forward rollout, then every step "
+                f"re-solved with its adjoint, then the knot update), {how}, {dt:.1f} s")
+
+    def close(self):
+        if self.pool is not None:
+            self.pool.close()
+            self.pool.join()
+
+
+def run_cpu_baseline(args):
+    """FP64 oracle on one host thread: one Adam iteration of the optimisation workload on a
+    bounded sample of args.cpu_worlds worlds."""
+    smp = OracleOptSample(max(1, args.cpu_worlds), procs=1)
+    n, dt = smp.iteration()
+    return {"value": n / dt, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": smp.describe(dt)}
+
+
+def opt_config(W):
+    """The optimisation workload's `config` (both arms)."""
+    return {"workload": f"robot_over_box_{W}_worlds_fp32_adam_T{OPT_T}_ckpt{CHUNK}",
+            "worlds_per_gpu": W, "horizon_steps": OPT_T, "h": H, "checkpoint_every": CHUNK,
+            "step": "one Adam iteration (lr 0.3) on 8-knot wheel splines: T forward steps, the backward's "
+                    "T recomputed steps and T adjoint steps; world-steps = W x T per iteration",
+            "newton_budget": S.SolverConfig().budget, "tol": FP32_TOL}
 
 
 # ---------------------------------------------------------------------------
@@ -839,7 +889,10 @@ def main():
     ap.add_argument("--linear-solvers", type=int, default=1,
                     help="1: time the direct factor against PCR (robot and terrain legs); 0: skip")
     ap.add_argument("--plain-worlds", type=int, default=512)
-    ap.add_argument("--cpu-worlds", type=int, default=24)
+    ap.add_argument("--cpu-worlds", type=int, default=48,
+                    help="worlds of the cpu_baseline sample (one Adam iteration on one host thread)")
+    ap.add_argument("--ref-worlds", type=int, default=8,
+                    help="worlds per process of the reference arm's sample (each step one Adam iteration)")
     ap.add_argument("--cpu-procs", type=int, default=0,
                     help="processes for the reference arm's oracle (0: all host cores)")
     ap.add_argument("--skip-extras", action="store_true",
@@ -849,19 +902,22 @@ def main():
     if args.impl == "reference":
         if rank != 0:
             return
-        times = []
         procs = max(1, args.cpu_procs or (os.cpu_count() or 1))
+        smp = OracleOptSample(args.ref_worlds * procs, procs=procs)
         for _ in range(args.warmup):
-            run_cpu_baseline(args, procs=procs)
-        for _ in range(args.steps):
-            times.append(run_cpu_baseline(args, procs=procs))
-        v = statistics.median(t["value"] for t in times)
+            smp.iteration()
+        runs = [smp.iteration() for _ in range(args.steps)]
+        smp.close()
+        vals = [n / dt for n, dt in runs]
+        v = statistics.median(vals)
+        dt_med = statistics.median(dt for _, dt in runs)
         line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
-                "warmup": args.warmup, "ms_per_step": 1e3 * args.cpu_worlds * procs * CHUNK / v,
+                "warmup": args.warmup, "ms_per_step": 1e3 * dt_med,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-                "config": {"workload": "robot_over_box_8192_worlds_fp32_fwd_adj_chunk10",
-                           "sample_worlds": args.cpu_worlds * procs},
-                "cpu_baseline": dict(times[-1], value=v),
+                "config": dict(opt_config(args.worlds), sample_worlds=smp.n,
+                               parallelism=f"oracle on {procs} host processes"),
+                "cpu_baseline": {"value": v, "unit": UNIT, "cores": procs, "kind": "oracle",
+                                 "sample": smp.describe(dt_med) + " (median step)"},
                 "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
         print(json.dumps(line))
         return

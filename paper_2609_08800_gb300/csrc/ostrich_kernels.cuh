@@ -1617,18 +1617,45 @@ __device__ __forceinline__ void step_world(const DevScene& sc, WS<Real>& w, cons
     for (int i = tid; i < m; i += nth) w.lk[i] = qnan;
     __syncthreads();
   }
-  for (k = 0; k < sc.budget && !nan0; ++k) {
-    if (k >= sc.kmin && merit < best) {
-      best = merit; best_k = k;
-      for (int i = tid; i < 6 * nb; i += nth) w.ub[i] = w.uk[i];
-      for (int i = tid; i < m; i += nth) w.lb[i] = w.lk[i];
+  uint32_t status = 0;
+  Real mret = merit;
+  for (k = 0;; ++k) {
+    bool fin = nan0 || k >= sc.budget;
+    if (!fin) {
+      if (k >= sc.kmin && merit < best) {
+        best = merit; best_k = k;
+        for (int i = tid; i < 6 * nb; i += nth) w.ub[i] = w.uk[i];
+        for (int i = tid; i < m; i += nth) w.lb[i] = w.lk[i];
+      }
+      if (merit < tol2) { conv = 1; fin = true; }
     }
-    if (merit < tol2) { conv = 1; break; }
+    if (fin) {
+      // the returned iterate: the last one, or the best from k_min on.  The workspace holds
+      // the evaluation of (uk, lk) -- the last one the loop made -- unless the best
+      // iterate is restored (or the iterate was set to NaN).
+      bool evald = !nan0;
+      if (!conv) {
+        if (k >= sc.kmin && merit < best) { best = merit; best_k = k; }
+        else if (best_k >= 0) {
+          for (int i = tid; i < 6 * nb; i += nth) w.uk[i] = w.ub[i];
+          for (int i = tid; i < m; i += nth) w.lk[i] = w.lb[i];
+          merit = best;
+          evald = false;
+        }
+        status |= 1u;
+      }
+      __syncthreads();
+      mret = evald ? merit : evaluate(sc, w, w.uk, w.lk, h);
+      // a recording direct-mode step factors the returned iterate for the tape at the
+      // loop's own assembly and factorisation below; otherwise the loop ends here
+      if (!(tpw && sc.lin == LIN_DIRECT)) break;
+    }
     // Schur step, Eq. (12): (h J M^-1 J^T + C + delta) dl = J M^-1 r_dyn - rhat, by the
     // block-arrowhead factor or by PCR (the preconditioner formed at this iterate)
     if (sc.lin == LIN_DIRECT) {
       assemble(sc, w, h);
       factor(sc, w, h);
+      if (fin) break;
     } else if (sc.pc == PC_BLOCK) {
       assemble(sc, w, h);
       factor_blocks(sc, w);
@@ -1681,32 +1708,12 @@ __device__ __forceinline__ void step_world(const DevScene& sc, WS<Real>& w, cons
     if (trace && tid == 0) trace[k + 1] = (double)merit;
     __syncthreads();
   }
-  uint32_t status = 0;
-  // the workspace holds the evaluation of (uk, lk) -- the last one the loop made -- unless
-  // the best iterate is restored (or the iterate was set to NaN)
-  bool evald = !nan0;
-  if (!conv) {
-    if (k >= sc.kmin && merit < best) { best = merit; best_k = k; }
-    else if (best_k >= 0) {
-      for (int i = tid; i < 6 * nb; i += nth) w.uk[i] = w.ub[i];
-      for (int i = tid; i < m; i += nth) w.lk[i] = w.lb[i];
-      merit = best;
-      evald = false;
-    }
-    status |= 1u;
-  }
-  __syncthreads();
-  // the returned iterate: its Jacobian, compliance and Schur factor go to the tape
-  const Real mret = evald ? merit : evaluate(sc, w, w.uk, w.lk, h);
   if (!(mret == mret) || !(fabs((double)mret) < 1e300)) status |= 2u;
   status |= (uint32_t)w.ints[7];
   if (tpw) {
-    // the direct mode records the factor at the returned iterate; PCR records no matrix
-    // (the adjoint forms its operator and preconditioner at the taped iterate)
-    if (sc.lin == LIN_DIRECT) {
-      assemble(sc, w, h);
-      factor(sc, w, h);
-    }
+    // the returned iterate with (direct mode) its Schur factor, formed by the loop's last
+    // pass; PCR records no matrix (the adjoint forms its operator and preconditioner at
+    // the taped iterate)
     Real* tp = tpw;
     for (int i = tid; i < 7 * nb; i += nth) tp[tl.off_qm + i] = w.qm[i];
     for (int i = tid; i < 6 * nb; i += nth) { tp[tl.off_um + i] = w.um[i]; tp[tl.off_u + i] = w.uk[i]; }

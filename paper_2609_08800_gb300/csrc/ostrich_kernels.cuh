@@ -1595,31 +1595,58 @@ __device__ __forceinline__ void step_world(const DevScene& sc, WS<Real>& w, cons
   Src<Real> sb = {ctl ? ctl + world : sin, ctl ? (size_t)ld : (size_t)0};
   world_setup<Real>(sc, w, sq, su, sb, h, tpw ? tpw + tl.off_ct : nullptr);
   const int m = w.ints[0];
-  // warm start: lambda from the previous step on the active rows
-  for (int i = tid; i < m; i += nth) w.lk[i] = sin[(size_t)(13 * nb + w.meta[4 * i + 3]) * ld + world];
+  // warm start: lambda from the previous step on the active rows, into the trial buffers;
+  // the loop's evaluation takes it as its first trial
+  for (int i = tid; i < 6 * nb; i += nth) w.ut[i] = w.uk[i];
+  for (int i = tid; i < m; i += nth) w.lt[i] = sin[(size_t)(13 * nb + w.meta[4 * i + 3]) * ld + world];
   __syncthreads();
-  clamp_cone(sc, w, w.lk);
+  clamp_cone(sc, w, w.lt);
   __syncthreads();
-  Real merit = evaluate(sc, w, w.uk, w.lk, h);
   double* trace = a.trace ? a.trace + (size_t)world * (sc.budget + 2) : nullptr;
-  if (trace && tid == 0) trace[0] = (double)merit;
+  Real merit = Real(0);
   Real best = Real(INFINITY);
   int best_k = -1, k = 0, conv = 0;
   const Real tol2 = Real(sc.tol) * Real(sc.tol);
   const int n_alpha = sc.ls ? 4 : 1;
-  // A NaN merit at the warm start (a non-finite input, or an input that has blown up)
-  // makes every Newton step NaN: the iterate is set to NaN at once instead of after the
-  // whole budget of NaN iterations, and the step returns it with status bits 1 and 2.
-  const bool nan0 = !(merit == merit);
-  if (nan0) {
-    const Real qnan = Real(NAN);
-    for (int i = tid; i < 6 * nb; i += nth) w.uk[i] = qnan;
-    for (int i = tid; i < m; i += nth) w.lk[i] = qnan;
-    __syncthreads();
-  }
+  bool warm = true, nan0 = false;
   uint32_t status = 0;
   Real mret = merit;
-  for (k = 0;; ++k) {
+  Real alpha = Real(1);
+  int ai = 0;
+  for (;;) {
+    // the trial iterate's evaluation (first the warm start); step control: the full step
+    // (Sec. III-C) or backtracking on the merit
+    const Real mt = evaluate(sc, w, w.ut, w.lt, h);
+    if (!warm && !(mt < merit) && ai + 1 < n_alpha) {
+      ++ai;
+      alpha *= Real(0.5);
+      for (int i = tid; i < 6 * nb; i += nth) w.ut[i] = w.uk[i] + alpha * w.du[i];
+      for (int i = tid; i < m; i += nth) w.lt[i] = w.lk[i] + alpha * w.dl[i];
+      __syncthreads();
+      clamp_cone(sc, w, w.lt);
+      __syncthreads();
+      continue;
+    }
+    for (int i = tid; i < 6 * nb; i += nth) w.uk[i] = w.ut[i];
+    for (int i = tid; i < m; i += nth) w.lk[i] = w.lt[i];
+    merit = mt;
+    if (trace && tid == 0) trace[warm ? 0 : k + 1] = (double)merit;
+    if (warm) {
+      warm = false;
+      // A NaN merit at the warm start (a non-finite input, or an input that has blown up)
+      // makes every Newton step NaN: the iterate is set to NaN at once instead of after
+      // the whole budget of NaN iterations, and the step returns it with status bits 1 and 2.
+      nan0 = !(merit == merit);
+      if (nan0) {
+        __syncthreads();
+        const Real qnan = Real(NAN);
+        for (int i = tid; i < 6 * nb; i += nth) w.uk[i] = qnan;
+        for (int i = tid; i < m; i += nth) w.lk[i] = qnan;
+      }
+    } else {
+      ++k;
+    }
+    __syncthreads();
     bool fin = nan0 || k >= sc.budget;
     if (!fin) {
       if (k >= sc.kmin && merit < best) {
@@ -1690,22 +1717,13 @@ __device__ __forceinline__ void step_world(const DevScene& sc, WS<Real>& w, cons
       minv6(sc, w, b, t, w.du + 6 * b);
     }
     __syncthreads();
-    // step control: full step (Sec. III-C) or backtracking on the merit
-    Real alpha = Real(1), mt = merit;
-    for (int ai = 0; ai < n_alpha; ++ai) {
-      if (ai > 0) alpha *= Real(0.5);
-      for (int i = tid; i < 6 * nb; i += nth) w.ut[i] = w.uk[i] + alpha * w.du[i];
-      for (int i = tid; i < m; i += nth) w.lt[i] = w.lk[i] + alpha * w.dl[i];
-      __syncthreads();
-      clamp_cone(sc, w, w.lt);
-      __syncthreads();
-      mt = evaluate(sc, w, w.ut, w.lt, h);
-      if (mt < merit) break;
-    }
-    for (int i = tid; i < 6 * nb; i += nth) w.uk[i] = w.ut[i];
-    for (int i = tid; i < m; i += nth) w.lk[i] = w.lt[i];
-    merit = mt;
-    if (trace && tid == 0) trace[k + 1] = (double)merit;
+    // the full-step trial
+    ai = 0;
+    alpha = Real(1);
+    for (int i = tid; i < 6 * nb; i += nth) w.ut[i] = w.uk[i] + alpha * w.du[i];
+    for (int i = tid; i < m; i += nth) w.lt[i] = w.lk[i] + alpha * w.dl[i];
+    __syncthreads();
+    clamp_cone(sc, w, w.lt);
     __syncthreads();
   }
   if (!(mret == mret) || !(fabs((double)mret) < 1e300)) status |= 2u;

@@ -1258,39 +1258,42 @@ __device__ void schur_solve(const DevScene& sc, WS<Real>& w, const Real* b, Real
                             int sweeps, Real stop_rel = Real(0)) {
   const int tid = threadIdx.x, nth = blockDim.x, m = w.ints[0];
   const Real hR = Real(h);
-  for (int i = tid; i < m; i += nth) x[i] = b[i];
+  // pass -1 solves for x itself (its correction from x = 0 is A^-1 b), so that one inlined
+  // copy of the arrowhead solve serves the first solve and the sweeps
+  for (int i = tid; i < m; i += nth) { x[i] = Real(0); r[i] = b[i]; }
   __syncthreads();
-  arrow_solve(sc, w, x);
   const Real delta = w.scal[2];
-  for (int sweep = 0; sweep < sweeps; ++sweep) {
-    jt_apply(sc, w, x, t6);
-    __syncthreads();
-    for (int bb = tid; bb < sc.nb; bb += nth) {
-      Real o[6];
-      minv6(sc, w, bb, t6 + 6 * bb, o);
-      for (int k = 0; k < 6; ++k) t6[6 * bb + k] = o[k];
-    }
-    __syncthreads();
-    for (int i = tid; i < m; i += nth) {
-      const Real* Ji = w.J + 12 * i;
-      int b0 = w.meta[4 * i + 1], b1 = w.meta[4 * i + 2];
-      acc2<Real> ax;
-      for (int k = 0; k < 6; ++k) ax.add_prod(Ji[k], t6[6 * b0 + k]);
-      if (b1 >= 0) for (int k = 0; k < 6; ++k) ax.add_prod(Ji[6 + k], t6[6 * b1 + k]);
-      acc2<Real> res;                   // r = b - A x, compensated throughout
-      res.add(b[i]);
-      res.add_prod(-hR, ax.s);
-      res.add_prod(-hR, ax.c);
-      res.add_prod(-(w.C[i] + delta), x[i]);
-      int t = w.meta[4 * i] & 15, sub = w.meta[4 * i] >> 4;
-      if (t == ROW_FRIC) {
-        const Real* rd = w.srad + 3 * w.ref[i];
-        if (sub == 1) { res.add_prod(-rd[0], x[i]); res.add_prod(-rd[1], x[i + 1]); }
-        else { res.add_prod(-rd[1], x[i - 1]); res.add_prod(-rd[2], x[i]); }
+  for (int sweep = -1; sweep < sweeps; ++sweep) {
+    if (sweep >= 0) {
+      jt_apply(sc, w, x, t6);
+      __syncthreads();
+      for (int bb = tid; bb < sc.nb; bb += nth) {
+        Real o[6];
+        minv6(sc, w, bb, t6 + 6 * bb, o);
+        for (int k = 0; k < 6; ++k) t6[6 * bb + k] = o[k];
       }
-      r[i] = res.value();
+      __syncthreads();
+      for (int i = tid; i < m; i += nth) {
+        const Real* Ji = w.J + 12 * i;
+        int b0 = w.meta[4 * i + 1], b1 = w.meta[4 * i + 2];
+        acc2<Real> ax;
+        for (int k = 0; k < 6; ++k) ax.add_prod(Ji[k], t6[6 * b0 + k]);
+        if (b1 >= 0) for (int k = 0; k < 6; ++k) ax.add_prod(Ji[6 + k], t6[6 * b1 + k]);
+        acc2<Real> res;                   // r = b - A x, compensated throughout
+        res.add(b[i]);
+        res.add_prod(-hR, ax.s);
+        res.add_prod(-hR, ax.c);
+        res.add_prod(-(w.C[i] + delta), x[i]);
+        int t = w.meta[4 * i] & 15, sub = w.meta[4 * i] >> 4;
+        if (t == ROW_FRIC) {
+          const Real* rd = w.srad + 3 * w.ref[i];
+          if (sub == 1) { res.add_prod(-rd[0], x[i]); res.add_prod(-rd[1], x[i + 1]); }
+          else { res.add_prod(-rd[1], x[i - 1]); res.add_prod(-rd[2], x[i]); }
+        }
+        r[i] = res.value();
+      }
+      __syncthreads();
     }
-    __syncthreads();
     arrow_solve(sc, w, r);
     Real cmax = Real(0), xmax = Real(0);
     for (int i = tid; i < m; i += nth) {
@@ -1300,7 +1303,7 @@ __device__ void schur_solve(const DevScene& sc, WS<Real>& w, const Real* b, Real
     }
     __syncthreads();
     // optional early stop once the correction no longer changes x at working precision
-    if (stop_rel > Real(0)) {
+    if (sweep >= 0 && stop_rel > Real(0)) {
       block_max2(w, cmax, xmax);
       if (cmax <= stop_rel * xmax) break;
     }

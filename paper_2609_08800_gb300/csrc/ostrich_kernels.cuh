@@ -1611,16 +1611,19 @@ __device__ __forceinline__ void step_world(const DevScene& sc, WS<Real>& w, cons
   int best_k = -1, k = 0, conv = 0;
   const Real tol2 = Real(sc.tol) * Real(sc.tol);
   const int n_alpha = sc.ls ? 4 : 1;
-  bool warm = true, nan0 = false;
+  // phase 0: the warm start; 1: a Newton trial; 2: the returned iterate when it is not the
+  // last one evaluated (the best iterate from k_min on, or the NaN iterate)
+  int phase = 0;
+  bool nan0 = false;
   uint32_t status = 0;
   Real mret = merit;
   Real alpha = Real(1);
   int ai = 0;
   for (;;) {
-    // the trial iterate's evaluation (first the warm start); step control: the full step
-    // (Sec. III-C) or backtracking on the merit
+    // the loop's one evaluation: of the trial iterate, the warm start or the returned
+    // iterate; step control: the full step (Sec. III-C) or backtracking on the merit
     const Real mt = evaluate(sc, w, w.ut, w.lt, h);
-    if (!warm && !(mt < merit) && ai + 1 < n_alpha) {
+    if (phase == 1 && !(mt < merit) && ai + 1 < n_alpha) {
       ++ai;
       alpha *= Real(0.5);
       for (int i = tid; i < 6 * nb; i += nth) w.ut[i] = w.uk[i] + alpha * w.du[i];
@@ -1632,54 +1635,49 @@ __device__ __forceinline__ void step_world(const DevScene& sc, WS<Real>& w, cons
     }
     for (int i = tid; i < 6 * nb; i += nth) w.uk[i] = w.ut[i];
     for (int i = tid; i < m; i += nth) w.lk[i] = w.lt[i];
-    merit = mt;
-    if (trace && tid == 0) trace[warm ? 0 : k + 1] = (double)merit;
-    if (warm) {
-      warm = false;
+    if (phase == 2) {
+      mret = mt;
+    } else {
+      merit = mt;
+      if (trace && tid == 0) trace[phase == 0 ? 0 : k + 1] = (double)merit;
       // A NaN merit at the warm start (a non-finite input, or an input that has blown up)
       // makes every Newton step NaN: the iterate is set to NaN at once instead of after
       // the whole budget of NaN iterations, and the step returns it with status bits 1 and 2.
-      nan0 = !(merit == merit);
-      if (nan0) {
-        __syncthreads();
-        const Real qnan = Real(NAN);
-        for (int i = tid; i < 6 * nb; i += nth) w.uk[i] = qnan;
-        for (int i = tid; i < m; i += nth) w.lk[i] = qnan;
-      }
-    } else {
-      ++k;
+      if (phase == 0) nan0 = !(merit == merit);
+      else ++k;
     }
     __syncthreads();
-    bool fin = nan0 || k >= sc.budget;
-    if (!fin) {
-      if (k >= sc.kmin && merit < best) {
-        best = merit; best_k = k;
-        for (int i = tid; i < 6 * nb; i += nth) w.ub[i] = w.uk[i];
-        for (int i = tid; i < m; i += nth) w.lb[i] = w.lk[i];
-      }
-      if (merit < tol2) { conv = 1; fin = true; }
-    }
-    if (fin) {
-      // the returned iterate: the last one, or the best from k_min on.  The workspace holds
-      // the evaluation of (uk, lk) -- the last one the loop made -- unless the best
-      // iterate is restored (or the iterate was set to NaN).
-      bool evald = !nan0;
-      if (!conv) {
-        if (k >= sc.kmin && merit < best) { best = merit; best_k = k; }
-        else if (best_k >= 0) {
-          for (int i = tid; i < 6 * nb; i += nth) w.uk[i] = w.ub[i];
-          for (int i = tid; i < m; i += nth) w.lk[i] = w.lb[i];
-          merit = best;
-          evald = false;
+    bool fin = phase == 2 || nan0 || k >= sc.budget;
+    if (phase != 2) {
+      phase = 1;
+      if (!fin) {
+        if (k >= sc.kmin && merit < best) {
+          best = merit; best_k = k;
+          for (int i = tid; i < 6 * nb; i += nth) w.ub[i] = w.uk[i];
+          for (int i = tid; i < m; i += nth) w.lb[i] = w.lk[i];
         }
-        status |= 1u;
+        if (merit < tol2) { conv = 1; fin = true; }
       }
-      __syncthreads();
-      mret = evald ? merit : evaluate(sc, w, w.uk, w.lk, h);
-      // a recording direct-mode step factors the returned iterate for the tape at the
-      // loop's own assembly and factorisation below; otherwise the loop ends here
-      if (!(tpw && sc.lin == LIN_DIRECT)) break;
+      if (fin) {
+        // the returned iterate: the last one (evaluated: the workspace holds its rows), or
+        // the best from k_min on, or the NaN iterate, which go through the evaluation first
+        mret = merit;
+        if (!conv) {
+          status |= 1u;
+          if (nan0 || (!(k >= sc.kmin && merit < best) && best_k >= 0)) {
+            const Real qnan = Real(NAN);
+            for (int i = tid; i < 6 * nb; i += nth) w.ut[i] = nan0 ? qnan : w.ub[i];
+            for (int i = tid; i < m; i += nth) w.lt[i] = nan0 ? qnan : w.lb[i];
+            __syncthreads();
+            phase = 2;
+            continue;
+          }
+        }
+      }
     }
+    // a recording direct-mode step factors the returned iterate for the tape at the loop's
+    // own assembly and factorisation below; otherwise the loop ends here
+    if (fin && !(tpw && sc.lin == LIN_DIRECT)) break;
     // Schur step, Eq. (12): (h J M^-1 J^T + C + delta) dl = J M^-1 r_dyn - rhat, by the
     // block-arrowhead factor or by PCR (the preconditioner formed at this iterate)
     if (sc.lin == LIN_DIRECT) {

@@ -69,6 +69,39 @@ __device__ __forceinline__ void contact_group(const DevScene& sc, const WS<Real>
   o.cn = dot3(n, x) - d;
 }
 
+// The contact rows of slot sl with q- in S and u+ held (real): what the q- pull-back of
+// Eq. (17) takes from them -- the signed distance cn, the row velocities vel_k = J_k u+ and
+// the products jw_k = J_k . w_u -- with the angular parts' E applied to the constant
+// vectors instead of to each row, (E a) . v = a . (E^T v); the same geometry as
+// contact_group.
+template <class S, class Real>
+__device__ __forceinline__ void contact_rows_dot(const DevScene& sc, const WS<Real>& w, int sl, int b, const S* qm7,
+                                                 const Real* u6, double h, vec3<Real> wlin, vec3<Real> wang, S& cn,
+                                                 S* vel, S* jw) {
+  const int local = sl - sc.slot_base[b];
+  S qp[7];
+  kin_body<S, Real>(qm7, u6, h, qp);
+  vec3<S> n;
+  S d;
+  const Real ns[3] = {w.sn[3 * sl], w.sn[3 * sl + 1], w.sn[3 * sl + 2]};
+  slot_frame2<S, Real>(sc, b, local, w.sftype[sl], qm7, ns, w.sd[sl], w.sedge + 2 * sl, n, d);
+  vec3<S> t1, t2;
+  tangent_basis(n, t1, t2);
+  const vec3<S> p = v3(qp[0], qp[1], qp[2]);
+  const vec3<S> x = slot_point<S>(sc, b, local, p, qp + 3, n);
+  const vec3<S> lev = x - p;
+  const vec3<Real> wk = v3(u6[3], u6[4], u6[5]), ul = v3(u6[0], u6[1], u6[2]);
+  const MapE<Real> Ek(wk, h);
+  const vec3<Real> ew = Ek.T_(wk), ea = Ek.T_(wang);
+  const vec3<S> dir[3] = {n, t1, t2};
+  for (int k = 0; k < 3; ++k) {
+    const vec3<S> a = cross3(lev, dir[k]);
+    vel[k] = dotm(dir[k], ul) + dotm(a, ew);
+    jw[k] = dotm(dir[k], wlin) + dotm(a, ea);
+  }
+  cn = dot3(n, x) - d;
+}
+
 // Friction weight W of Eq. (7) (the FB reading, cancellation-free numerator) and the
 // friction residuals v_k + (W + kappa) lambda_fk, in S; lambda enters as S so that the
 // same code differentiates along lambda_n.
@@ -227,29 +260,26 @@ __device__ Real group_vjp_q(const DevScene& sc, const WS<Real>& w, const ExWS<Re
       const D c = dot3(lift<D>(n), x) - D(w.sd[sl]);
       return (wl[i] * c / D(hR)).d;
     }
-    D qm[7], u[6];
+    D qm[7];
     for (int c = 0; c < 7; ++c) qm[c] = D(w.qm[7 * b + c], c == dc ? Real(1) : Real(0));
-    for (int c = 0; c < 6; ++c) u[c] = D(w.uk[6 * b + c]);
-    CGroup<D> g;
-    contact_group<D, Real>(sc, w, sl, b, qm, u, h, g);
-    const vec3<D> wl_ = lift<D>(v3(wu[6 * b], wu[6 * b + 1], wu[6 * b + 2]));
-    const vec3<D> wa_ = lift<D>(v3(wu[6 * b + 3], wu[6 * b + 4], wu[6 * b + 5]));
+    D cn, vel[3], jw[3];
+    contact_rows_dot<D, Real>(sc, w, sl, b, qm, w.uk + 6 * b, h, v3(wu[6 * b], wu[6 * b + 1], wu[6 * b + 2]),
+                              v3(wu[6 * b + 3], wu[6 * b + 4], wu[6 * b + 5]), cn, vel, jw);
     D acc(Real(0));
     // normal row
     const Real fs = MODE == ADJ_EXACT ? ex.fsc[sl] : Real(1);
-    acc = acc + D(wl[i] * fs) * g.cn / D(hR);
+    acc = acc + D(wl[i] * fs) * cn / D(hR);
     // friction rows
     if (MODE == ADJ_EXACT) {
       D rf[2];
-      friction_rows<D, Real>(sc, g.vel[1], g.vel[2], D(w.lk[i]), w.lk[i + 1], w.lk[i + 2], hR * w.swhat[sl],
+      friction_rows<D, Real>(sc, vel[1], vel[2], D(w.lk[i]), w.lk[i + 1], w.lk[i + 2], hR * w.swhat[sl],
                              D(Real(sc.mu)), rf);
       acc = acc + D(wl[i + 1]) * rf[0] + D(wl[i + 2]) * rf[1];
     } else {
-      acc = acc + D(wl[i + 1]) * g.vel[1] + D(wl[i + 2]) * g.vel[2];
+      acc = acc + D(wl[i + 1]) * vel[1] + D(wl[i + 2]) * vel[2];
     }
     // force terms -h lambda J . w_u of the three rows
-    for (int k = 0; k < 3; ++k)
-      acc = acc - D(hR * w.lk[i + k]) * (dot3(g.dir[k], wl_) + dot3(g.ang[k], wa_));
+    for (int k = 0; k < 3; ++k) acc = acc - D(hR * w.lk[i + k]) * jw[k];
     return acc.d;
   }
   const int j = grp - sc.n_slots, bp = sc.jp[j], bc = sc.jc[j];
@@ -272,19 +302,22 @@ __device__ Real group_vjp_q(const DevScene& sc, const WS<Real>& w, const ExWS<Re
   const vec3<Real> wca = v3(wu[6 * bc + 3], wu[6 * bc + 4], wu[6 * bc + 5]);
   const int i0 = w.ints[1] + 5 * j;
   D acc(Real(0));
+  // the rows' angular parts enter through E (u+ is constant along q-), only in products
+  // with constant vectors: (E a) . v = a . (E^T v), E^T v formed once per joint
   const MapE<Real> Ep(wp, h), Ec(wc, h);
+  const vec3<Real> epa = Ep.T_(wpa), eca = Ec.T_(wca);
   joint_rows_each<D>(sc, j, pp, rotp, pc, rotc, [&](int k, vec3<D> lp, vec3<D> ap, vec3<D> lc, vec3<D> ac, D c) {
-    const D Jw = dotm(lp, wpl) + dotm(Ep(ap), wpa) + dotm(lc, wcl) + dotm(Ec(ac), wca);
+    const D Jw = dotm(lp, wpl) + dotm(ap, epa) + dotm(lc, wcl) + dotm(ac, eca);
     acc = acc + D(wl[i0 + k]) * c / D(hR) - D(hR * w.lk[i0 + k]) * Jw;
   });
   const int is = servo_row(sc, w, j);
   if (is >= 0) {
     SRow<D> sr;
     servo_row_geom<D>(sc, j, pp, rotp, pc, rotc, sr);
-    const vec3<D> sa_p = Ep(sr.ang_p), sa_c = Ec(sr.ang_c);
-    const D sv = dotm(sr.lin_p, v3(w.uk[6 * bp], w.uk[6 * bp + 1], w.uk[6 * bp + 2])) + dotm(sa_p, wp) +
-                 dotm(sr.lin_c, v3(w.uk[6 * bc], w.uk[6 * bc + 1], w.uk[6 * bc + 2])) + dotm(sa_c, wc);
-    const D Jw = dotm(sr.lin_p, wpl) + dotm(sa_p, wpa) + dotm(sr.lin_c, wcl) + dotm(sa_c, wca);
+    const vec3<Real> epw = Ep.T_(wp), ecw = Ec.T_(wc);
+    const D sv = dotm(sr.lin_p, v3(w.uk[6 * bp], w.uk[6 * bp + 1], w.uk[6 * bp + 2])) + dotm(sr.ang_p, epw) +
+                 dotm(sr.lin_c, v3(w.uk[6 * bc], w.uk[6 * bc + 1], w.uk[6 * bc + 2])) + dotm(sr.ang_c, ecw);
+    const D Jw = dotm(sr.lin_p, wpl) + dotm(sr.ang_p, epa) + dotm(sr.lin_c, wcl) + dotm(sr.ang_c, eca);
     acc = acc + D(wl[is]) * sv - D(hR * w.lk[is]) * Jw;
     // a position target's bias (x(q-) - target)/h holds q- directly
     if (sc.smode[j] == SERVO_POSITION) acc = acc + D(wl[is]) * joint_coord_qm<D>(sc, j, qmp, qmc) / D(hR);

@@ -121,6 +121,11 @@ template <class T> struct MapE {
     const vec3<S> c = cross3(a, lift<S>(wk));
     return v3((a.x + c.x * hh) * inv, (a.y + c.y * hh) * inv, (a.z + c.z * hh) * inv);
   }
+  // the transposed map: (E a) . v = a . (E^T v), with (a x w) . v = a . (w x v)
+  __device__ __forceinline__ vec3<T> T_(vec3<T> v) const {
+    const vec3<T> c = cross3(wk, v);
+    return v3((v.x + c.x * hh) * inv, (v.y + c.y * hh) * inv, (v.z + c.z * hh) * inv);
+  }
 };
 template <class S, class T> __device__ __forceinline__ vec3<S> map_Et(vec3<S> a, vec3<T> wk, double h) {
   return MapE<T>(wk, h)(a);

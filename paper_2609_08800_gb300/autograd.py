@@ -2,9 +2,11 @@
 
 Forward runs T steps s_{t+1} = step(s_t, a_t); backward sweeps the IFT adjoint of
 each step in reverse (Sec. III-D), adding the loss's direct gradient of every state on
-the way.  With checkpointing the forward records nothing but the states; the backward
-recomputes each segment's steps into a tape of `segment` slots just before sweeping
-it, so device memory for the factors is O(segment) instead of O(T).  The kernels are
+the way.  With checkpointing the forward keeps the states and records only the last
+segment's steps into the tape of `segment` slots; the backward sweeps that segment
+straight from the tape (when nothing has recorded into the engine's tape since) and
+recomputes each earlier segment's steps into the same slots just before sweeping it,
+so device memory for the factors is O(segment) instead of O(T).  The kernels are
 deterministic, so the checkpointed gradient is bit-identical to the plain one.
 
 The stepping engine is a small object with `step(s_in, a, slot) -> s_out` and
@@ -37,10 +39,15 @@ class CudaEngine:
         self.dtype = self.ctx.dtype
         self.slots = slots
         self.n_state, self.n_servo, self.ld = self.ctx.n_state, self.ctx.n_servo, self.ctx.ld
+        # counts the recordings into the tape (steps with a slot, clears): a rollout's
+        # backward reuses the slots its forward recorded only while the count is unchanged
+        self.tape_epoch = 0
 
     def step(self, s_in, a, slot):
         out = torch.empty_like(s_in)
         self.ctx.ostrich_step(s_in, a, self.h, out, tape_slot=slot)
+        if slot >= 0:
+            self.tape_epoch += 1
         return out
 
     def adjoint(self, slot, g):
@@ -58,6 +65,7 @@ class CudaEngine:
 
     def clear(self):
         self.ctx.ostrich_tape_clear()
+        self.tape_epoch += 1
 
     def close(self):
         self.ctx.close()
@@ -79,13 +87,17 @@ class _Rollout(torch.autograd.Function):
     def forward(fctx, s0, controls, theta, engine, segment):
         T = controls.shape[0]
         ckpt = segment is not None and segment < T
+        # with checkpointing, the last segment's steps are recorded now (slots 0, 1, ...),
+        # so that the backward need not recompute them
+        t_last = ((T - 1) // segment) * segment if ckpt else 0
         states = [s0]
         with torch.no_grad():
             for t in range(T):
-                slot = -1 if ckpt else t
+                slot = (t - t_last if t >= t_last else -1) if ckpt else t
                 states.append(engine.step(states[t], controls[t], slot))
         traj = torch.stack(states)
         fctx.engine, fctx.segment, fctx.ckpt = engine, segment, ckpt
+        fctx.tape_epoch = getattr(engine, "tape_epoch", None)
         fctx.with_theta = theta is not None
         fctx.theta_shape = None if theta is None else theta.shape
         fctx.theta_dtype = None if theta is None else theta.dtype
@@ -104,7 +116,11 @@ class _Rollout(torch.autograd.Function):
         n_seg = math.ceil(T / seg)
         for k in reversed(range(n_seg)):
             t0, t1 = k * seg, min(T, (k + 1) * seg)
-            if ckpt:
+            # the last segment is still on the tape if nothing recorded into it since the
+            # forward (an engine without a recording count always recomputes)
+            taped = k == n_seg - 1 and fctx.tape_epoch is not None \
+                and getattr(engine, "tape_epoch", None) == fctx.tape_epoch
+            if ckpt and not taped:
                 # recompute the segment into slots 0..t1-t0-1 (deterministic: same factors)
                 with torch.no_grad():
                     s = traj[t0]

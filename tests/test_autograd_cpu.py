@@ -182,3 +182,60 @@ def test_theta_must_be_the_scene_parameters():
     theta = scene_theta(sc) * 1.01
     with pytest.raises(ValueError):
         rollout(st.clone(), ctl.clone(), OracleEngine(sc, cfg, 0.1, O.ADJ_PAPER), theta=theta)
+
+
+class CountingEngine(OracleEngine):
+    """The oracle engine with the recording count the rollout's tape reuse reads, and a
+    count of the steps it takes."""
+
+    def __init__(self, *a):
+        super().__init__(*a)
+        self.tape_epoch = 0
+        self.steps = 0
+
+    def step(self, s_in, a, slot):
+        self.steps += 1
+        if slot >= 0:
+            self.tape_epoch += 1
+        return super().step(s_in, a, slot)
+
+
+def test_checkpointed_backward_reuses_the_last_segment():
+    """With checkpoints every 4 of 6 steps, the forward records steps 4-5 and the
+    backward recomputes only steps 0-3 (10 steps in all), with the plain gradient."""
+    sc, st, ctl, cfg = _setup()
+    ref = OracleEngine(sc, cfg, 0.1, O.ADJ_PAPER)
+    s0 = st.clone().requires_grad_(True)
+    u = ctl.clone().requires_grad_(True)
+    _loss(rollout(s0, u, ref), sc).backward()
+    eng = CountingEngine(sc, cfg, 0.1, O.ADJ_PAPER)
+    s1 = st.clone().requires_grad_(True)
+    u1 = ctl.clone().requires_grad_(True)
+    _loss(rollout(s1, u1, eng, segment=4), sc).backward()
+    assert eng.steps == 6 + 4
+    assert torch.equal(s1.grad, s0.grad) and torch.equal(u1.grad, u.grad)
+
+
+def test_checkpointed_backward_recomputes_an_overwritten_last_segment():
+    """Two rollouts on one engine, backward in either order: the second forward's
+    recording overwrites the first one's last segment, so the first one's backward
+    recomputes it; both gradients equal their plain ones."""
+    sc, st, ctl, cfg = _setup()
+    st2 = st.clone()
+    st2[35] += 0.3                       # chassis vx
+    plain = []
+    for s in (st, st2):
+        s0 = s.clone().requires_grad_(True)
+        u = ctl.clone().requires_grad_(True)
+        _loss(rollout(s0, u, OracleEngine(sc, cfg, 0.1, O.ADJ_PAPER)), sc).backward()
+        plain.append((s0.grad, u.grad))
+    eng = CountingEngine(sc, cfg, 0.1, O.ADJ_PAPER)
+    ins = [(s.clone().requires_grad_(True), ctl.clone().requires_grad_(True)) for s in (st, st2)]
+    losses = [_loss(rollout(s0, u, eng, segment=4), sc) for s0, u in ins]
+    assert eng.steps == 12
+    losses[0].backward()                 # its last segment was overwritten: recomputed
+    assert eng.steps == 12 + 6
+    losses[1].backward()                 # the first backward recorded since: recomputed
+    assert eng.steps == 12 + 12
+    for (s0, u), (gs, gu) in zip(ins, plain):
+        assert torch.equal(s0.grad, gs) and torch.equal(u.grad, gu)

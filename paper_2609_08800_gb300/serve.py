@@ -14,9 +14,11 @@ neither small nor large requests starve).  Columns are released when the request
 results have reached the host.
 
 Every tick each pool issues, on its step stream, one `ostrich_step_list` over the
-columns of all its requests that are stepping forward (no record) or re-running a
-checkpointed segment (recording slot t - t0), and, on its adjoint stream, one
-`ostrich_adjoint_list` over the columns of all requests sweeping a segment backwards.
+columns of all its requests that are stepping forward (no record, except that a
+forward+adjoint request records its last segment, so that its backward sweep starts
+without a re-run) or re-running a checkpointed segment (recording slot t - t0), and, on
+its adjoint stream, one `ostrich_adjoint_list` over the columns of all requests sweeping
+a segment backwards.
 Requests at different steps of different horizons therefore share launches; the two
 streams of a pool and the pools themselves run concurrently.  Tick t of the step
 stream waits for tick t-1 of the adjoint stream and vice versa, which orders every
@@ -269,9 +271,14 @@ class Server:
             if r._finish_pending:
                 continue
             if r.phase == FWD and r.t < r.T:
-                if r.adjoint and r.t % K == 0:
+                # a forward+adjoint request checkpoints every segment start but the last
+                # and records the last segment's steps (slot t - t_last)
+                t_last = ((r.T - 1) // K) * K
+                rec = r.adjoint and r.t >= t_last
+                if r.adjoint and r.t % K == 0 and not rec:
                     saves.append(r)
-                step_w.append(r.cols); step_s.append(np.full(r.n, -1)); step_t.append(np.full(r.n, r.t))
+                step_w.append(r.cols); step_s.append(np.full(r.n, r.t - t_last if rec else -1))
+                step_t.append(np.full(r.n, r.t))
             elif r.phase == REC:
                 t0 = r.seg * K
                 if r.t == t0:
@@ -325,8 +332,9 @@ class Server:
                     if r.t == r.T and not r.adjoint:
                         finish_a.append(r)
                 elif r in to_bwd:
-                    r.phase, r.seg = REC, (r.T - 1) // K
-                    r.t = r.seg * K
+                    # the last segment is on the tape: its adjoint sweep starts at once
+                    r.phase, r.seg = ADJ, (r.T - 1) // K
+                    r.t = r.T - 1
             elif r.phase == REC:
                 r.t += 1
                 if r.t == min(r.T, (r.seg + 1) * K):
@@ -488,12 +496,15 @@ class PlainServer:
         g = torch.empty(2, ns, n, dtype=dt, device="cuda")
         dct = torch.zeros(r.T, max(nsv, 1), n, dtype=dt, device="cuda")
         fin = torch.empty(ns, n, dtype=dt, device="cuda")
+        t_last = (n_seg - 1) * K
         for w in range(n):
             cur = 0
             for t in range(r.T):
-                if r.adjoint and t % K == 0:
+                rec = r.adjoint and t >= t_last
+                if r.adjoint and t % K == 0 and not rec:
                     ck[t // K, :, w] = st[cur, :, w]
-                ctx.ostrich_step(_Column(st[cur], w), _Column(CT[t], w), p.h, _Column(st[1 - cur], w))
+                ctx.ostrich_step(_Column(st[cur], w), _Column(CT[t], w), p.h, _Column(st[1 - cur], w),
+                                 tape_slot=t - t_last if rec else -1)
                 cur = 1 - cur
             fin[:, w] = st[cur, :, w]
             if not r.adjoint:
@@ -503,12 +514,13 @@ class PlainServer:
             gc = 0
             for k in reversed(range(n_seg)):
                 t0, t1 = k * K, min(r.T, (k + 1) * K)
-                st[0, :, w] = ck[k, :, w]
-                cur = 0
-                for t in range(t0, t1):
-                    ctx.ostrich_step(_Column(st[cur], w), _Column(CT[t], w), p.h, _Column(st[1 - cur], w),
-                                     tape_slot=t - t0)
-                    cur = 1 - cur
+                if k < n_seg - 1:                # the last segment was recorded by the forward
+                    st[0, :, w] = ck[k, :, w]
+                    cur = 0
+                    for t in range(t0, t1):
+                        ctx.ostrich_step(_Column(st[cur], w), _Column(CT[t], w), p.h, _Column(st[1 - cur], w),
+                                         tape_slot=t - t0)
+                        cur = 1 - cur
                 for t in reversed(range(t0, t1)):
                     ctx.ostrich_adjoint(t - t0, _Column(g[gc], w), p.h, _Column(g[1 - gc], w),
                                         _Column(dct[t], w) if nsv else None)

@@ -259,7 +259,7 @@ def run_ours(args, rank, world_size, local_rank):
     sm_mhz = (clocks or {}).get("sm_mhz") or measured_peaks().get("sm_max_mhz", 2070.0)
     peak_derived = SM_COUNT_GB300 * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
     chunk_value = W * CHUNK * world_size / (ms * 1e-3)
-    traj_b, seg_b = (OPT_T + 1) * ctx.n_state * W * 4, ctx.tape_bytes()
+    traj_b, seg_b = (OPT_T + 1) * ctx.n_state * W * 4, CHUNK * ctx.tape_bytes()     # tape_bytes: one slot
     l2_note = (f"trajectory {traj_b / 1e9:.2f} GB and tape of one segment {seg_b / 1e9:.2f} GB per iteration "
                + ("> 129 MB L2 (no flush needed)" if min(traj_b, seg_b) > L2_BYTES else
                   "(at this world count not all beyond the 129 MB L2: not a bench-sized run)"))

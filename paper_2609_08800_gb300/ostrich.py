@@ -118,7 +118,7 @@ def scene_desc(scene: "S.Scene") -> SceneDesc:
         d.hm_spacing = scene.env.spacing
         d.hm_origin[0], d.hm_origin[1] = scene.env.origin
         d.heights = hts.ctypes.data_as(ctypes.POINTER(ctypes.c_float))
-        d._heights = hts          # keeps the host array alive while the descriptor is
+        d._heights = hts          # keeps the host array alive as long as the descriptor
     for i, b in enumerate(scene.bodies):
         bd = d.bodies[i]
         bd.mass = b.mass
@@ -160,6 +160,22 @@ def _ptr(t):
     return ctypes.c_void_p(t.data_ptr())
 
 
+def _checked(t, dtype, numel, what):
+    """Device pointer of `t` after checking what the library assumes of it through the
+    raw pointer: element type `dtype` and at least `numel` elements (a smaller array
+    would be read or written past its end on the device).  Objects without a dtype --
+    the column addresses of a wider array that the one-world-per-launch form passes --
+    go to _ptr unchecked."""
+    if t is None:
+        return None
+    if hasattr(t, "dtype"):
+        if t.dtype != dtype:
+            raise ValueError(f"{what}: expected element type {dtype}, got {t.dtype}")
+        if t.numel() < numel:
+            raise ValueError(f"{what}: needs at least {numel} elements, got {t.numel()} (shape {tuple(t.shape)})")
+    return _ptr(t)
+
+
 def _stream(stream):
     if stream is None:
         import torch
@@ -174,10 +190,19 @@ def ostrich_step_adjoint_noalloc(scene, cfg, n_worlds, state_in, controls, h, st
                                  dL_dcontrols=None, ld=0, stream=None):
     """Step + adjoint with the tape in the library's fixed array (no device allocation);
     FP32 tensors [rows, ld].  Raises on a non-OK status (EINVAL beyond the array's size)."""
+    import torch
     d, c = scene_desc(scene), solver_cfg(cfg)
-    rc = lib().ostrich_step_adjoint_noalloc(ctypes.byref(d), ctypes.byref(c), int(n_worlds), int(ld), _ptr(state_in),
-                                            _ptr(controls), float(h), _ptr(state_out), _ptr(dL_dnext),
-                                            _ptr(dL_dstate), _ptr(dL_dcontrols), _stream(stream))
+    W, L = int(n_worlds), int(ld) or int(n_worlds)
+
+    def arr(t, rows, what):
+        return _checked(t, torch.float32, (rows - 1) * L + W if rows > 0 else 0, what)
+
+    ns, nsv = scene.n_state, scene.n_servos
+    rc = lib().ostrich_step_adjoint_noalloc(ctypes.byref(d), ctypes.byref(c), W, int(ld),
+                                            arr(state_in, ns, "state_in"), arr(controls, nsv, "controls"), float(h),
+                                            arr(state_out, ns, "state_out"), arr(dL_dnext, ns, "dL_dnext"),
+                                            arr(dL_dstate, ns, "dL_dstate"), arr(dL_dcontrols, nsv, "dL_dcontrols"),
+                                            _stream(stream))
     if rc != OSTRICH_OK:
         raise RuntimeError(f"ostrich_step_adjoint_noalloc failed with status {rc}")
 
@@ -236,6 +261,15 @@ class Context:
         if getattr(cfg, "linear_solver", LIN_DIRECT) != LIN_DIRECT:
             self.set_linear_solver(cfg.linear_solver, cfg.precond, cfg.pcr_iters, cfg.pcr_iters_adj, cfg.pcr_rtol_adj)
 
+    def _arr(self, t, rows, what):
+        """A [rows, ld] array of the context's element type (the library touches element
+        c * ld + w for c < rows and every world w < n_worlds)."""
+        return _checked(t, self.dtype, (rows - 1) * self.ld + self.n_worlds if rows > 0 else 0, what)
+
+    def _i32(self, t, n, what):
+        import torch
+        return _checked(t, torch.int32, n, what)
+
     def _check(self, rc, what):
         if rc != OSTRICH_OK:
             msg = lib().ostrich_last_error(self._h).decode()
@@ -252,25 +286,39 @@ class Context:
 
     def ostrich_step(self, state_in, controls, h, state_out, impulses=None, ids=None, status=None, iters=None,
                      tape_slot=-1, stream=None):
-        self._check(lib().ostrich_step(self._h, _ptr(state_in), _ptr(controls), float(h), _ptr(state_out),
-                                       _ptr(impulses), _ptr(ids), _ptr(status), _ptr(iters), int(tape_slot),
+        self._check(lib().ostrich_step(self._h, self._arr(state_in, self.n_state, "state_in"),
+                                       self._arr(controls, self.n_servo, "controls"), float(h),
+                                       self._arr(state_out, self.n_state, "state_out"),
+                                       self._arr(impulses, self.m_max, "impulses"),
+                                       self._i32(ids, (self.n_slots - 1) * self.ld + self.n_worlds if self.n_slots
+                                                 else 0, "ids"),
+                                       self._i32(status, self.n_worlds, "status"),
+                                       self._i32(iters, self.n_worlds, "iters"), int(tape_slot),
                                        _stream(stream)), "ostrich_step")
 
     def ostrich_adjoint(self, tape_slot, dL_dnext, h, dL_dstate, dL_dcontrols=None, stream=None):
-        self._check(lib().ostrich_adjoint(self._h, int(tape_slot), _ptr(dL_dnext), float(h), _ptr(dL_dstate),
-                                          _ptr(dL_dcontrols), _stream(stream)), "ostrich_adjoint")
+        self._check(lib().ostrich_adjoint(self._h, int(tape_slot), self._arr(dL_dnext, self.n_state, "dL_dnext"),
+                                          float(h), self._arr(dL_dstate, self.n_state, "dL_dstate"),
+                                          self._arr(dL_dcontrols, self.n_servo, "dL_dcontrols"), _stream(stream)),
+                    "ostrich_adjoint")
 
     def ostrich_adjoint_params(self, tape_slot, dL_dnext, h, dL_dstate, dL_dcontrols=None, dL_dkp=None,
                                dL_dmass=None, dL_dinertia=None, dL_dmu=None, stream=None):
-        self._check(lib().ostrich_adjoint_params(self._h, int(tape_slot), _ptr(dL_dnext), float(h), _ptr(dL_dstate),
-                                                 _ptr(dL_dcontrols), _ptr(dL_dkp), _ptr(dL_dmass), _ptr(dL_dinertia),
-                                                 _ptr(dL_dmu), _stream(stream)),
+        self._check(lib().ostrich_adjoint_params(self._h, int(tape_slot), self._arr(dL_dnext, self.n_state, "dL_dnext"),
+                                                 float(h), self._arr(dL_dstate, self.n_state, "dL_dstate"),
+                                                 self._arr(dL_dcontrols, self.n_servo, "dL_dcontrols"),
+                                                 self._arr(dL_dkp, self.n_servo, "dL_dkp"),
+                                                 self._arr(dL_dmass, self.nb, "dL_dmass"),
+                                                 self._arr(dL_dinertia, 3 * self.nb, "dL_dinertia"),
+                                                 _checked(dL_dmu, self.dtype, self.n_worlds, "dL_dmu"), _stream(stream)),
                     "ostrich_adjoint_params")
 
     def set_adjoint_mode(self, mode, krylov_iters=None):
         """ADJ_PAPER (the paper's frozen-W adjoint, default) or ADJ_EXACT (the exact IFT by
         GMRES on the taped factor); krylov_iters: optional int32 device tensor [n_worlds]."""
-        self._check(lib().ostrich_set_adjoint_mode(self._h, int(mode), _ptr(krylov_iters)), "ostrich_set_adjoint_mode")
+        self._check(lib().ostrich_set_adjoint_mode(self._h, int(mode), self._i32(krylov_iters, self.n_worlds,
+                                                                                 "krylov_iters")),
+                    "ostrich_set_adjoint_mode")
         self.adj_mode = int(mode)
 
     def set_linear_solver(self, solver, precond=PC_JACOBI, iters=16, adj_iters=256, adj_rtol=0.0):
@@ -282,18 +330,32 @@ class Context:
 
     def ostrich_step_list(self, state_in, controls, h, state_out, worlds, tape_slots=None, impulses=None, ids=None,
                           status=None, iters=None, stream=None):
-        self._check(lib().ostrich_step_list(self._h, _ptr(state_in), _ptr(controls), float(h), _ptr(state_out),
-                                            _ptr(impulses), _ptr(ids), _ptr(status), _ptr(iters), _ptr(worlds),
-                                            _ptr(tape_slots), int(worlds.numel()), _stream(stream)),
+        n = int(worlds.numel())
+        self._check(lib().ostrich_step_list(self._h, self._arr(state_in, self.n_state, "state_in"),
+                                            self._arr(controls, self.n_servo, "controls"), float(h),
+                                            self._arr(state_out, self.n_state, "state_out"),
+                                            self._arr(impulses, self.m_max, "impulses"),
+                                            self._i32(ids, (self.n_slots - 1) * self.ld + self.n_worlds if self.n_slots
+                                                      else 0, "ids"),
+                                            self._i32(status, self.n_worlds, "status"),
+                                            self._i32(iters, self.n_worlds, "iters"), self._i32(worlds, n, "worlds"),
+                                            self._i32(tape_slots, n, "tape_slots"), n, _stream(stream)),
                     "ostrich_step_list")
 
     def ostrich_adjoint_list(self, dL_dnext, h, dL_dstate, worlds, tape_slots, dL_dcontrols=None, stream=None):
-        self._check(lib().ostrich_adjoint_list(self._h, _ptr(dL_dnext), float(h), _ptr(dL_dstate), _ptr(dL_dcontrols),
-                                               _ptr(worlds), _ptr(tape_slots), int(worlds.numel()), _stream(stream)),
+        n = int(worlds.numel())
+        self._check(lib().ostrich_adjoint_list(self._h, self._arr(dL_dnext, self.n_state, "dL_dnext"), float(h),
+                                               self._arr(dL_dstate, self.n_state, "dL_dstate"),
+                                               self._arr(dL_dcontrols, self.n_servo, "dL_dcontrols"),
+                                               self._i32(worlds, n, "worlds"), self._i32(tape_slots, n, "tape_slots"),
+                                               n, _stream(stream)),
                     "ostrich_adjoint_list")
 
     def ostrich_debug_trace(self, merits):
-        self._check(lib().ostrich_debug_trace(self._h, _ptr(merits)), "ostrich_debug_trace")
+        import torch
+        self._check(lib().ostrich_debug_trace(self._h, _checked(merits, torch.float64,
+                                                                self.n_worlds * (self.cfg.budget + 2), "merits")),
+                    "ostrich_debug_trace")
 
     def ostrich_tape_clear(self):
         self._check(lib().ostrich_tape_clear(self._h), "ostrich_tape_clear")

@@ -109,3 +109,17 @@ def test_noalloc_capacity_of_the_robot_and_refusals(lib):
     with pytest.raises(ValueError):
         M.noalloc_capacity(S.terrain_scene(n=16))
     assert lib.ostrich_noalloc_capacity(None, None, None, None) == OSTRICH_EINVAL
+
+
+def test_binding_checks_element_type_and_size_before_the_pointer():
+    """The binding hands the library raw pointers, so it checks first what the library
+    will assume: the element type and enough elements for [rows, ld] (a smaller array
+    would be overrun on the device); a host tensor is refused as well."""
+    torch = pytest.importorskip("torch")
+    with pytest.raises(ValueError, match="element type"):
+        M._checked(torch.zeros(8, dtype=torch.float64), torch.float32, 8, "state_in")
+    with pytest.raises(ValueError, match="at least 9 elements"):
+        M._checked(torch.zeros(8, dtype=torch.float32), torch.float32, 9, "state_in")
+    with pytest.raises(ValueError, match="host tensor"):
+        M._checked(torch.zeros(9, dtype=torch.float32), torch.float32, 9, "state_in")
+    assert M._checked(None, torch.float32, 9, "state_in") is None

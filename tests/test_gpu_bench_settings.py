@@ -1,4 +1,5 @@
-"""The benchmarked configuration under parity, every world accounted for.
+"""The benchmarked configurations under parity, every world accounted for: the robot
+over the box obstacle below, and the mesh terrain (test_terrain_bench_settings_every_world).
 
 Workload: the robot over the box obstacle in FP32 with the settings bench.py times
 (Newton budget 16, k_min 4, tol 1e-4 m/s on sqrt(merit), full steps; also with the

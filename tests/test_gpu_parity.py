@@ -283,6 +283,34 @@ def test_hinged_boxes_matches_oracle(ostrich, dtype):
                  oracle_cfg=S.SolverConfig(budget=60, tol=1e-8), floor=3e-4, tol_grad_exact=3e-3)
 
 
+def test_tilted_wheel_closed_form_fp64(ostrich):
+    """The CUDA path's heightmap contacts, friction rows and rotation-rate map against the
+    closed form of a free wheel released on a planar slope (one step from rest: rolling
+    under sticking friction with the contact compliance kappa; the closed form and its
+    derivation sit beside the oracle's pin of the same case).  The contact frames come
+    from the oracle's FP32 contact generation, whose index set the step matches bit for
+    bit; FP64 build, tangential and angular velocities to 1e-8, the sinking velocity and
+    the normal force to 1e-7, friction magnitudes to 1e-6."""
+    from tests.test_oracle_terrain import _tilted_wheel, tilted_wheel_closed_form
+    sc, st = _tilted_wheel()
+    h, kappa = 0.1, 1e-4
+    cfg = S.SolverConfig(budget=60, tol=1e-12, kappa=kappa)
+    r = _run_gpu(ostrich, sc, cfg, st, np.zeros((0, 1)), h, "f64")
+    act, ids, nd = O.Oracle(sc, cfg).contacts(st[:, 0], h)
+    assert np.array_equal(r["ids"][:, 0].numpy(), ids)
+    assert int(r["status"][0]) == 0
+    sl = np.nonzero(act)[0]
+    t, nu, v_t, v_n, w, N, F = tilted_wheel_closed_form(sc, st, h, kappa, nd, sl)
+    out = r["state"][:, 0].numpy()
+    u = out[7:13]
+    assert abs(u[0:3] @ t - v_t) <= 1e-8 * abs(v_t)
+    assert abs(u[0:3] @ nu - v_n) <= 1e-7 * abs(v_n)
+    assert abs(u[4] - w) <= 1e-8 * abs(w)
+    lam = out[sc.contact_lam_index:].reshape(-1, 3)[sl]
+    assert abs(lam[:, 0].sum() - N) <= 1e-7 * N
+    assert np.abs(np.hypot(lam[:, 1], lam[:, 2]) - abs(F) / len(sl)).max() <= 1e-6 * abs(F)
+
+
 @pytest.mark.parametrize("dtype", ["f64", "f32"])
 def test_resting_robot_closed_form(ostrich, dtype):
     """The CUDA path against the closed form of the robot standing on the plane (equal

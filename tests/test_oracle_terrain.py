@@ -10,7 +10,12 @@
 * Stored face planes are unit normals pointing up, with d = n . vertex.
 * Converged terrain steps satisfy non-penetration, complementarity sign and the cone.
 * Rows on terrain match the definition d c(q+(u))/du / h (dual numbers).
+* A free wheel released on a planar slope (a tilted heightmap) follows the closed form
+  of one backward-Euler step with sticking friction: rolling with the contact
+  compliance kappa and the rotation-rate map of Eq. (1) on the axle direction.
 """
+import math
+
 import numpy as np
 import pytest
 
@@ -234,3 +239,83 @@ def test_robot_resting_on_flat_heightmap_closed_form():
     assert np.abs(cl[:, 1:]).max() <= 1e-9 * ln
     u = r["state"][7 * nb:13 * nb].reshape(nb, 6)
     assert np.abs(u[:, 2] - uz).max() <= 1e-9 * abs(uz)
+
+
+def _tilted_wheel(theta=0.1, n=64, sp=0.05):
+    """One free wheel (the robot's: 1 kg, r = 0.15 m, half width 0.04 m, axle along body
+    y) at rest on a planar heightmap z = tan(theta) x, its rims touching the plane inside
+    one triangle each (local cell coordinates (0.04, 0.005) and (0.04, 0.035))."""
+    s = math.tan(theta)
+    ox = oy = -(n // 2) * sp
+    xs = ox + sp * np.arange(n)
+    H = np.repeat((s * xs)[:, None], n, axis=1).astype(np.float32)
+    bodies, _ = S.robot_bodies_joints()
+    wheel = bodies[1]
+    sc = S.Scene("tilted", [wheel], [], S.Env(S.ENV_HEIGHTMAP, heights=H, spacing=sp, origin=(ox, oy)), 1.0)
+    xc, y1 = 0.04, 0.005                       # contact point of rim 0 (x) and its y
+    nrm = np.array([-s, 0.0, 1.0]) / math.hypot(s, 1.0)
+    p = np.array([xc, y1 + wheel.half_width, s * xc]) + wheel.radius * nrm
+    st = np.zeros((sc.n_state, 1))
+    st[0:3, 0] = p
+    st[3, 0] = 1.0
+    return sc, st
+
+
+def tilted_wheel_closed_form(sc, st, h, kappa, nd, sl):
+    """(downhill unit tangent t, unit normal, v_t, v_n, w, N, F) of one step of the wheel
+    of _tilted_wheel from rest, given the active slots sl and their contact frames nd."""
+    m, r, I = sc.bodies[0].mass, sc.bodies[0].radius, sc.bodies[0].inertia[1]
+    nc, g = len(sl), -sc.gravity
+    n = nd[sl, :3].astype(np.float64).mean(axis=0)
+    cos_t = n[2] / np.linalg.norm(n)
+    down = np.array([0.0, 0.0, -1.0]) - (-n[2] / (n @ n)) * n
+    t = down / np.linalg.norm(down)
+    sin_t = float(np.linalg.norm(down))
+    cn0 = float(n @ st[0:3, 0]) - r * np.linalg.norm(n) - float(nd[sl, 3].mean())
+    gamma, F, w = 1.0, 0.0, 0.0
+    for _ in range(50):                    # fixed point on gamma (|h w / 2| ~ 0.02)
+        F = -h * g * sin_t / (h / m + h * gamma ** 2 * r * r / I + kappa / nc)
+        w = h * gamma * r * F / I
+        gamma = 1.0 / (1.0 + (h * w / 2.0) ** 2)
+    N = (h * m * g * cos_t - m * cn0 / h) / (h + m * kappa / nc)
+    v_t = h * g * sin_t + h * F / m
+    v_n = -cn0 / h - kappa * N / nc
+    return t, n / np.linalg.norm(n), v_t, v_n, w, N, F
+
+
+def test_wheel_on_tilted_heightmap_closed_form():
+    """A free wheel released on a planar slope (Sec. III-A/B, backward Euler with sticking
+    friction): one step from rest is linear in the total friction force F (along the
+    downhill tangent t) and the total normal force N over the n_c contacts (one per rim):
+        m v_t = h (m g sin(theta) + F),  I w = h gamma r F,  v_t + gamma r w = -kappa F / n_c
+    (the friction rows: slip velocity = -kappa lambda_f, W = 0 when sticking; gamma =
+    1 / (1 + (h w / 2)^2) is the rotation-rate map of Eq. (1) on the axle direction),
+        m v_n = h (N - m g cos(theta)),  v_n = -c_n(q-) / h - kappa N / n_c
+    (the FB normal rows at a positive multiplier: c_n(q+) / h + kappa lambda_n = 0).  The
+    kappa and gamma terms move F by 2e-4 and 3e-4 of itself and kappa moves N by 5e-4;
+    the pin holds the tangential and angular velocities to 1e-8 (they agree to 1e-10), the
+    sinking velocity -kappa N / n_c - c_n(q-) / h to 1e-7, the per-contact friction
+    magnitudes to 1e-6 and N to 1e-7 (the two faces' FP32 normals differ by a rounding,
+    which splits F and N unevenly at that level)."""
+    sc, st = _tilted_wheel()
+    h, kappa = 0.1, 1e-4
+    cfg = S.SolverConfig(budget=60, tol=1e-12, kappa=kappa)
+    orc = O.Oracle(sc, cfg)
+    res = orc.step(st[:, 0], np.zeros(1), h)
+    assert res["status"] == 0
+    act, _, nd = orc.contacts(st[:, 0], h)
+    sl = np.nonzero(act)[0]
+    assert sl.tolist() == [0, 8]                        # one face under each rim
+    # the two faces' FP32 normals agree to a rounding (their vertices' FP32 coordinates
+    # differ); the closed form takes their mean, the bounds below allow for the rest
+    assert np.abs(nd[sl[0]] - nd[sl[1]]).max() <= 1e-6
+    t, nu, v_t, v_n, w, N, F = tilted_wheel_closed_form(sc, st, h, kappa, nd, sl)
+    nc = len(sl)
+    u = res["state"][7:13]
+    assert abs(u[0:3] @ t - v_t) <= 1e-8 * abs(v_t)
+    assert abs(u[0:3] @ nu - v_n) <= 1e-7 * abs(v_n)
+    assert abs(u[1]) <= 1e-6 * abs(v_t) and np.abs(u[[3, 5]]).max() <= 1e-6 * abs(w)
+    assert abs(u[4] - w) <= 1e-8 * abs(w)
+    lam = res["state"][sc.contact_lam_index:].reshape(-1, 3)[sl]
+    assert abs(lam[:, 0].sum() - N) <= 1e-7 * N
+    assert np.abs(np.hypot(lam[:, 1], lam[:, 2]) - abs(F) / nc).max() <= 1e-6 * abs(F)

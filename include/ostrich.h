@@ -251,7 +251,13 @@ size_t ostrich_tape_bytes(const ostrich_ctx* ctx);
  * allocation of one CTA); with the registers it bounds the worlds resident per SM. */
 size_t ostrich_workspace_bytes(const ostrich_ctx* ctx);
 
+/* Message of the context's last failed call (a NUL-terminated string owned by the
+ * context, valid until its next failing call or ostrich_destroy; "" when none failed);
+ * for a NULL context a fixed message. */
 const char* ostrich_last_error(const ostrich_ctx* ctx);
+
+/* Free the context, its tape and its device buffers (cudaFree; NULL is ignored).  No
+ * call may use the context afterwards, and no queued work may still read its tape. */
 void ostrich_destroy(ostrich_ctx* ctx);
 
 /* Allocation-free step + adjoint (FP32), for callers that cannot call cudaMalloc: a
